@@ -1,0 +1,300 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+None of these compares the oracle with a retyped copy of itself: each check
+is a closed form, an invariant, a textbook result, a hand-evaluated fixture
+(tests/golden/) or an exhaustive brute force on a tiny input, chosen so that
+a dropped term, a flipped sign, a wrong index or normalisation fails one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def complete_csr(n):
+    rows = [[j for j in range(n) if j != i] for i in range(n)]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=rowptr[1:])
+    col = np.array([c for r in rows for c in r], dtype=np.int32)
+    return rowptr, col
+
+
+# ---------------------------------------------------------------- integrators
+
+def test_rk4_linear_amplification(oracle_mod):
+    """One RK4 step of x' = lam x multiplies by 1 + z + z^2/2 + z^3/6 + z^4/24,
+    z = lam dt (textbook stability polynomial); Euler by 1 + z."""
+    for lam in (-1.0, -3.7, 0.4):
+        for dt in (0.01, 0.1, 0.5):
+            z = lam * dt
+            x0 = np.array([1.0, -2.5, 3.25])
+            x1 = oracle_mod.rk4_step(lambda x: lam * x, x0, dt)
+            R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+            np.testing.assert_allclose(x1, R * x0, rtol=1e-15, atol=0)
+            xe = oracle_mod.euler_step(lambda x: lam * x, x0, dt)
+            np.testing.assert_allclose(xe, (1 + z) * x0, rtol=1e-15, atol=0)
+
+
+def test_rk4_fourth_order_on_adler_equation(oracle_mod):
+    """Two linked identical oscillators: psi = theta_2 - theta_1 obeys
+    psi' = -K sin psi (N = 2, so each node gets (K/2) sin of the difference),
+    solved by tan(psi/2) = tan(psi0/2) e^{-K t}; the mean phase moves at omega.
+    Halving dt must shrink the RK4 error by about 2^4."""
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([1, 0], dtype=np.int32)
+    K, omega, psi0, T = 1.5, 0.3, 2.0, 2.0
+    th0 = np.array([0.1, 0.1 + psi0])
+    om = np.array([omega, omega])
+    rhs = lambda th: oracle_mod.kuramoto_direct(rowptr, col, th, om, K)
+    exact_psi = 2 * math.atan(math.tan(psi0 / 2) * math.exp(-K * T))
+    errs = []
+    for steps in (40, 80):
+        th, _ = oracle_mod.integrate(rhs, th0, T / steps, steps)
+        errs.append(abs((th[1] - th[0]) - exact_psi))
+        assert abs(th.mean() - (th0.mean() + omega * T)) < 1e-13
+    assert errs[0] < 1e-6
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
+def test_adler_phase_locking_sign(oracle_mod):
+    """With omega_2 - omega_1 = d and |d| < K the difference locks at
+    arcsin(d / K) (psi' = d - K sin psi); a sign error in h or in omega would
+    lock at the mirrored angle or drift."""
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([1, 0], dtype=np.int32)
+    K, d = 2.0, 0.8
+    om = np.array([0.0, d])
+    rhs = lambda th: oracle_mod.kuramoto_direct(rowptr, col, th, om, K)
+    th, _ = oracle_mod.integrate(rhs, np.array([0.0, 0.0]), 0.01, 3000)
+    assert abs((th[1] - th[0]) - math.asin(d / K)) < 1e-9
+
+
+# ---------------------------------------------------------------- P1 split
+
+def test_split_is_lossless_and_permutation_consistent(oracle_mod):
+    for seed in range(4):
+        g = S.random_labels_graph(37, 0.3, 4, seed=seed, free_frac=0.2)
+        sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+        n = g.n
+        assert np.array_equal(sp.perm[sp.iperm], np.arange(n))
+        assert np.all(np.diff(sp.off) >= 0)
+        assert sp.off[-1] == int((g.labels >= 0).sum())
+        # communities are contiguous and ordered by label, ids ascending inside
+        for c in range(sp.M):
+            members = sp.perm[sp.off[c]:sp.off[c + 1]]
+            assert np.all(g.labels[members] == c)
+            assert np.all(np.diff(members) > 0)
+        # B = D + S reproduces P A P^T exactly
+        rp, cl = oracle_mod.rebuild_b(sp)
+        for m in range(n):
+            i = sp.perm[m]
+            want = np.sort(sp.iperm[g.col[g.rowptr[i]:g.rowptr[i + 1]]])
+            assert np.array_equal(cl[rp[m]:rp[m + 1]], want)
+        # S holds -1 on the diagonal of every community block
+        for m in range(sp.off[-1]):
+            row = sp.s_col[sp.s_rowptr[m]:sp.s_rowptr[m + 1]]
+            vals = sp.s_val[sp.s_rowptr[m]:sp.s_rowptr[m + 1]]
+            assert vals[list(row).index(m)] == -1
+
+
+# ---------------------------------------------------------------- Kuramoto
+
+@pytest.mark.parametrize("d_sin,d_cos", [((1.0,), (0.0,)), ((0.0,), (1.0,)),
+                                         ((0.7, -0.2, 0.05), (0.3, 0.1, -0.4))])
+def test_cia_equals_direct_on_complete_communities(oracle_mod, d_sin, d_cos):
+    """The addition theorems make E1 exact for a finite Fourier coupling
+    (Sec. 3.2, App. A.4): on complete communities with no extra links, S is
+    the diagonal only and the CIA equals the direct sum to rounding."""
+    g = S.complete_graph_communities([7, 12, 5], seed=11)
+    rng = np.random.default_rng(3)
+    th = rng.uniform(0, 2 * np.pi, g.n)
+    om = rng.normal(size=g.n)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    assert np.all(sp.s_val == -1) and len(sp.s_col) == g.n
+    d = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 2.5, d_sin, d_cos)
+    c = oracle_mod.kuramoto_cia(sp, th[sp.perm], om[sp.perm], 2.5, d_sin, d_cos)
+    np.testing.assert_allclose(c, d[sp.perm], rtol=0, atol=1e-13)
+
+
+def test_cosine_coupling_closed_form(oracle_mod):
+    """h = cos on a complete graph with equal phases: every node gets
+    omega + K (N-1)/N, since a_mm = 0 (the diagonal of the block is removed)."""
+    n = 9
+    rowptr, col = complete_csr(n)
+    labels = np.zeros(n, dtype=np.int32)
+    th = np.full(n, 0.77)
+    om = np.linspace(-1, 1, n)
+    sp = oracle_mod.split(rowptr, col, labels)
+    for f in (lambda: oracle_mod.kuramoto_direct(rowptr, col, th, om, 3.0, (0.0,), (1.0,)),
+              lambda: oracle_mod.kuramoto_cia(sp, th[sp.perm], om[sp.perm], 3.0,
+                                              (0.0,), (1.0,))[sp.iperm]):
+        np.testing.assert_allclose(f(), om + 3.0 * (n - 1) / n, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cia_equals_brute_force_on_tiny_random_graphs(oracle_mod, seed):
+    """Exhaustive check on <= 50 nodes: arbitrary labels (unlabelled nodes,
+    empty communities, dense S) must still give the direct sum."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 51))
+    g = S.random_labels_graph(n, float(rng.uniform(0.05, 0.9)), int(rng.integers(1, 6)),
+                              seed=seed, free_frac=0.15)
+    th = rng.uniform(-10, 10, n)
+    om = rng.normal(size=n)
+    ds, dc = rng.normal(size=2), rng.normal(size=2)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    d = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 1.3, ds, dc)
+    c = oracle_mod.kuramoto_cia(sp, th[sp.perm], om[sp.perm], 1.3, ds, dc)
+    np.testing.assert_allclose(c[sp.iperm], d, rtol=0, atol=1e-12)
+
+
+def test_sum_of_rhs_equals_sum_of_frequencies(oracle_mod):
+    """For symmetric A and odd h the coupling cancels pairwise: sum theta' =
+    sum omega (direct and CIA)."""
+    w = S.kuramoto_sbm_small(scale=0.25)
+    g = w.graph
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    d = oracle_mod.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K, (1.0, 0.5), (0.0, 0.0))
+    c = oracle_mod.kuramoto_cia(sp, w.theta0[sp.perm], w.omega[sp.perm], w.K, (1.0, 0.5), (0.0, 0.0))
+    assert abs(d.sum() - w.omega.sum()) < 1e-11
+    assert abs(c.sum() - w.omega.sum()) < 1e-11
+    assert np.abs(d - w.omega).max() > 1e-2   # the coupling is not trivially zero
+
+
+def test_identical_all_to_all_synchronises(oracle_mod):
+    """Identical oscillators, all-to-all: a gradient flow of -r^2 (textbook),
+    so r(t) never decreases and tends to 1."""
+    n = 64
+    rowptr, col = complete_csr(n)
+    sp = oracle_mod.split(rowptr, col, np.zeros(n, dtype=np.int32))
+    th0 = np.random.default_rng(5).uniform(0, 2 * np.pi, n)
+    rhs = lambda x: oracle_mod.kuramoto_cia(sp, x, np.zeros(n), 1.0)
+    _, r = oracle_mod.integrate(rhs, th0, 0.05, 800, wrap=True,
+                                observe=oracle_mod.order_parameter)
+    r = np.array(r)
+    assert np.all(np.diff(r) > -1e-12)
+    assert r[-1] > 1 - 1e-6
+
+
+def test_lorentzian_self_consistency(oracle_mod):
+    """All-to-all Kuramoto with Lorentzian frequencies of half-width D has the
+    stationary order parameter r = sqrt(1 - 2D/K) for K > 2D (Kuramoto's
+    self-consistency; textbook, not in the paper).  Deterministic quantiles of
+    the Lorentzian keep the finite-N deviation small."""
+    n, D, K = 1500, 0.5, 2.0
+    q = (np.arange(n) + 0.5) / n
+    om = D * np.tan(np.pi * (q - 0.5))
+    rowptr, col = complete_csr(n)
+    sp = oracle_mod.split(rowptr, col, np.zeros(n, dtype=np.int32))
+    th0 = np.random.default_rng(9).uniform(0, 2 * np.pi, n)
+    rhs = lambda x: oracle_mod.kuramoto_cia(sp, x, om, K)
+    _, r = oracle_mod.integrate(rhs, th0, 0.05, 1200, wrap=True,
+                                observe=oracle_mod.order_parameter)
+    r_late = float(np.mean(r[-400:]))
+    assert abs(r_late - math.sqrt(1 - 2 * D / K)) < 0.02
+
+
+# ---------------------------------------------------------------- higher order
+
+def test_triadic_hand_evaluated(oracle_mod):
+    gd = json.load(open(os.path.join(GOLDEN, "triadic_three_nodes.json")))
+    n = gd["N"]
+    rowptr, col = complete_csr(n)
+    sp = oracle_mod.split(rowptr, col, np.zeros(n, dtype=np.int32))
+    phi = np.array(gd["phi"])
+    d = oracle_mod.ho_triadic_direct(sp, phi, gd["K2"], np.arange(n))
+    c = oracle_mod.ho_triadic_cia(sp, phi, gd["K2"])
+    np.testing.assert_allclose(d, gd["expected"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(c, gd["expected"], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_triadic_moments_equal_brute_force(oracle_mod, seed):
+    """The moment formula with the degenerate tuples removed equals the plain
+    sum over ordered pairs of distinct other members (App. A.7)."""
+    rng = np.random.default_rng(seed)
+    g = S.random_labels_graph(48, 0.2, 3, seed=seed, free_frac=0.1)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    phi = rng.uniform(-4, 4, g.n)
+    d = oracle_mod.ho_triadic_direct(sp, phi, 2.0, np.arange(g.n))
+    c = oracle_mod.ho_triadic_cia(sp, phi, 2.0)
+    np.testing.assert_allclose(c, d, rtol=0, atol=1e-13)
+    assert np.abs(d).max() > 1e-4
+
+
+# ---------------------------------------------------------------- Cucker-Smale
+
+def test_cs_two_agents_hand_evaluated(oracle_mod):
+    gd = json.load(open(os.path.join(GOLDEN, "cucker_smale_two_agents.json")))
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    col = np.array([1, 0], dtype=np.int32)
+    out = oracle_mod.cs_direct(rowptr, col, np.array(gd["x"]), 1.0, 1.0, 0.4)
+    np.testing.assert_allclose(out, gd["expected"], rtol=0, atol=1e-15)
+
+
+def test_cs_momentum_conservation(oracle_mod):
+    """Symmetric A and an even weight: sum_m v_m' = 0."""
+    g = S.sbm_graph([30, 25, 20], 0.8, inter_degree=3.0, seed=4)
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(0, 10, (g.n, 2)), rng.normal(size=(g.n, 2))], axis=1)
+    out = oracle_mod.cs_direct(g.rowptr, g.col, x)
+    assert np.abs(out[:, 2:].sum(axis=0)).max() < 1e-14
+    assert np.abs(out[:, 2:]).max() > 1e-3
+
+
+def test_cs_cia_exact_for_constant_weight(oracle_mod):
+    """With beta = 0 the weight is the constant K, exactly separable with the
+    single feature sqrt(K); the CIA must then equal the direct sum."""
+    g = S.random_labels_graph(40, 0.4, 3, seed=8, free_frac=0.1)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    rng = np.random.default_rng(2)
+    x = np.concatenate([rng.uniform(0, 10, (g.n, 2)), rng.normal(size=(g.n, 2))], axis=1)
+    K = 1.7
+    d = oracle_mod.cs_direct(g.rowptr, g.col, x, K, 1.0, 0.0)
+    feat = np.full((g.n, 1), math.sqrt(K))
+    c = oracle_mod.cs_cia(sp, x[sp.perm], feat, K, 1.0, 0.0)
+    np.testing.assert_allclose(c[sp.iperm], d, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- learned basis
+
+def _params(rng, H=8, R=4):
+    return {"W1": rng.normal(size=(H, 2)), "b1": rng.normal(size=H),
+            "W2": rng.normal(size=(R, H)) / np.sqrt(H), "b2": rng.normal(size=R) * 0.1}
+
+
+def test_mlp_forward_hand_evaluated(oracle_mod):
+    """H = R = 1: phi(x) = w2 silu(w1 . x + b1) + b2; silu(0) = 0 and
+    silu(1) = 1/(1 + e^-1)."""
+    p = {"W1": np.array([[1.0, -2.0]]), "b1": np.array([0.0]),
+         "W2": np.array([[3.0]]), "b2": np.array([0.25])}
+    out, _ = oracle_mod.mlp_forward(p, np.array([[2.0, 1.0], [1.0, 0.0]]))
+    np.testing.assert_allclose(out[:, 0], [0.25, 3.0 / (1.0 + math.exp(-1.0)) + 0.25],
+                               rtol=0, atol=1e-15)
+
+
+def test_mlp_gradient_central_differences(oracle_mod):
+    rng = np.random.default_rng(0)
+    p = _params(rng)
+    a, c = rng.normal(size=(16, 2)), rng.normal(size=(16, 2))
+    t = oracle_mod.cs_kernel_weight(((a - c) ** 2).sum(axis=1))
+    loss, grads = oracle_mod.pair_loss_grad(p, a, c, t)
+    assert abs(loss - oracle_mod.pair_loss(p, a, c, t)) < 1e-15
+    h = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in range(flat.size):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = oracle_mod.pair_loss(p, a, c, t)
+            flat[idx] = old - h
+            lm = oracle_mod.pair_loss(p, a, c, t)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grads[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), (k, idx)
