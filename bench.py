@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput of the CIA hot path on one GB300 (or N replicas under torchrun).
+
+Workload: Kuramoto network, N = 262144 oscillators in 256 planted communities
+with lognormal sizes (mean 1024, sigma 0.5), p_in = 0.95, inter-community
+Erdos-Renyi links of mean degree 8, omega ~ Cauchy(0, 0.5), K = 2, RK4 with
+dt = 0.01; FP32 stage state and observables, FP64 time accumulation.
+
+One step = one classical RK4 step of the whole network (four right-hand-side
+evaluations with the CIA: observables + sparse corrections + stage update).
+Metric: node-updates/s = N x steps / device time, next to the direct CSR
+method on the same GPU and the error of both against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The L2 cache (129 MB) is flushed between timed steps by writing a 256 MB
+buffer outside the timed events.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CIA node-updates/s vs direct RHS on 1 GB300 at fixed FP64-oracle error; % HBM roof"
+UNIT = "node-updates/s"
+WORKLOAD = ("kuramoto_lognormal: N=262144, 256 lognormal communities (mean 1024, sigma 0.5), "
+            "p_in=0.95, inter ER degree 8, omega~Cauchy(0,0.5), K=2, RK4 dt=0.01, "
+            "FP32 state + FP64 time accumulation")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full size)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-method timing")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
+    ap.add_argument("--cpu-steps", type=int, default=0, help="oracle RK4 steps in the CPU sample")
+    return ap.parse_args()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ byte model
+
+def stage_bytes(info: dict, precision: str) -> float:
+    """Algorithmic (compulsory) bytes of one CIA stage launch, averaged over
+    the four RK4 stages.
+
+    Per node: its stage phasor read once (8 B; every gather of it, from the
+    shared-memory community window or from L2, reuses that read), the FP64
+    master (8 B), the next-stage frequency constant (4 B), the stage
+    accumulator read in 3 of 4 stages (3 B on average) and written (4 B), the
+    next phasor written (8 B); the final stage also writes the master and
+    reads wrap(dt omega) in FP64 (+12 B, i.e. +3 B on average): 38 B.
+    Per missing link: its 16-bit community-local index (2 B).
+    Per inter-community link: its 32-bit index (4 B).
+    """
+    rb = 4 if precision == "fp32" else 8
+    c = 2 * rb
+    per_node = c + 8 + rb + 0.75 * rb + rb + c + 0.25 * (8 + 8 - rb)
+    return (info["n"] * per_node + info["nnz_missing"] * info["missing_index_bytes"]
+            + info["nnz_inter"] * 4)
+
+
+def direct_stage_bytes(info: dict, precision: str) -> float:
+    """Same per-node bytes plus the row pointer (8 B) and 4 B per CSR entry."""
+    rb = 4 if precision == "fp32" else 8
+    c = 2 * rb
+    per_node = c + 8 + rb + 0.75 * rb + rb + c + 0.25 * (8 + 8 - rb) + 8
+    return info["n"] * per_node + info["nnz_graph"] * 4
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(w, steps: int) -> dict:
+    """The FP64 oracle's CIA (as it stands) on the full network, timed for a
+    bounded number of RK4 steps on the host cores; node-updates/s."""
+    import oracle
+    g = w.graph
+    sp = oracle.split(g.rowptr, g.col, g.labels)
+    phi = w.theta0[sp.perm].copy()
+    om = w.omega[sp.perm].copy()
+    rhs = lambda x: oracle.kuramoto_cia(sp, x, om, w.K)
+    if steps <= 0:
+        t0 = time.perf_counter()
+        rhs(phi)
+        one = time.perf_counter() - t0
+        steps = max(1, min(200, int(15.0 / max(4 * one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.integrate(rhs, phi, w.dt, steps, wrap=True)
+    el = time.perf_counter() - t0
+    return {"value": g.n * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "%d RK4 steps of the full %d-node network (FP64 CIA "
+            "oracle, OpenMP over nodes), %.1f s" % (steps, g.n, el), "seconds": el,
+            "steps": steps}
+
+
+def coupling_rel_err(got, ref, omega) -> float:
+    """inf-norm error of the coupling part (RHS minus omega), relative."""
+    return float(np.abs((got - omega) - (ref - omega)).max() / np.abs(ref - omega).max())
+
+
+def cpu_leg(w, steps: int, gpu_rhs: dict):
+    """CPU leg: the FP64 oracle judges the GPU right-hand sides at the initial
+    state, and its own CIA is timed as the CPU baseline."""
+    import oracle
+    oracle.set_num_threads(host_cores())
+    g = w.graph
+    ref = oracle.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
+    err = {m: coupling_rel_err(v, ref, w.omega) for m, v in gpu_rhs.items()}
+    return oracle_sample(w, steps), err
+
+
+def reference_arm(args, w):
+    import oracle
+    cores = host_cores()
+    oracle.set_num_threads(cores)
+    g = w.graph
+    sp = oracle.split(g.rowptr, g.col, g.labels)
+    phi = w.theta0[sp.perm].copy()
+    om = w.omega[sp.perm].copy()
+    rhs = lambda x: oracle.kuramoto_cia(sp, x, om, w.K)
+    for _ in range(args.warmup):
+        phi = oracle.wrap_phase(oracle.rk4_step(rhs, phi, w.dt))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi = oracle.wrap_phase(oracle.rk4_step(rhs, phi, w.dt))
+    el = time.perf_counter() - t0
+    value = g.n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": "each step one RK4 step of the full network with the FP64 "
+                                       "CIA oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, profile: bool):
+    plan.state_load(x0)
+    for _ in range(warmup):
+        plan.advance(dt, 1, method=method)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if profile:
+        plan.profile_begin(4 * steps)
+    for i in range(steps):
+        flush.add_(1.0)                 # evict L2 between timed steps (outside the events)
+        ev[i][0].record()
+        plan.advance(dt, 1, method=method)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    prof = plan.profile_end() if profile else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, prof
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import synthetic as S
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = S.kuramoto_lognormal(scale=args.scale)
+        reference_arm(args, w)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2203_16657_gb300 as cia
+    w = S.kuramoto_lognormal(scale=args.scale)
+    g = w.graph
+    plan = cia.Plan(g.rowptr, g.col, g.labels, w.omega, K=w.K, precision="fp32",
+                    build_direct=not args.no_direct)
+    info = plan.info()
+    x0 = torch.from_numpy(w.theta0.copy()).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    # the GPU right-hand sides at the initial state, judged in the CPU leg
+    gpu_rhs = {}
+    if rank == 0:
+        for m in ("cia",) if args.no_direct else ("cia", "direct"):
+            gpu_rhs[m] = plan.rhs(x0, method=m).cpu().numpy()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # CIA, timed
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, prof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "cia", flush, True)
+    barrier()
+    total_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * g.n * args.steps / (total_ms / 1e3)
+
+    # direct method, same GPU, same steps
+    dtotal, dprof = None, None
+    if not args.no_direct:
+        dms, dprof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "direct", flush, True)
+        dtotal = float(sum(dms))
+
+    # end to end through the public host-buffer call: copies in every step
+    e2e_s = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(w.theta0.copy()).pin_memory().numpy()
+        rh = torch.zeros(1, dtype=torch.float64).pin_memory().numpy()
+        for _ in range(args.warmup):
+            plan.integrate_host(xh, w.dt, 1, r_out=rh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.integrate_host(xh, w.dt, 1, r_out=rh)
+        e2e_s = time.perf_counter() - t0
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    sb = stage_bytes(info, "fp32")
+    achieved = sb / (stage_avg_ms * 1e-3) / 1e9
+    direct = None
+    if dprof is not None:
+        d_stage_avg_ms = dprof["stage_ms"] / max(1, dprof["stage_launches"])
+        direct = {"value": g.n * args.steps / (dtotal / 1e3), "unit": UNIT,
+                  "ms_per_step": dtotal / args.steps,
+                  "speedup_cia_over_direct": dtotal / max(total_ms, 1e-12),
+                  "stage_kernel_gbs": direct_stage_bytes(info, "fp32") / (d_stage_avg_ms * 1e-3) / 1e9,
+                  "avg_launch_ms": d_stage_avg_ms}
+
+    cpu, err = None, {}
+    if not args.no_cpu_baseline:
+        cpu, err = cpu_leg(w, args.cpu_steps, gpu_rhs)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "communities": info["M"],
+                   "nnz_graph": info["nnz_graph"], "nnz_missing": info["nnz_missing"],
+                   "nnz_inter": info["nnz_inter"], "method": "cia", "precision": "fp32+fp64acc",
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "group_size": info["group_size"], "tile_nodes": info["tile_nodes"]},
+        "error_vs_fp64_oracle": {"cia_rhs_coupling_rel": err.get("cia"),
+                                 "direct_rhs_coupling_rel": err.get("direct")},
+        "direct": direct,
+        "e2e": None if e2e_s is None else {
+            "value": g.n * args.steps / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 8},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "stage_kernel (CIA RK4 stage)", "bytes_per_launch": sb,
+                     "avg_launch_ms": stage_avg_ms, "peak_source": pk["source"]},
+        "gpu_launches": int(prof["stage_launches"] + prof["other_launches"]),
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * cia.h -- C ABI of the GB300 community integration algorithm (CIA) library.
+ *
+ * The library evaluates the right-hand side of a network ODE
+ *
+ *     x_m' = f_m(x_m) + (1/N) sum_l a_ml g(x_l, x_m),   m = 1..N
+ *
+ * (eq. GeneralNetworkSystem, Sec. 2 of Boehle, Thalhammer, Kuehn, "Community
+ * Integration Algorithms (CIAs) for Dynamical Systems on Networks",
+ * arXiv 2203.16657) with the CIA of Sec. 3: community observables stand in for
+ * the dense diagonal blocks D of the permuted adjacency B = P A P^T = D + S,
+ * and the sparse remainder S (missing links inside a block, extra links
+ * between blocks) is summed directly.  A direct O(|E|) CSR evaluation of the
+ * same sum is provided for comparison.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a cia_status; nothing aborts, throws or exits.  The
+ *    text of the last error of the calling thread is cia_last_error().
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the device that was current when the plan was made.
+ *  - State at the boundary is always FP64 in the ORIGINAL node numbering of
+ *    the graph.  The compute precision inside is the plan's (cia_options).
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is asynchronous on that stream; an asynchronous CUDA error
+ *    surfaces as CIA_ERR_CUDA from a later call on the same plan.
+ *  - The caller owns every buffer it passes; the plan owns the device copies
+ *    of the network structure and its work buffers until cia_plan_destroy.
+ *  - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef CIA_H
+#define CIA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CIA_OK = 0,
+    CIA_ERR_INVALID_ARG = 1,    /* null pointer, bad size or option */
+    CIA_ERR_INVALID_GRAPH = 2,  /* asymmetric, self loop, unsorted/duplicate or out-of-range column */
+    CIA_ERR_UNSUPPORTED = 3,    /* valid request the library does not implement */
+    CIA_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
+    CIA_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    CIA_ERR_FALLBACK = 6,       /* informational: a learned basis failed its check, direct was used */
+    CIA_ERR_NUMERIC = 7,        /* NaN or Inf in an input */
+    CIA_ERR_OOM = 8             /* device or host allocation failed */
+} cia_status;
+
+typedef enum {
+    CIA_MODEL_KURAMOTO = 0      /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
+} cia_model;
+
+typedef enum {
+    CIA_FP64 = 0,               /* state, observables and sums in FP64 */
+    CIA_FP32 = 1                /* stage state, observables and sums in FP32; FP64 time accumulation */
+} cia_precision;
+
+typedef enum {
+    CIA_METHOD_CIA = 0,         /* community observables + sparse corrections (Sec. 3.2, E1 + E2) */
+    CIA_METHOD_DIRECT = 1       /* direct O(|E|) sum over the CSR neighbours */
+} cia_method;
+
+#define CIA_MAX_HARMONICS 4
+
+/* Undirected, unweighted graph without self loops as a symmetric CSR (host).
+ * Columns of each row must be strictly increasing.  A is 0/1 (Sec. 2). */
+typedef struct {
+    int64_t n;                  /* number of nodes N >= 1 */
+    const int64_t *rowptr;      /* host, n + 1 entries, rowptr[0] = 0 */
+    const int32_t *col;         /* host, rowptr[n] entries in [0, n) */
+} cia_graph;
+
+/* The model: f_m and g.  For CIA_MODEL_KURAMOTO,
+ *   f_m(theta) = omega_m,  g(x_l, x_m) = K h(x_l - x_m),
+ *   h(x) = sum_{k=1..p} d_sin[k-1] sin(kx) + d_cos[k-1] cos(kx)
+ * (the higher-harmonics Kuramoto model, App. A.4; p = 1, d_sin = {1},
+ * d_cos = {0} is the classical model). */
+typedef struct {
+    int model;                  /* cia_model */
+    int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
+    double d_sin[CIA_MAX_HARMONICS];
+    double d_cos[CIA_MAX_HARMONICS];
+    double K;                   /* coupling constant multiplying (1/N) sum */
+} cia_coupling;
+
+typedef struct {
+    int precision;              /* cia_precision */
+    int build_direct;           /* nonzero: also keep the full CSR on the device (CIA_METHOD_DIRECT) */
+    int tile_nodes;             /* nodes per work tile, 0 = default (256); a multiple of 32, <= 1024 */
+    int group_size;             /* threads per row of the direct method's CSR sums: 0 = default,
+                                   else 4, 8, 16 or 32 (the CIA sums use one thread per row) */
+    int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (24576); a multiple of 16.
+                                   A tile is cut at tile_nodes rows or at this many index bytes. */
+    int staging;                /* 0 = auto: TMA bulk copies of each tile's indices and community
+                                   phasors into shared memory when they fit; 1 = plain loads */
+} cia_options;
+
+typedef struct cia_plan cia_plan_t;
+
+/* Sizes of a plan (all counts, no pointers). */
+typedef struct {
+    int64_t n;                  /* nodes */
+    int64_t M;                  /* communities (labels 0..M-1) */
+    int64_t n_free;             /* nodes with label -1 (no community) */
+    int64_t max_community;      /* largest lambda_c */
+    int64_t nnz_graph;          /* entries of the input CSR (2 |E|) */
+    int64_t nnz_missing;        /* missing links inside blocks, off-diagonal, both directions */
+    int64_t nnz_inter;          /* links between different blocks (or touching free nodes), both directions */
+    int64_t n_tiles;            /* work tiles of the CIA kernels */
+    int64_t device_bytes;       /* device memory held by the plan */
+    int precision;
+    int group_size;
+    int tile_nodes;
+    int missing_index_bytes;    /* 2 (16-bit community-local index) or 4 */
+    int staging;                /* 0 = TMA bulk staging in use, 1 = plain loads */
+    int group_size_direct;      /* threads per row of the direct method */
+    int64_t max_tile_index_bytes; /* largest sparse-index footprint of a tile */
+} cia_plan_info;
+
+/* ---- status -------------------------------------------------------------- */
+
+/* Static string naming a status code. */
+const char *cia_status_string(cia_status s);
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next library call on this thread. */
+const char *cia_last_error(void);
+
+/* ---- planning: step P1 (Sec. 3.1, App. A.1), offline and untimed --------- */
+
+/* Build a plan for graph g with the given community labels.
+ *
+ * community: host, g->n entries; community[i] in [0, M) names the block of
+ *   node i, -1 puts node i in no community (allowed "for numerical reasons",
+ *   Sec. 3.1): all its links are then treated as sparse extra links.
+ *   Labels need not be contiguous in i; M = max label + 1 (empty labels allowed).
+ * omega: host, g->n natural frequencies f_m = omega_m (NULL = all zero).
+ *   With CIA_FP32 they are rounded to FP32.
+ * The plan computes the permutation kappa that sorts nodes by (label, id)
+ * with unlabelled nodes last, the community offsets, and the two halves of S:
+ *   missing links inside each block (the -1 entries of S without the
+ *   diagonal, which is handled analytically) and extra links (+1 entries).
+ * Validation: symmetric, no self loops, columns sorted, unique and in range;
+ * violations return CIA_ERR_INVALID_GRAPH and no plan.  NaN/Inf in omega or
+ * the coupling returns CIA_ERR_NUMERIC.
+ * On success *out owns device memory until cia_plan_destroy(*out). */
+cia_status cia_plan_create(const cia_graph *g, const int32_t *community, const double *omega,
+                           const cia_coupling *coupling, const cia_options *opt,
+                           cia_plan_t **out);
+
+/* Release everything the plan owns (NULL is a no-op). */
+cia_status cia_plan_destroy(cia_plan_t *plan);
+
+/* Fill *info with the plan's sizes. */
+cia_status cia_plan_get_info(const cia_plan_t *plan, cia_plan_info *info);
+
+/* Bookkeeping of step P1, copied to host arrays the caller allocated:
+ *   perm:   n entries, perm[m] = original id of permuted node m (kappa)
+ *   offsets: M + 1 entries, community c = permuted ids [offsets[c], offsets[c+1])
+ * Either pointer may be NULL. */
+cia_status cia_plan_get_permutation(const cia_plan_t *plan, int32_t *perm, int64_t *offsets);
+
+/* The sparse remainder S as two CSRs over PERMUTED ids (host arrays the
+ * caller allocated with sizes from cia_plan_info):
+ *   miss_rowptr[n+1], miss_col[nnz_missing]: the -1 entries of S except the
+ *     diagonal, columns ascending, as permuted global ids;
+ *   inter_rowptr[n+1], inter_col[nnz_inter]: the +1 entries, ascending.
+ * Any pointer may be NULL. */
+cia_status cia_plan_get_split(const cia_plan_t *plan, int64_t *miss_rowptr, int32_t *miss_col,
+                              int64_t *inter_rowptr, int32_t *inter_col);
+
+/* ---- evaluation: steps E1 + E2 (Sec. 3.2) --------------------------------- */
+
+/* One right-hand-side evaluation dxdt = H(x) with the CIA:
+ * (E1) per-community observables Z_{c,k} = sum_{l in c} e^{i k x_l} and the
+ * dense term from them (eq. FastHdense), (E2) the sparse sum over S, plus f.
+ * x, dxdt: device, n doubles each, original node order; they may not alias.
+ * With CIA_FP32 the state is rounded to FP32 and all sums run in FP32
+ * (per-community observables with FP64 accumulation across tiles). */
+cia_status cia_rhs(cia_plan_t *plan, const double *x, double *dxdt, void *stream);
+
+/* Same result by the direct sum over all CSR neighbours (needs
+ * opt.build_direct).  Same layout and precision rules as cia_rhs. */
+cia_status cia_rhs_direct(cia_plan_t *plan, const double *x, double *dxdt, void *stream);
+
+/* Advance x by nsteps classical RK4 steps of size dt (the paper allows any
+ * Runge-Kutta method, Sec. 3), evaluating every stage with `method`.
+ * x: device, n doubles, original order, in/out; returned wrapped to
+ *   [-pi, pi].  Time accumulation theta += dt sum_s b_s k_s is FP64 in both
+ *   precisions; stage states are in the plan's precision.
+ * r_out: device, nsteps doubles or NULL; r_out[j] = |(1/N) sum_l e^{i x_l}|
+ *   after step j+1 (the Kuramoto order parameter, eq. KuramotoFirstOP).
+ * nsteps = 0 only round-trips x through the wrap. */
+cia_status cia_integrate(cia_plan_t *plan, int method, double *x, double dt, int64_t nsteps,
+                         double *r_out, void *stream);
+
+/* cia_integrate with HOST buffers: copies x (n doubles) to the device, runs,
+ * copies x and, if r_out_host is not NULL, nsteps order parameters back, and
+ * synchronises the stream.  Pinned host memory makes the copies asynchronous. */
+cia_status cia_integrate_host(cia_plan_t *plan, int method, double *x_host, double dt,
+                              int64_t nsteps, double *r_out_host, void *stream);
+
+/* ---- resident state: the pieces cia_integrate is made of ------------------ */
+
+/* Load x (device, n doubles, original order) into the plan's resident FP64
+ * master state (permuted, wrapped to [-pi, pi]) and compute the observables
+ * of that state.  Until the next load the plan owns the state. */
+cia_status cia_state_load(cia_plan_t *plan, const double *x, void *stream);
+
+/* Copy the resident master state to x (device, n doubles, original order). */
+cia_status cia_state_store(cia_plan_t *plan, double *x, void *stream);
+
+/* Advance the resident state by nsteps RK4 steps of size dt (see
+ * cia_integrate for method and r_out).  One step is four stage launches; the
+ * state never leaves the device. */
+cia_status cia_advance(cia_plan_t *plan, int method, double dt, int64_t nsteps, double *r_out,
+                       void *stream);
+
+/* ---- profiling: CUDA events around every stage launch ---------------------- */
+
+typedef struct {
+    int64_t stage_launches;     /* stage kernels launched while profiling */
+    double stage_ms;            /* summed device time of those launches */
+    int64_t other_launches;     /* other kernels of the plan (observables, order parameter, I/O) */
+} cia_profile;
+
+/* Start recording: up to `capacity` stage launches get a CUDA event pair on
+ * the launching stream (capacity <= 0 stops recording).  Recording adds two
+ * event records per launch. */
+cia_status cia_profile_begin(cia_plan_t *plan, int64_t capacity);
+
+/* Stop recording, wait for the recorded events and return the totals. */
+cia_status cia_profile_end(cia_plan_t *plan, cia_profile *out);
+
+/* Wait for the plan's work on `stream` and report any asynchronous error.
+ * Returns CIA_ERR_TIMEOUT (and clears the flag) if a device-side wait of the
+ * plan's kernels gave up since the last cia_sync; results of that work are
+ * then invalid. */
+cia_status cia_sync(cia_plan_t *plan, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CIA_H */

@@ -1,0 +1,190 @@
+"""GB300-native community integration algorithm (CIA) for network ODEs.
+
+Python binding of libcia (include/cia.h): argument marshalling only.  Every
+step of the hot path runs in the library's CUDA kernels; there is no CPU or
+PyTorch fallback, and importing this package fails if libcia.so is missing.
+PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import CiaError, load
+
+__all__ = ["Plan", "CiaError", "load", "status_string"]
+
+
+def status_string(status: int) -> str:
+    return load().cia_status_string(int(status)).decode()
+
+
+def _stream_handle(stream=None) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype_name: str, n: int) -> ctypes.c_void_p:
+    import torch
+    want = getattr(torch, dtype_name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != want or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("expected a contiguous %s tensor of %d elements" % (dtype_name, n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A CIA plan: step P1 done once, then E1 + E2 on the device every call.
+
+    rowptr/col: symmetric CSR (host int64 / int32), labels: int32 community ids
+    (-1 = no community), omega: natural frequencies (host float64).
+    Coupling h(x) = sum_k d_sin[k] sin((k+1)x) + d_cos[k] cos((k+1)x), scaled by K/N.
+    """
+
+    def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
+                 precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
+                 tile_index_bytes=0, staging="auto"):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        n = len(rowptr) - 1
+        if len(labels) != n:
+            raise ValueError("labels must have n entries")
+        g = _abi.Graph(n, rowptr.ctypes.data, col.ctypes.data)
+        d_sin = list(d_sin)
+        d_cos = list(d_cos)
+        p = len(d_sin)
+        if len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS:
+            raise ValueError("d_sin and d_cos must have the same length in [1, %d]"
+                             % _abi.CIA_MAX_HARMONICS)
+        cp = _abi.Coupling()
+        cp.model = _abi.MODEL["kuramoto"]
+        cp.p = p
+        for k in range(p):
+            cp.d_sin[k] = float(d_sin[k])
+            cp.d_cos[k] = float(d_cos[k])
+        cp.K = float(K)
+        opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
+                           int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging])
+        om = None
+        if omega is not None:
+            om = np.ascontiguousarray(omega, dtype=np.float64)
+            if len(om) != n:
+                raise ValueError("omega must have n entries")
+        handle = ctypes.c_void_p()
+        _abi.check(lib.cia_plan_create(ctypes.byref(g), labels.ctypes.data,
+                                       om.ctypes.data if om is not None else None,
+                                       ctypes.byref(cp), ctypes.byref(opt), ctypes.byref(handle)))
+        self._h = handle
+        self.n = n
+        self.precision = precision
+
+    # ------------------------------------------------------------ bookkeeping
+    def info(self) -> dict:
+        inf = _abi.PlanInfo()
+        _abi.check(self._lib.cia_plan_get_info(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _abi.PlanInfo._fields_}
+
+    def permutation(self):
+        inf = self.info()
+        perm = np.empty(self.n, dtype=np.int32)
+        off = np.empty(inf["M"] + 1, dtype=np.int64)
+        _abi.check(self._lib.cia_plan_get_permutation(self._h, perm.ctypes.data, off.ctypes.data))
+        return perm, off
+
+    def split(self):
+        inf = self.info()
+        n = self.n
+        mrp = np.empty(n + 1, dtype=np.int64)
+        mcol = np.empty(max(1, inf["nnz_missing"]), dtype=np.int32)
+        irp = np.empty(n + 1, dtype=np.int64)
+        icol = np.empty(max(1, inf["nnz_inter"]), dtype=np.int32)
+        _abi.check(self._lib.cia_plan_get_split(self._h, mrp.ctypes.data, mcol.ctypes.data,
+                                                irp.ctypes.data, icol.ctypes.data))
+        return mrp, mcol[:inf["nnz_missing"]], irp, icol[:inf["nnz_inter"]]
+
+    # ------------------------------------------------------------ evaluation
+    def rhs(self, x, out=None, method="cia", stream=None):
+        """dx/dt for x (CUDA float64, original order); returns `out`."""
+        import torch
+        if out is None:
+            out = torch.empty_like(x)
+        fn = self._lib.cia_rhs if method == "cia" else self._lib.cia_rhs_direct
+        _abi.check(fn(self._h, _dev_ptr(x, "float64", self.n), _dev_ptr(out, "float64", self.n),
+                      _stream_handle(stream)))
+        return out
+
+    def integrate(self, x, dt, steps, method="cia", r_out=None, stream=None):
+        """Advance x (CUDA float64, original order) in place by `steps` RK4 steps."""
+        rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
+        _abi.check(self._lib.cia_integrate(self._h, _abi.METHOD[method],
+                                           _dev_ptr(x, "float64", self.n), float(dt), int(steps),
+                                           rp, _stream_handle(stream)))
+        return x
+
+    def integrate_host(self, x: np.ndarray, dt, steps, method="cia", r_out=None, stream=None):
+        """Host-buffer integration (copies inside the call); x is updated in place."""
+        if x.dtype != np.float64 or not x.flags.c_contiguous or len(x) != self.n:
+            raise ValueError("x must be a contiguous float64 array of n entries")
+        rp = None
+        if r_out is not None:
+            if r_out.dtype != np.float64 or len(r_out) != steps:
+                raise ValueError("r_out must be float64 with `steps` entries")
+            rp = r_out.ctypes.data
+        _abi.check(self._lib.cia_integrate_host(self._h, _abi.METHOD[method], x.ctypes.data,
+                                                float(dt), int(steps), rp,
+                                                _stream_handle(stream)))
+        return x
+
+    def state_load(self, x, stream=None):
+        """Make x (CUDA float64, original order) the resident state."""
+        _abi.check(self._lib.cia_state_load(self._h, _dev_ptr(x, "float64", self.n),
+                                            _stream_handle(stream)))
+
+    def state_store(self, x, stream=None):
+        """Copy the resident state into x (CUDA float64, original order)."""
+        _abi.check(self._lib.cia_state_store(self._h, _dev_ptr(x, "float64", self.n),
+                                             _stream_handle(stream)))
+        return x
+
+    def advance(self, dt, steps, method="cia", r_out=None, stream=None):
+        """Advance the resident state by `steps` RK4 steps."""
+        rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
+        _abi.check(self._lib.cia_advance(self._h, _abi.METHOD[method], float(dt), int(steps), rp,
+                                         _stream_handle(stream)))
+
+    def profile_begin(self, capacity: int):
+        _abi.check(self._lib.cia_profile_begin(self._h, int(capacity)))
+
+    def profile_end(self) -> dict:
+        pr = _abi.Profile()
+        _abi.check(self._lib.cia_profile_end(self._h, ctypes.byref(pr)))
+        return {"stage_launches": pr.stage_launches, "stage_ms": pr.stage_ms,
+                "other_launches": pr.other_launches}
+
+    def sync(self, stream=None):
+        _abi.check(self._lib.cia_sync(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cia_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,112 @@
+"""ctypes declarations of the libcia C ABI (include/cia.h).
+
+Argument marshalling only: every computation happens inside libcia.so.
+Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcia.so")
+
+CIA_MAX_HARMONICS = 4
+
+STATUS = {
+    0: "CIA_OK", 1: "CIA_ERR_INVALID_ARG", 2: "CIA_ERR_INVALID_GRAPH", 3: "CIA_ERR_UNSUPPORTED",
+    4: "CIA_ERR_CUDA", 5: "CIA_ERR_TIMEOUT", 6: "CIA_ERR_FALLBACK", 7: "CIA_ERR_NUMERIC",
+    8: "CIA_ERR_OOM",
+}
+PRECISION = {"fp64": 0, "fp32": 1}
+METHOD = {"cia": 0, "direct": 1}
+MODEL = {"kuramoto": 0}
+
+
+class CiaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.status_name = STATUS.get(status, "CIA_ERR_UNKNOWN")
+        super().__init__("%s: %s" % (self.status_name, message))
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class Coupling(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("p", ctypes.c_int),
+                ("d_sin", ctypes.c_double * CIA_MAX_HARMONICS),
+                ("d_cos", ctypes.c_double * CIA_MAX_HARMONICS),
+                ("K", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("build_direct", ctypes.c_int),
+                ("tile_nodes", ctypes.c_int), ("group_size", ctypes.c_int),
+                ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("M", ctypes.c_int64), ("n_free", ctypes.c_int64),
+                ("max_community", ctypes.c_int64), ("nnz_graph", ctypes.c_int64),
+                ("nnz_missing", ctypes.c_int64), ("nnz_inter", ctypes.c_int64),
+                ("n_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("precision", ctypes.c_int), ("group_size", ctypes.c_int),
+                ("tile_nodes", ctypes.c_int), ("missing_index_bytes", ctypes.c_int),
+                ("staging", ctypes.c_int), ("group_size_direct", ctypes.c_int),
+                ("max_tile_index_bytes", ctypes.c_int64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("stage_launches", ctypes.c_int64), ("stage_ms", ctypes.c_double),
+                ("other_launches", ctypes.c_int64)]
+
+
+# exported symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "cia_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cia_last_error": (ctypes.c_char_p, []),
+    "cia_plan_create": (ctypes.c_int, [ctypes.POINTER(Graph), _P, _P, ctypes.POINTER(Coupling),
+                                       ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "cia_plan_destroy": (ctypes.c_int, [_P]),
+    "cia_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
+    "cia_plan_get_permutation": (ctypes.c_int, [_P, _P, _P]),
+    "cia_plan_get_split": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "cia_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cia_rhs_direct": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cia_integrate": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int64, _P, _P]),
+    "cia_integrate_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int64,
+                                          _P, _P]),
+    "cia_sync": (ctypes.c_int, [_P, _P]),
+    "cia_state_load": (ctypes.c_int, [_P, _P, _P]),
+    "cia_state_store": (ctypes.c_int, [_P, _P, _P]),
+    "cia_advance": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _P, _P]),
+    "cia_profile_begin": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "cia_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libcia.so (built by paper_2203_16657_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libcia.so is not built (%s); run `python -m "
+                              "paper_2203_16657_gb300.build` -- there is no fallback" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != 0:
+        msg = load().cia_last_error().decode(errors="replace")
+        raise CiaError(status, msg)

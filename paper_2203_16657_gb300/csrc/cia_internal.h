@@ -1,0 +1,141 @@
+// Internal declarations of libcia: the plan object and the kernel launchers.
+// Not part of the public ABI (include/cia.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cia.h"
+
+namespace cia {
+
+// Thread-local error text behind cia_last_error().
+void set_error(const std::string &msg);
+void clear_error();
+cia_status cuda_fail(cudaError_t e, const char *what);
+
+#define CIA_CUDA_TRY(expr)                                                  \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) return ::cia::cuda_fail(_e, #expr);          \
+    } while (0)
+
+// Descriptor of one work tile (64 bytes, read by every CIA kernel).
+struct alignas(16) TileDesc {
+    int32_t comm, first, count, nsl;      // community (-1: unlabelled), first node, nodes, slices
+    uint32_t blob_bytes, mvec_off, ivec_off, lam;   // blob size; byte offsets of its vector sections
+    int64_t blob_off;                     // byte offset of the blob
+    int64_t lo;                           // first node of the community
+    int32_t run, pbuf, shift;             // community run inside the CTA's tile range, its buffer,
+                                          // lo - (lo rounded down to 16 bytes of phasors)
+    uint32_t vtab_off;                    // byte offset of the row -> chunk table
+};
+static_assert(sizeof(TileDesc) == 64, "tile descriptor is 64 bytes");
+
+// Device layout of one plan.  All node-indexed arrays are in PERMUTED order
+// (communities contiguous, unlabelled nodes last).
+struct DeviceBuffers {
+    // step P1 bookkeeping
+    int32_t *perm = nullptr;            // [n] permuted -> original id
+    int64_t *off = nullptr;             // [M+1]
+    // work tiles: a tile is a run of consecutive nodes of one community
+    int32_t *tile_comm = nullptr;       // [T] community id, -1 for unlabelled nodes
+    int32_t *tile_first = nullptr;      // [T] first permuted node
+    int32_t *tile_count = nullptr;      // [T] nodes in the tile
+    int32_t *comm_tile_begin = nullptr; // [M+1] tiles of community c: [begin[c], begin[c+1])
+    // S, split in its two signs, as sliced ELL: a slice is 32 rows of a tile
+    // (one per lane), rows ordered by decreasing list length; missing lists
+    // hold 16-bit community-local indices (sentinel lambda_c), inter lists
+    // 32-bit permuted ids (sentinel n); vector j of lane r sits at
+    // slice_offset + 32 j + r.  Each tile is one contiguous blob:
+    //   [slice descriptors: nsl x uint4 (miss offset, miss vectors, inter offset, inter vectors)]
+    //   [row maps: nsl x 32 x u32 (lane -> missing chunk | inter row << 16, 0xffff = none)]
+    //   [row -> chunk table: count x u32 (first chunk | chunks << 16), padded to 16 bytes]
+    //   [missing vectors over chunks: 8 x u16][inter vectors over rows: 4 x i32]
+    // A missing list longer than 64 entries is split into chunks whose
+    // partial sums are added per row in chunk order.
+    cia::TileDesc *tile_desc = nullptr; // [T]
+    unsigned char *blob = nullptr;      // [sum of blob bytes]
+    int32_t *cta_tile_begin = nullptr;  // [n_ctas+1] tile range of each persistent CTA
+    int32_t *cta_runs = nullptr;        // [n_ctas] community runs (maximal same-community tile runs) per CTA
+    // full permuted CSR for the direct method (optional), rows padded to
+    // whole 4 x i32 vectors with the sentinel n
+    int64_t *full_rowptr = nullptr;     // [n+1]
+    int32_t *full_col = nullptr;        // [padded nnz]
+    // model
+    void *omega = nullptr;              // [n] compute precision
+    // work buffers
+    double *theta = nullptr;            // [n] FP64 master state
+    void *acc = nullptr;                // [n] sum_s b_s C_s, compute precision
+    void *ph[2] = {nullptr, nullptr};   // [p][n] complex phasors e^{i k y}, compute precision
+    double *part[2] = {nullptr, nullptr}; // [T][p] complex tile sums (FP64)
+    void *wdt_half = nullptr;           // [n] wrap(dt omega / 2), compute precision
+    void *wdt_full = nullptr;           // [n] wrap(dt omega), compute precision
+    double *wdt_full64 = nullptr;       // [n] wrap(dt omega), FP64
+    double *rhs_tmp = nullptr;          // [n] staging for host-buffer calls
+    double *x_tmp = nullptr;            // [n] staging for host-buffer calls
+    int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up
+    double *r_tmp = nullptr;            // [r_cap] staging for order parameters
+    int64_t r_cap = 0;
+};
+
+}  // namespace cia
+
+struct cia_plan {
+    int device = 0;
+    int64_t n = 0, M = 0, n_free = 0, max_comm = 0;
+    int64_t nnz_graph = 0, nnz_missing = 0, nnz_inter = 0, n_tiles = 0;
+    int64_t device_bytes = 0;
+    int precision = CIA_FP64;
+    int model = CIA_MODEL_KURAMOTO;
+    int p = 1;
+    double d_sin[CIA_MAX_HARMONICS] = {0};
+    double d_cos[CIA_MAX_HARMONICS] = {0};
+    double K = 0.0;
+    int tile_nodes = 256;
+    int group_size = 8;                 // threads per row, CIA sparse sums
+    int group_size_direct = 32;         // threads per row, direct sums
+    int miss_idx_bytes = 2;
+    int has_direct = 0;
+    int64_t ph_stride = 0;              // phasor entries per harmonic: n + 1 rounded up to even
+    int tile_index_bytes = 24576;
+    int64_t max_tile_idx_bytes = 0;     // largest index footprint of one tile (bytes)
+    int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0;
+    int n_ctas = 0;                     // persistent grid of the pipelined CIA kernel (one per SM)
+    int ring_stages = 0;                // tile buffers of its TMA ring
+    int staging = 0;                    // 0 = persistent TMA pipeline, 1 = plain loads
+    double dt_cached = 0.0;             // dt the wdt_* buffers were computed for
+    bool wdt_valid = false;
+    std::vector<int32_t> perm;          // host copy of kappa
+    std::vector<int64_t> off;           // host copy of the offsets
+    cia::DeviceBuffers d;
+    std::vector<void *> allocations;    // everything to cudaFree
+    // profiling (cia_profile_begin / cia_profile_end)
+    bool prof_on = false;
+    int64_t prof_cap = 0, prof_used = 0, prof_other = 0;
+    std::vector<cudaEvent_t> prof_ev;   // 2 per recorded launch
+    int state_slot = 0;                 // phasor/partial slot holding the resident state
+};
+
+namespace cia {
+
+// Kernel launchers (kuramoto.cu).  All return cudaGetLastError() of the launch.
+struct Method {
+    enum { CIA = 0, DIRECT = 1 };
+};
+
+cudaError_t launch_phasors_from_x(cia_plan *pl, const double *x, bool write_master, int ph_slot,
+                                  cudaStream_t s);
+cudaError_t launch_rhs(cia_plan *pl, int method, int ph_slot, double *dxdt, cudaStream_t s);
+cudaError_t launch_omega_constants(cia_plan *pl, double dt, cudaStream_t s);
+cudaError_t launch_rk4_stage(cia_plan *pl, int method, int stage, int ph_in_slot, double dt,
+                             cudaStream_t s);
+cudaError_t launch_order_parameter(cia_plan *pl, int ph_slot, double *r_out, cudaStream_t s);
+cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
+size_t stage_smem_bytes(const cia_plan *pl, int method);
+size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
+
+}  // namespace cia

@@ -1,0 +1,1169 @@
+// Device kernels of the Kuramoto CIA hot path (sm_103a).
+//
+// Model (App. A.4): theta_m' = omega_m + (K/N) sum_l a_ml h(theta_l - theta_m),
+//   h(x) = sum_{k=1..p} d_sin_k sin(kx) + d_cos_k cos(kx).
+// With phasors u_{l,k} = e^{i k theta_l} the pair sum separates (Sec. 3.2):
+//   sum_l a_ml h(theta_l - theta_m)
+//     = sum_k d_sin_k Im(W_mk conj(u_mk)) + d_cos_k Re(W_mk conj(u_mk)),
+//   W_mk = sum_l a_ml u_lk.
+// CIA (steps E1 + E2): for m in community c,
+//   W_mk = Z_ck - u_mk - sum_{l in miss(m)} u_lk + sum_{l in inter(m)} u_lk,
+// where Z_ck = sum_{l in c} u_lk is the community observable
+// (eq. PrecomputeQuantities up to the 1/N factor), u_mk removes the diagonal
+// of the block (a_mm = 0), miss(m) are the -1 entries of S and inter(m) the +1
+// entries.  The direct method sums W_mk over all CSR neighbours.
+//
+// One launch per RK4 stage.  A CTA owns a tile of consecutive nodes of one
+// community: it (1) reduces the community's tile partial sums into Z_c,
+// (2) stages the community's phasors in shared memory so that the missing-link
+// gathers are shared-memory reads, (3) evaluates the coupling C_m of each node
+// of the tile with `group` threads per row, (4) applies the RK4 stage update,
+// computes the phasors of the next stage state and (5) writes its tile's
+// partial sums of those phasors, which the next launch reduces into Z.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cia_internal.h"
+
+namespace cia {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxChunks = 512;    // missing-list chunks per tile (partial sums in shared memory)
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ void sincos_t(float y, float *s, float *c) { sincosf(y, s, c); }
+__device__ __forceinline__ void sincos_t(double y, double *s, double *c) { sincos(y, s, c); }
+
+// Representative of y in R / 2 pi Z within [-pi, pi] (FP64).
+__device__ __forceinline__ double wrap_pi(double y) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double inv_two_pi = 0.15915494309189533576888376337251;
+    return y - two_pi * rint(y * inv_two_pi);
+}
+
+// Phasors e^{i k y}, k = 1..P, by repeated multiplication of e^{i y}.
+template <typename T, int P>
+__device__ __forceinline__ void phasors(T y, typename Vec2<T>::type (&u)[P]) {
+    T s, c;
+    sincos_t(y, &s, &c);
+    u[0] = mk2(c, s);
+#pragma unroll
+    for (int k = 1; k < P; ++k)
+        u[k] = mk2(u[k - 1].x * c - u[k - 1].y * s, u[k - 1].x * s + u[k - 1].y * c);
+}
+
+// ---- Blackwell bulk-copy (TMA) and mbarrier primitives, inline PTX ---------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy completing on `bar`; dst, src and bytes are
+// multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Barrier 1 among the first `count` threads (the consumer warps).
+__device__ __forceinline__ void consumer_sync(int count) {
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+// Barrier 1 among the first `count` threads that also returns the OR of
+// every participant's `pred`: a decision all of them receive identically.
+__device__ __forceinline__ bool consumer_sync_or(int count, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;     // 2 s: far beyond any healthy copy
+
+enum Mode { kRhs = 0, kStage = 1, kFinal = 2 };
+
+// Shared-memory phasor entries per harmonic for TMA staging: lambda_max + 1
+// plus up to one entry on each side from rounding the window to 16 bytes.
+int64_t tma_ph_region(const cia_plan *pl) { return (pl->max_comm + 4) & ~(int64_t)1; }
+
+template <typename T>
+struct StageParams {
+    using C = typename Vec2<T>::type;
+    int64_t n;
+    int64_t ph_stride;         // phasor entries per harmonic (>= n + 1; slot n is a zero phasor)
+    int group;                 // threads per row of the direct method: 4, 8, 16 or 32
+    int tile_nodes;
+    T d_sin[CIA_MAX_HARMONICS], d_cos[CIA_MAX_HARMONICS];
+    T k_over_n;                // K / N
+    const int64_t *off;
+    const int32_t *tile_comm, *tile_first, *tile_count, *comm_tile_begin;
+    // CIA: sliced-ELL sparse remainder, one blob per tile
+    const TileDesc *tile_desc;
+    const unsigned char *blob;
+    // direct: padded full CSR
+    const int64_t *sp_rowptr;
+    const int32_t *sp_col;
+    const C *ph_in;            // [P][ph_stride] phasors of the stage state
+    C *ph_out;                 // [P][ph_stride] phasors of the next stage state
+    const double *part_in;     // [tiles][P] complex tile sums of ph_in
+    double *part_out;          // [tiles][P] complex tile sums of ph_out
+    // kRhs
+    const T *omega;
+    const int32_t *perm;
+    double *rhs_out;
+    // kStage / kFinal
+    T *acc;                    // sum_s b_s C_s
+    double *theta;             // FP64 master
+    const T *wdt_next;         // wrap(c_{s+1} dt omega)
+    const double *wdt64;       // wrap(dt omega) (kFinal)
+    T c_next_dt;               // c_{s+1} dt
+    T b_s;                     // RK4 weight of this stage
+    double dt;
+    int first_stage;
+    // TMA staging
+    int ph_region;             // shared-memory phasor entries per harmonic
+    int idx_cap;               // shared-memory index buffer bytes
+    int *err_flag;             // set when a bounded wait gives up
+    int stages;                // ring buffers of the pipelined kernel
+    int max_cta_tiles;         // most tiles of one persistent CTA
+    const int32_t *cta_tile_begin;
+    const int32_t *cta_runs;   // community runs in each CTA's tile range
+};
+
+// Sum of per-thread values over the block, returned to thread 0..2P-1 as
+// doubles: each warp reduces by a shuffle tree, then thread j adds the warps.
+template <typename T, int P>
+__device__ __forceinline__ void block_tile_sum(T (&re)[P], T (&im)[P], double (*red)[2 * P],
+                                               double *dst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re[k] += __shfl_xor_sync(0xffffffffu, re[k], o);
+            im[k] += __shfl_xor_sync(0xffffffffu, im[k], o);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            red[warp][2 * k] = (double)re[k];
+            red[warp][2 * k + 1] = (double)im[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * P) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+}
+
+// Phase B, one thread per node of the tile: coupling from the sparse sums
+// sW (plus the dense term Z - u_m for community nodes), RK4 stage update,
+// phasors of the next stage state and the tile's partial sums of them.
+// own(k, m) returns u_{m,k}.
+template <typename T, int P, int MODE, typename Own>
+__device__ __forceinline__ void finalize_tile(const StageParams<T> &a, int t, int first, int count,
+                                              bool dense, const typename Vec2<T>::type *zc,
+                                              const typename Vec2<T>::type *sW, double (*red)[2 * P],
+                                              Own own) {
+    using C = typename Vec2<T>::type;
+    const int64_t stride = a.ph_stride;
+    T sre[P], sim[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
+    for (int r = threadIdx.x; r < count; r += kThreads) {
+        const int64_t m = first + r;
+        T coup = T(0);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const C u = own(k, m);
+            const C wv = sW[k * a.tile_nodes + r];
+            T zr = wv.x, zi = wv.y;
+            if (dense) {
+                // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
+                zr += zc[k].x - u.x;
+                zi += zc[k].y - u.y;
+            }
+            // W conj(u_m): real part -> cosine harmonics, imaginary part -> sine
+            const T re = zr * u.x + zi * u.y;
+            const T im = zi * u.x - zr * u.y;
+            coup += a.d_sin[k] * im + a.d_cos[k] * re;
+        }
+        coup *= a.k_over_n;
+        if (MODE == kRhs) {
+            a.rhs_out[a.perm[m]] = (double)a.omega[m] + (double)coup;
+        } else {
+            const T accv = (a.first_stage ? T(0) : a.acc[m]) + a.b_s * coup;
+            T y;
+            if (MODE == kStage) {
+                a.acc[m] = accv;
+                y = (T)a.theta[m] + a.wdt_next[m] + a.c_next_dt * coup;
+            } else {
+                // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
+                const double th = wrap_pi(a.theta[m] + a.wdt64[m] + a.dt * (double)accv);
+                a.theta[m] = th;
+                y = (T)th;
+            }
+            C u[P];
+            phasors<T, P>(y, u);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                a.ph_out[k * stride + m] = u[k];
+                sre[k] += u[k].x;
+                sim[k] += u[k].y;
+            }
+        }
+    }
+    if (MODE == kRhs) return;
+    block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
+}
+
+// (E1.1) community observable Z_ck = sum over the community's tiles of their
+// partial sums, by warp 0: lane j adds tiles j, j + 32, ... in FP64, then a
+// fixed shuffle tree combines the lanes (deterministic order).
+template <typename T, int P>
+__device__ __forceinline__ void community_observable(const StageParams<T> &a, int comm,
+                                                     typename Vec2<T>::type *zc) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int u0 = a.comm_tile_begin[comm], u1 = a.comm_tile_begin[comm + 1];
+    double re[P], im[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) re[k] = im[k] = 0.0;
+    for (int u = u0 + lane; u < u1; u += 32) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(a.part_in) + (int64_t)u * P + k);
+            re[k] += v.x;
+            im[k] += v.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re[k] += __shfl_xor_sync(0xffffffffu, re[k], o);
+            im[k] += __shfl_xor_sync(0xffffffffu, im[k], o);
+        }
+        if (lane == 0) zc[k] = mk2((T)re[k], (T)im[k]);
+    }
+}
+
+// CIA stage with plain loads, one CTA per tile (fallback when the pipelined
+// kernel's shared-memory ring does not fit).  Phase A: one warp per slice,
+// one lane per row, no cross-lane reduction -- first the missing links (-1
+// entries of S, gathered from the community's phasors), then the
+// inter-community links (+1 entries).  Phase B: one thread per node.
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(kThreads) cia_stage_kernel(const StageParams<T> a) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ C zc[P];
+    __shared__ double red[kWarps][2 * P];
+
+    const int t = blockIdx.x;
+    const TileDesc d = a.tile_desc[t];
+    const int64_t stride = a.ph_stride;
+    const bool dense = d.comm >= 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lam = (int)d.lam;
+    if (dense) community_observable<T, P>(a, d.comm, zc);
+    C *sWm = reinterpret_cast<C *>(smem_raw);           // [P][kMaxChunks] chunk sums
+    C *sWi = sWm + P * kMaxChunks;                      // [P][tile_nodes] inter sums
+    const C *cph = a.ph_in + d.lo;
+    const unsigned char *b = a.blob + d.blob_off;
+    const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
+    const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
+    const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
+    const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
+
+    for (int s = warp; s < d.nsl; s += kWarps) {
+        const uint4 sd = __ldg(sdesc + s);
+        const uint32_t rows = __ldg(srows + s * 32 + lane);
+        const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+        T mre[P], mim[P], ire[P], iim[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) mre[k] = mim[k] = ire[k] = iim[k] = T(0);
+        const uint4 *mv = mvec + sd.x + lane;
+#pragma unroll 2
+        for (uint32_t j = 0; j < sd.y; ++j) {
+            const uint4 q = __ldg(mv + 32 * j);
+            const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int l0 = (int)(w4[h] & 0xffffu), l1 = (int)(w4[h] >> 16);
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const C v0 = l0 < lam ? __ldg(cph + k * stride + l0) : mk2(T(0), T(0));
+                    const C v1 = l1 < lam ? __ldg(cph + k * stride + l1) : mk2(T(0), T(0));
+                    mre[k] -= v0.x + v1.x;
+                    mim[k] -= v0.y + v1.y;
+                }
+            }
+        }
+        const int4 *iv = ivec + sd.z + lane;
+#pragma unroll 2
+        for (uint32_t j = 0; j < sd.w; ++j) {
+            const int4 q = __ldg(iv + 32 * j);
+            const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const C u = __ldg(a.ph_in + k * stride + l4[h]);
+                    ire[k] += u.x;
+                    iim[k] += u.y;
+                }
+            }
+        }
+        if (mrow != 0xffffu) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) sWm[k * kMaxChunks + mrow] = mk2(mre[k], mim[k]);
+        }
+        if (irow != 0xffffu) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) sWi[k * a.tile_nodes + irow] = mk2(ire[k], iim[k]);
+        }
+    }
+    __syncthreads();
+    // per row: its chunk sums in chunk order plus its inter sum, then Phase B
+    const uint32_t *vtab = reinterpret_cast<const uint32_t *>(b + d.vtab_off);
+    for (int r = threadIdx.x; r < d.count; r += kThreads) {
+        const uint32_t vt = __ldg(vtab + r);
+        const int c0 = (int)(vt & 0xffffu), nc = (int)(vt >> 16);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            C w = sWi[k * a.tile_nodes + r];
+            for (int c = c0; c < c0 + nc; ++c) {
+                const C v = sWm[k * kMaxChunks + c];
+                w.x += v.x;
+                w.y += v.y;
+            }
+            sWi[k * a.tile_nodes + r] = w;
+        }
+    }
+    __syncthreads();
+    finalize_tile<T, P, MODE>(a, t, d.first, d.count, dense, zc, sWi, red,
+                              [&](int k, int64_t m) { return __ldg(a.ph_in + k * stride + m); });
+}
+
+// ---- persistent, warp-specialised CIA stage (the main path) ----------------
+//
+// One CTA per SM walks a contiguous range of tiles.  The last warp is the
+// producer: its lane 0 copies, with TMA bulk copies, each tile's sliced-ELL
+// index vectors into a ring of `stages` shared-memory buffers (mbarrier
+// full/empty pairs) and the phasors of each new community into one of two
+// community buffers (pfull/pempty), running ahead of the consumers.  Two
+// consumer groups of eight warps take alternate tiles (ping-pong), so one
+// group's latency-bound phase overlaps the other's.  Per tile a group runs
+// Phase A (warp per slice, lane per row: inter-community gathers issued
+// first, then the shared-memory gathers of the missing links; separate sum
+// arrays, so no barrier between them) and Phase B (thread per node).  Every
+// wait is bounded; a wait that gives up sets the plan's error flag and all
+// warps leave once the copies already issued have landed.
+
+constexpr int kConsumerWarps = 8;                 // per group
+constexpr int kConsumers = 32 * kConsumerWarps;   // threads per group = max tile rows
+constexpr int kGroups = 2;
+constexpr int kPipeThreads = kGroups * kConsumers + 32;
+constexpr int kMaxStages = 4;
+
+
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const StageParams<T> a) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t pfull_bar[2], pempty_bar[kGroups][2], desc_bar;
+    __shared__ C zbuf[2][P];               // community observable of each community buffer
+    __shared__ double red[kGroups][kConsumerWarps][2 * P];
+    __shared__ volatile int s_prod_abort, s_cons_abort;
+
+    const int S = a.stages;
+    const int tb = a.cta_tile_begin[blockIdx.x], te = a.cta_tile_begin[blockIdx.x + 1];
+    // shared memory: tile descriptors | ring of tile blobs | 2 community windows | W sums
+    TileDesc *sdesc = reinterpret_cast<TileDesc *>(smem_raw);               // [max_cta_tiles]
+    unsigned char *ring = smem_raw + (size_t)a.max_cta_tiles * sizeof(TileDesc);   // [S][idx_cap]
+    C *pbuf = reinterpret_cast<C *>(ring + (size_t)S * a.idx_cap);         // [2][P][ph_region]
+    C *sWall = pbuf + 2 * P * a.ph_region;                                 // [groups][2][P][kConsumers]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = a.ph_stride;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], kConsumerWarps);
+        }
+        for (int b = 0; b < 2; ++b) {
+            // two arrivals: the phasor copy (with its bytes) and "Z written"
+            mbar_init(&pfull_bar[b], 2);
+            for (int g = 0; g < kGroups; ++g) mbar_init(&pempty_bar[g][b], kConsumerWarps);
+        }
+        mbar_init(&desc_bar, 1);
+        s_prod_abort = 0;
+        s_cons_abort = 0;
+        // this CTA's tile descriptors, one bulk copy
+        const uint32_t dbytes = (uint32_t)((te - tb) * sizeof(TileDesc));
+        mbar_arrive_expect_tx(&desc_bar, dbytes);
+        if (dbytes) bulk_g2s(sdesc, a.tile_desc + tb, dbytes, &desc_bar);
+    }
+    __syncthreads();
+    {
+        bool fail = false;
+        if (threadIdx.x == 0) {
+            fail = !mbar_wait_bounded(&desc_bar, 0, kWaitLimitNs);
+            if (fail) {
+                atomicExch(a.err_flag, 1);
+                mbar_wait_bounded(&desc_bar, 0, kWaitLimitNs / 2);
+            }
+        }
+        if (__syncthreads_or(fail)) return;
+    }
+
+    if (warp == kGroups * kConsumerWarps) {
+        // ------------------------------------------------------------ producer
+        // lane 0 waits and issues the copies; the whole warp reduces the
+        // community observable of every new run while the copies fly
+        int issued = 0, last_pload = -1;
+        for (int i = tb; i < te; ++i) {
+            const int li = i - tb, s = li % S, k = li / S;
+            const TileDesc &d = sdesc[li];
+            const bool dense = d.comm >= 0;
+            const bool new_run = dense && (li == 0 || sdesc[li - 1].run != d.run);
+            int ok = 1;
+            if (lane == 0) {
+                if (s_cons_abort) ok = 0;
+                else if (k >= 1) ok = mbar_wait_bounded(&empty_bar[s], (k - 1) & 1, kWaitLimitNs);
+                if (!ok && !s_cons_abort) {
+                    atomicExch(a.err_flag, 1);
+                    s_prod_abort = 1;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (new_run) {
+                const int run = d.run, b = run & 1;
+                if (lane == 0) {
+                    // every group releases run - 2 of this buffer before it is reused
+                    for (int g = 0; g < kGroups && ok && run >= 2; ++g)
+                        ok = mbar_wait_bounded(&pempty_bar[g][b], ((run >> 1) - 1) & 1, kWaitLimitNs);
+                    if (!ok) {
+                        atomicExch(a.err_flag, 1);
+                        s_prod_abort = 1;
+                    } else {
+                        constexpr int64_t per16 = 16 / (int64_t)sizeof(C);
+                        const int64_t pstart = d.lo - d.shift;
+                        const int64_t pend = (d.lo + d.lam + 1 + per16 - 1) & ~(per16 - 1);
+                        const uint32_t pbytes = (uint32_t)((pend - pstart) * (int64_t)sizeof(C));
+                        mbar_arrive_expect_tx(&pfull_bar[b], P * pbytes);
+                        for (int kk = 0; kk < P; ++kk)
+                            bulk_g2s(pbuf + (b * P + kk) * a.ph_region, a.ph_in + kk * stride + pstart, pbytes,
+                                     &pfull_bar[b]);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+                // (E1.1) community observable: lane j adds tiles j, j + 32, ...
+                // in FP64, then a fixed shuffle tree (deterministic order)
+                const int u0 = a.comm_tile_begin[d.comm], u1 = a.comm_tile_begin[d.comm + 1];
+                double re[P], im[P];
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) re[kk] = im[kk] = 0.0;
+                for (int u = u0 + lane; u < u1; u += 32) {
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk) {
+                        const double2 v = __ldg(reinterpret_cast<const double2 *>(a.part_in) + (int64_t)u * P + kk);
+                        re[kk] += v.x;
+                        im[kk] += v.y;
+                    }
+                }
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        re[kk] += __shfl_xor_sync(0xffffffffu, re[kk], o);
+                        im[kk] += __shfl_xor_sync(0xffffffffu, im[kk], o);
+                    }
+                    if (lane == 0) zbuf[b][kk] = mk2((T)re[kk], (T)im[kk]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pfull_bar[b]);   // Z is written (release)
+                last_pload = run;
+            }
+            if (lane == 0) {
+                unsigned char *slot = ring + (size_t)s * a.idx_cap;
+                mbar_arrive_expect_tx(&full_bar[s], d.blob_bytes);
+                if (d.blob_bytes) bulk_g2s(slot, a.blob + d.blob_off, d.blob_bytes, &full_bar[s]);
+            }
+            ++issued;
+        }
+        // let every copy this warp issued land before the CTA can retire
+        if (lane == 0) {
+            for (int li = (issued > S ? issued - S : 0); li < issued; ++li)
+                mbar_wait_bounded(&full_bar[li % S], (li / S) & 1, kWaitLimitNs);
+            for (int r = (last_pload > 0 ? last_pload - 1 : 0); r <= last_pload; ++r)
+                mbar_wait_bounded(&pfull_bar[r & 1], (r >> 1) & 1, kWaitLimitNs);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int grp = warp / kConsumerWarps;                 // 0 or 1
+    const int gw = warp % kConsumerWarps;                  // warp within the group
+    const int gt = threadIdx.x - grp * kConsumers;         // thread within the group
+    C *sWm = sWall + (size_t)grp * P * (kMaxChunks + kConsumers);   // [P][kMaxChunks] chunk sums
+    C *sWi = sWm + P * kMaxChunks;                                    // [P][kConsumers] inter sums
+    int released = -1;                                     // last run this group released
+    const int nruns = a.cta_runs[blockIdx.x];              // community runs of this CTA
+    auto gsync_or = [&](bool pred) {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\t"
+            "setp.ne.u32 p, %1, 0;\n\t"
+            "bar.red.or.pred q, %2, %3, p;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)pred), "r"(1 + grp), "r"(kConsumers)
+            : "memory");
+        return r != 0;
+    };
+    auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(kConsumers) : "memory"); };
+    // release of a community buffer: once per run, in run order, as soon as
+    // the group knows it has no further tile of that run (from the tile
+    // descriptors, never from the producer, which may itself be waiting for
+    // this release).  A run is released only after its own phasor load has
+    // landed: that load was issued after the producer saw the release of
+    // run - 2, so a buffer's pempty barrier never runs two phases ahead of
+    // its waiter.
+    auto release_through = [&](int run_upto) {
+        for (int r = released + 1; r <= run_upto; ++r) {
+            if (gt % 32 == 0 && !s_cons_abort && !s_prod_abort) {
+                if (mbar_wait_bounded(&pfull_bar[r & 1], (r >> 1) & 1, kWaitLimitNs)) {
+                    mbar_arrive(&pempty_bar[grp][r & 1]);
+                } else {
+                    atomicExch(a.err_flag, 1);
+                    s_cons_abort = 1;
+                }
+            }
+        }
+        if (run_upto > released) released = run_upto;
+    };
+    // runs that end before the group's first tile
+    {
+        const int i0 = tb + grp;
+        release_through((i0 >= te || sdesc[i0 - tb].comm < 0) ? nruns - 1 : sdesc[i0 - tb].run - 1);
+    }
+
+    for (int i = tb + grp; i < te; i += kGroups) {
+        const int li = i - tb, s = li % S, k = li / S;
+        const unsigned char *slot = ring + (size_t)s * a.idx_cap;
+        const TileDesc h = sdesc[li];
+        const bool dense = h.comm >= 0;
+        bool fail = false;
+        if (gt == 0) {
+            fail = s_prod_abort || !mbar_wait_bounded(&full_bar[s], k & 1, kWaitLimitNs);
+            if (fail) {
+                atomicExch(a.err_flag, 1);
+                s_cons_abort = 1;
+            }
+        }
+        if (gsync_or(fail)) break;
+        if (dense) {
+            bool pfail = false;
+            if (gt == 0) {
+                pfail = !mbar_wait_bounded(&pfull_bar[h.pbuf], (h.run >> 1) & 1, kWaitLimitNs);
+                if (pfail) {
+                    atomicExch(a.err_flag, 1);
+                    s_cons_abort = 1;
+                } else {
+                    // the slot after the community is where padding entries point: zero it
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk)
+                        pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam] = mk2(T(0), T(0));
+                }
+            }
+            if (gsync_or(pfail)) break;
+        }
+        const C *cph = pbuf + (size_t)h.pbuf * P * a.ph_region + h.shift;   // cph[k * ph_region + l]
+        const uint4 *sdsl = reinterpret_cast<const uint4 *>(slot);
+        const uint32_t *srows = reinterpret_cast<const uint32_t *>(slot + 16 * h.nsl);
+        const uint4 *mvec = reinterpret_cast<const uint4 *>(slot + h.mvec_off);
+        const int4 *ivec = reinterpret_cast<const int4 *>(slot + h.ivec_off);
+
+        // Phase B inputs of this thread's node, loaded now, used after Phase A
+        const int r = gt;
+        const int64_t m = h.first + r;
+        const bool live = r < h.count;
+        // this row's chunks, read before the ring buffer is released
+        const uint32_t vt = live ? reinterpret_cast<const uint32_t *>(slot + h.vtab_off)[r] : 0u;
+        double theta_m = 0.0, wdt64_m = 0.0;
+        T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
+        int32_t perm_m = 0;
+        if (live) {
+            if (MODE == kRhs) {
+                omega_m = a.omega[m];
+                perm_m = a.perm[m];
+            } else {
+                theta_m = a.theta[m];
+                if (!a.first_stage) acc_m = a.acc[m];
+                if (MODE == kStage) wdt_m = a.wdt_next[m];
+                else wdt64_m = a.wdt64[m];
+            }
+        }
+
+        // Phase A: per slice, inter-community gathers (global) issued first,
+        // then the missing links from the community buffer (shared)
+        for (int sl = gw; sl < h.nsl; sl += kConsumerWarps) {
+            const uint4 d = sdsl[sl];
+            const uint32_t rows = srows[sl * 32 + lane];
+            const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+            T ire[P], iim[P], mre[P], mim[P];
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) ire[kk] = iim[kk] = mre[kk] = mim[kk] = T(0);
+            const int4 *iv = ivec + d.z + lane;
+            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 4 : 1;   // vectors gathered ahead
+            C pre[kPre][4][P];
+            const uint32_t npre = d.w < kPre ? d.w : kPre;
+#pragma unroll
+            for (uint32_t j = 0; j < kPre; ++j) {
+                if (j < npre) {
+                    const int4 q = iv[32 * j];
+                    const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                        for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
+                }
+            }
+            const uint4 *mv = mvec + d.x + lane;
+#pragma unroll 2
+            for (uint32_t j = 0; j < d.y; ++j) {
+                const uint4 q = mv[32 * j];
+                const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) {
+                    const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk) {
+                        const C v0 = cph[kk * a.ph_region + l0];
+                        const C v1 = cph[kk * a.ph_region + l1];
+                        mre[kk] -= v0.x + v1.x;
+                        mim[kk] -= v0.y + v1.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kPre; ++j) {
+                if (j < npre) {
+#pragma unroll
+                    for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                        for (int kk = 0; kk < P; ++kk) {
+                            ire[kk] += pre[j][hh][kk].x;
+                            iim[kk] += pre[j][hh][kk].y;
+                        }
+                }
+            }
+            // longer inter lists: further batches of kPre vectors, loads first
+            for (uint32_t j0 = kPre; j0 < d.w; j0 += kPre) {
+#pragma unroll
+                for (uint32_t j = 0; j < kPre; ++j) {
+                    if (j0 + j < d.w) {
+                        const int4 q = iv[32 * (j0 + j)];
+                        const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                            for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
+                    }
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < kPre; ++j) {
+                    if (j0 + j < d.w) {
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                            for (int kk = 0; kk < P; ++kk) {
+                                ire[kk] += pre[j][hh][kk].x;
+                                iim[kk] += pre[j][hh][kk].y;
+                            }
+                    }
+                }
+            }
+            if (mrow != 0xffffu) {
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) sWm[kk * kMaxChunks + mrow] = mk2(mre[kk], mim[kk]);
+            }
+            if (irow != 0xffffu) {
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) sWi[kk * kConsumers + irow] = mk2(ire[kk], iim[kk]);
+            }
+        }
+        gsync();
+        if (lane == 0) mbar_arrive(&empty_bar[s]);           // the ring buffer is free again
+
+        // Phase B: one thread per node
+        T sre[P], sim[P];
+#pragma unroll
+        for (int kk = 0; kk < P; ++kk) sre[kk] = sim[kk] = T(0);
+        if (live) {
+            T coup = T(0);
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) {
+                const C u = dense ? cph[kk * a.ph_region + (int)(m - h.lo)] : __ldg(a.ph_in + kk * stride + m);
+                const C wi = sWi[kk * kConsumers + r];
+                T zr = wi.x, zi = wi.y;
+                for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
+                    const C wm = sWm[kk * kMaxChunks + c];
+                    zr += wm.x;
+                    zi += wm.y;
+                }
+                if (dense) {
+                    // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
+                    zr += zbuf[h.pbuf][kk].x - u.x;
+                    zi += zbuf[h.pbuf][kk].y - u.y;
+                }
+                const T re = zr * u.x + zi * u.y;
+                const T im = zi * u.x - zr * u.y;
+                coup += a.d_sin[kk] * im + a.d_cos[kk] * re;
+            }
+            coup *= a.k_over_n;
+            if (MODE == kRhs) {
+                a.rhs_out[perm_m] = (double)omega_m + (double)coup;
+            } else {
+                const T accv = acc_m + a.b_s * coup;
+                T y;
+                if (MODE == kStage) {
+                    a.acc[m] = accv;
+                    y = (T)theta_m + wdt_m + a.c_next_dt * coup;
+                } else {
+                    // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
+                    const double th = wrap_pi(theta_m + wdt64_m + a.dt * (double)accv);
+                    a.theta[m] = th;
+                    y = (T)th;
+                }
+                C u[P];
+                phasors<T, P>(y, u);
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) {
+                    a.ph_out[kk * stride + m] = u[kk];
+                    sre[kk] = u[kk].x;
+                    sim[kk] = u[kk].y;
+                }
+            }
+        }
+        if (MODE != kRhs) {
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sre[kk] += __shfl_xor_sync(0xffffffffu, sre[kk], o);
+                    sim[kk] += __shfl_xor_sync(0xffffffffu, sim[kk], o);
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) {
+                    red[grp][gw][2 * kk] = (double)sre[kk];
+                    red[grp][gw][2 * kk + 1] = (double)sim[kk];
+                }
+            }
+        }
+        gsync();                                             // Phase B done
+        if (MODE != kRhs && gt < 2 * P) {
+            double sum = 0.0;
+            for (int w = 0; w < kConsumerWarps; ++w) sum += red[grp][w][gt];
+            a.part_out[(size_t)i * P * 2 + gt] = sum;
+        }
+        // release every run before the run of this group's next tile
+        {
+            const int ni = i + kGroups;
+            release_through((!dense || ni >= te || sdesc[ni - tb].comm < 0) ? nruns - 1 : sdesc[ni - tb].run - 1);
+        }
+    }
+    // every run of this CTA is finished for this group
+    release_through(nruns - 1);
+}
+
+// Direct method: every CSR neighbour gathered from global memory, `group`
+// threads per row over 16-byte index vectors, then Phase B (no dense term).
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(kThreads) direct_stage_kernel(const StageParams<T> a) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[kWarps][2 * P];
+    const int t = blockIdx.x;
+    const int first = a.tile_first[t];
+    const int count = a.tile_count[t];
+    const int64_t stride = a.ph_stride;
+    C *sW = reinterpret_cast<C *>(smem_raw);            // [P][tile_nodes]
+    const int G = a.group;
+    const int lane = threadIdx.x & (G - 1);
+    const int grp = threadIdx.x / G;
+    const int ngrp = kThreads / G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    for (int r = grp; r < count; r += ngrp) {
+        const int64_t m = first + r;
+        T wre[P], wim[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) wre[k] = wim[k] = T(0);
+        const int4 *sv = reinterpret_cast<const int4 *>(a.sp_col + a.sp_rowptr[m]);
+        const int nv = (int)((a.sp_rowptr[m + 1] - a.sp_rowptr[m]) >> 2);
+#pragma unroll 2
+        for (int v = lane; v < nv; v += G) {
+            const int4 q = __ldg(sv + v);
+            const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const C u = __ldg(a.ph_in + k * stride + l4[h]);
+                    wre[k] += u.x;
+                    wim[k] += u.y;
+                }
+            }
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                wre[k] += __shfl_xor_sync(gmask, wre[k], o);
+                wim[k] += __shfl_xor_sync(gmask, wim[k], o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) sW[k * a.tile_nodes + r] = mk2(wre[k], wim[k]);
+        }
+    }
+    __syncthreads();
+    finalize_tile<T, P, MODE>(a, t, first, count, false, (const C *)nullptr, sW, red,
+                              [&](int k, int64_t m) { return __ldg(a.ph_in + k * stride + m); });
+}
+
+// Phasors (and tile sums) of a state given in original order; optionally
+// stores the wrapped FP64 master in permuted order.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+phasor_kernel(int64_t n, int64_t stride, const int32_t *perm, const int32_t *tile_first,
+              const int32_t *tile_count, const double *x, double *theta, typename Vec2<T>::type *ph_out,
+              double *part_out) {
+    using C = typename Vec2<T>::type;
+    __shared__ double red[kWarps][2 * P];
+    const int t = blockIdx.x;
+    const int first = tile_first[t], count = tile_count[t];
+    T sre[P], sim[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
+    for (int r = threadIdx.x; r < count; r += kThreads) {
+        const int64_t m = first + r;
+        const double y = wrap_pi(x[perm[m]]);
+        if (theta) theta[m] = y;
+        C u[P];
+        phasors<T, P>((T)y, u);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            ph_out[k * stride + m] = u[k];
+            sre[k] += u[k].x;
+            sim[k] += u[k].y;
+        }
+    }
+    block_tile_sum<T, P>(sre, sim, red, part_out + (size_t)t * P * 2);
+}
+
+// Per-node constants of one time step: wrap(dt omega / 2), wrap(dt omega).
+template <typename T>
+__global__ void omega_constants_kernel(int64_t n, const T *omega, double dt, T *wh, T *wf, double *wf64) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+        const double w = (double)omega[m];
+        const double h = wrap_pi(0.5 * dt * w), f = wrap_pi(dt * w);
+        wh[m] = (T)h;
+        wf[m] = (T)f;
+        wf64[m] = f;
+    }
+}
+
+// r = |sum over all tiles of the first-harmonic tile sums| / N.
+template <int P>
+__global__ void order_parameter_kernel(int64_t n, int64_t tiles, const double *part, double *r_out) {
+    __shared__ double sre[kThreads], sim[kThreads];
+    double re = 0.0, im = 0.0;
+    for (int64_t t = threadIdx.x; t < tiles; t += kThreads) {
+        re += part[t * P * 2];
+        im += part[t * P * 2 + 1];
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sre[threadIdx.x] += sre[threadIdx.x + s];
+            sim[threadIdx.x] += sim[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *r_out = sqrt(sre[0] * sre[0] + sim[0] * sim[0]) / (double)n;
+}
+
+__global__ void scatter_master_kernel(int64_t n, const int32_t *perm, const double *theta, double *x) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x)
+        x[perm[m]] = theta[m];
+}
+
+template <typename T>
+StageParams<T> base_params(cia_plan *pl, int method) {
+    StageParams<T> a{};
+    a.n = pl->n;
+    a.ph_stride = pl->ph_stride;
+    a.group = pl->group_size_direct;
+    a.tile_nodes = pl->tile_nodes;
+    for (int k = 0; k < CIA_MAX_HARMONICS; ++k) {
+        a.d_sin[k] = (T)pl->d_sin[k];
+        a.d_cos[k] = (T)pl->d_cos[k];
+    }
+    a.k_over_n = (T)(pl->K / (double)pl->n);
+    a.off = pl->d.off;
+    a.tile_comm = pl->d.tile_comm;
+    a.tile_first = pl->d.tile_first;
+    a.tile_count = pl->d.tile_count;
+    a.comm_tile_begin = pl->d.comm_tile_begin;
+    a.tile_desc = pl->d.tile_desc;
+    a.blob = pl->d.blob;
+    a.sp_rowptr = pl->d.full_rowptr;
+    a.sp_col = pl->d.full_col;
+    a.omega = (const T *)pl->d.omega;
+    a.perm = pl->d.perm;
+    a.acc = (T *)pl->d.acc;
+    a.theta = pl->d.theta;
+    a.wdt64 = pl->d.wdt_full64;
+    a.ph_region = (int)tma_ph_region(pl);
+    a.idx_cap = (int)((pl->max_tile_idx_bytes + 15) & ~(int64_t)15);
+    a.err_flag = pl->d.err_flag;
+    a.stages = pl->ring_stages;
+    a.max_cta_tiles = (int)pl->max_cta_tiles;
+    a.cta_tile_begin = pl->d.cta_tile_begin;
+    a.cta_runs = pl->d.cta_runs;
+    (void)method;
+    return a;
+}
+
+template <typename K>
+cudaError_t launch_kernel(K kernel, size_t &configured, int64_t blocks, size_t smem, const void *params,
+                          cudaStream_t s) {
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    void *args[] = {const_cast<void *>(params)};
+    return cudaLaunchKernel((const void *)kernel, dim3((unsigned)blocks), dim3(kThreads), args, smem, s);
+}
+
+template <typename T, int P, int MODE>
+cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream_t s) {
+    if (pl->staging == 0) {
+        auto kernel = cia_pipeline_kernel<T, P, MODE>;
+        static size_t cfg = 0;
+        const size_t smem = pipeline_smem_bytes(pl, pl->ring_stages);
+        if (smem > 48 * 1024 && smem > cfg) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            cfg = smem;
+        }
+        void *args[] = {const_cast<StageParams<T> *>(&a)};
+        return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_ctas), dim3(kPipeThreads), args, smem, s);
+    }
+    static size_t cfg = 0;
+    return launch_kernel(cia_stage_kernel<T, P, MODE>, cfg, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
+}
+
+template <typename T, int P, int MODE>
+cudaError_t launch_direct_t(const cia_plan *pl, const StageParams<T> &a, cudaStream_t s) {
+    static size_t cfg = 0;
+    return launch_kernel(direct_stage_kernel<T, P, MODE>, cfg, pl->n_tiles, stage_smem_bytes(pl, Method::DIRECT),
+                         &a, s);
+}
+
+template <typename T, int MODE>
+cudaError_t dispatch_stage(cia_plan *pl, int method, const StageParams<T> &a, cudaStream_t s) {
+    const bool direct = method == Method::DIRECT;
+#define CIA_CASE(P)                                                                   \
+    case P:                                                                           \
+        return direct ? launch_direct_t<T, P, MODE>(pl, a, s) : launch_cia_t<T, P, MODE>(pl, a, s);
+    switch (pl->p) {
+        CIA_CASE(1)
+        CIA_CASE(2)
+        CIA_CASE(3)
+        CIA_CASE(4)
+    }
+#undef CIA_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t phasors_t(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
+    using C = typename Vec2<T>::type;
+    double *theta = write_master ? pl->d.theta : nullptr;
+    C *ph = (C *)pl->d.ph[slot];
+    double *part = pl->d.part[slot];
+    const unsigned g = (unsigned)pl->n_tiles;
+    switch (pl->p) {
+        case 1: phasor_kernel<T, 1><<<g, kThreads, 0, s>>>(pl->n, pl->ph_stride, pl->d.perm, pl->d.tile_first, pl->d.tile_count, x, theta, ph, part); break;
+        case 2: phasor_kernel<T, 2><<<g, kThreads, 0, s>>>(pl->n, pl->ph_stride, pl->d.perm, pl->d.tile_first, pl->d.tile_count, x, theta, ph, part); break;
+        case 3: phasor_kernel<T, 3><<<g, kThreads, 0, s>>>(pl->n, pl->ph_stride, pl->d.perm, pl->d.tile_first, pl->d.tile_count, x, theta, ph, part); break;
+        case 4: phasor_kernel<T, 4><<<g, kThreads, 0, s>>>(pl->n, pl->ph_stride, pl->d.perm, pl->d.tile_first, pl->d.tile_count, x, theta, ph, part); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rhs_t(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s) {
+    using C = typename Vec2<T>::type;
+    StageParams<T> a = base_params<T>(pl, method);
+    a.ph_in = (const C *)pl->d.ph[slot];
+    a.part_in = pl->d.part[slot];
+    a.rhs_out = dxdt;
+    return dispatch_stage<T, kRhs>(pl, method, a, s);
+}
+
+template <typename T>
+cudaError_t stage_t(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s) {
+    using C = typename Vec2<T>::type;
+    // classical RK4: nodes c = (0, 1/2, 1/2, 1), weights b = (1/6, 1/3, 1/3, 1/6)
+    static const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    static const double c_next[4] = {0.5, 0.5, 1.0, 0.0};
+    StageParams<T> a = base_params<T>(pl, method);
+    a.ph_in = (const C *)pl->d.ph[slot];
+    a.ph_out = (C *)pl->d.ph[slot ^ 1];
+    a.part_in = pl->d.part[slot];
+    a.part_out = pl->d.part[slot ^ 1];
+    a.b_s = (T)b[stage - 1];
+    a.c_next_dt = (T)(c_next[stage - 1] * dt);
+    a.wdt_next = (const T *)(stage == 3 ? pl->d.wdt_full : pl->d.wdt_half);
+    a.dt = dt;
+    a.first_stage = stage == 1;
+    return stage == 4 ? dispatch_stage<T, kFinal>(pl, method, a, s) : dispatch_stage<T, kStage>(pl, method, a, s);
+}
+
+}  // namespace
+
+// Dynamic shared memory of the plain-load CIA kernel and of the direct
+// kernel: the W sums of one tile.
+size_t stage_smem_bytes(const cia_plan *pl, int method) {
+    const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
+    return method == Method::DIRECT ? cb * (size_t)pl->tile_nodes : cb * (size_t)(kMaxChunks + pl->tile_nodes);
+}
+
+// Dynamic shared memory of the pipelined CIA kernel: a ring of tile buffers
+// (64-byte header + index vectors), two community phasor windows, W sums.
+size_t pipeline_smem_bytes(const cia_plan *pl, int stages) {
+    const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
+    const size_t idx_cap = (size_t)((pl->max_tile_idx_bytes + 15) & ~(int64_t)15);
+    return (size_t)pl->max_cta_tiles * sizeof(TileDesc) + (size_t)stages * idx_cap +
+           2 * cb * (size_t)tma_ph_region(pl) + (size_t)kGroups * cb * (size_t)(kMaxChunks + kConsumers);
+}
+
+cudaError_t launch_phasors_from_x(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
+    return pl->precision == CIA_FP64 ? phasors_t<double>(pl, x, write_master, slot, s)
+                                     : phasors_t<float>(pl, x, write_master, slot, s);
+}
+
+cudaError_t launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s) {
+    return pl->precision == CIA_FP64 ? rhs_t<double>(pl, method, slot, dxdt, s)
+                                     : rhs_t<float>(pl, method, slot, dxdt, s);
+}
+
+cudaError_t launch_rk4_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s) {
+    return pl->precision == CIA_FP64 ? stage_t<double>(pl, method, stage, slot, dt, s)
+                                     : stage_t<float>(pl, method, stage, slot, dt, s);
+}
+
+cudaError_t launch_omega_constants(cia_plan *pl, double dt, cudaStream_t s) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((pl->n + 255) / 256, 152 * 8);
+    if (pl->precision == CIA_FP64)
+        omega_constants_kernel<double><<<blocks, 256, 0, s>>>(pl->n, (const double *)pl->d.omega, dt,
+                                                             (double *)pl->d.wdt_half, (double *)pl->d.wdt_full,
+                                                             pl->d.wdt_full64);
+    else
+        omega_constants_kernel<float><<<blocks, 256, 0, s>>>(pl->n, (const float *)pl->d.omega, dt,
+                                                            (float *)pl->d.wdt_half, (float *)pl->d.wdt_full,
+                                                            pl->d.wdt_full64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_parameter(cia_plan *pl, int slot, double *r_out, cudaStream_t s) {
+    switch (pl->p) {
+        case 1: order_parameter_kernel<1><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
+        case 2: order_parameter_kernel<2><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
+        case 3: order_parameter_kernel<3><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
+        case 4: order_parameter_kernel<4><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((pl->n + 255) / 256, 152 * 8);
+    scatter_master_kernel<<<blocks, 256, 0, s>>>(pl->n, pl->d.perm, pl->d.theta, x);
+    return cudaGetLastError();
+}
+
+}  // namespace cia

@@ -1,0 +1,765 @@
+// Host planner of libcia: step P1 of the CIA (Sec. 3.1 and App. A.1).
+//
+// Given the symmetric 0/1 adjacency A (CSR) and community labels, the plan
+//  - validates A (symmetric, no self loops, sorted unique in-range columns),
+//  - builds the permutation kappa sorting nodes by (label, original id) with
+//    unlabelled nodes (label -1, "no community") last, so that B = P A P^T has
+//    the communities as consecutive diagonal blocks,
+//  - records the block sizes lambda_c as offsets (the dense part D is never
+//    stored, Sec. 3.1),
+//  - splits the sparse remainder S = B - D into its -1 entries (links missing
+//    inside a block; the diagonal is handled analytically by the kernels) and
+//    its +1 entries (links between blocks), each as a CSR over permuted ids,
+//  - cuts every community into work tiles of at most tile_nodes nodes,
+//  - uploads everything and allocates the device work buffers.
+// The planner is offline and untimed; it runs row-parallel with OpenMP.
+#include <omp.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cia_internal.h"
+
+namespace cia {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+cia_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? CIA_ERR_OOM : CIA_ERR_CUDA;
+}
+
+static cia_status fail(cia_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+// Validate the CSR: bounds, ordering, self loops, then symmetry in O(nnz):
+// rows are visited in increasing order, so the entries (j, i) with i < j of
+// row j are met in increasing i; a cursor per row checks they appear exactly
+// in that order, and at the end every entry below the diagonal was matched.
+static cia_status validate_graph(const cia_graph *g) {
+    const int64_t n = g->n;
+    if (g->rowptr[0] != 0) return fail(CIA_ERR_INVALID_GRAPH, "rowptr[0] != 0");
+    for (int64_t i = 0; i < n; ++i)
+        if (g->rowptr[i + 1] < g->rowptr[i])
+            return fail(CIA_ERR_INVALID_GRAPH, "rowptr decreases at row " + std::to_string(i));
+    int64_t bad_row = -1;
+    std::string why;
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t prev = -1;
+        for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) {
+            int32_t j = g->col[e];
+            const char *w = nullptr;
+            if (j < 0 || j >= n) w = "column out of range";
+            else if (j == i) w = "self loop";
+            else if (j <= prev) w = "columns not strictly increasing";
+            if (w) {
+#pragma omp critical
+                {
+                    if (bad_row < 0 || i < bad_row) { bad_row = i; why = w; }
+                }
+                break;
+            }
+            prev = j;
+        }
+    }
+    if (bad_row >= 0) return fail(CIA_ERR_INVALID_GRAPH, why + " in row " + std::to_string(bad_row));
+    std::vector<int64_t> cursor(g->rowptr, g->rowptr + n);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) {
+            int64_t j = g->col[e];
+            if (j <= i) continue;
+            int64_t &cj = cursor[j];
+            if (cj >= g->rowptr[j + 1] || g->col[cj] != i)
+                return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(i) + "->" +
+                                                       std::to_string(j) + " has no reverse");
+            ++cj;
+        }
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t c = cursor[j];
+        if (c < g->rowptr[j + 1] && g->col[c] < j)
+            return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(j) + "->" +
+                                                   std::to_string(g->col[c]) + " has no reverse");
+    }
+    return CIA_OK;
+}
+
+template <typename T>
+static cia_status upload(cia_plan *pl, T **dst, const T *src, size_t count) {
+    size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+    void *p = nullptr;
+    CIA_CUDA_TRY(cudaMalloc(&p, bytes));
+    pl->allocations.push_back(p);
+    pl->device_bytes += (int64_t)bytes;
+    if (src && count) CIA_CUDA_TRY(cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    else CIA_CUDA_TRY(cudaMemset(p, 0, bytes));
+    *dst = (T *)p;
+    return CIA_OK;
+}
+
+static cia_status alloc_bytes(cia_plan *pl, void **dst, size_t bytes) {
+    return upload<unsigned char>(pl, (unsigned char **)dst, nullptr, bytes);
+}
+
+static void free_all(cia_plan *pl) {
+    for (void *p : pl->allocations) cudaFree(p);
+    pl->allocations.clear();
+    for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
+    pl->prof_ev.clear();
+    if (pl->d.r_tmp) cudaFree(pl->d.r_tmp);
+    pl->d.r_tmp = nullptr;
+    pl->d.r_cap = 0;
+}
+
+}  // namespace cia
+
+using namespace cia;
+
+extern "C" const char *cia_status_string(cia_status s) {
+    switch (s) {
+        case CIA_OK: return "CIA_OK";
+        case CIA_ERR_INVALID_ARG: return "CIA_ERR_INVALID_ARG";
+        case CIA_ERR_INVALID_GRAPH: return "CIA_ERR_INVALID_GRAPH";
+        case CIA_ERR_UNSUPPORTED: return "CIA_ERR_UNSUPPORTED";
+        case CIA_ERR_CUDA: return "CIA_ERR_CUDA";
+        case CIA_ERR_TIMEOUT: return "CIA_ERR_TIMEOUT";
+        case CIA_ERR_FALLBACK: return "CIA_ERR_FALLBACK";
+        case CIA_ERR_NUMERIC: return "CIA_ERR_NUMERIC";
+        case CIA_ERR_OOM: return "CIA_ERR_OOM";
+    }
+    return "CIA_ERR_UNKNOWN";
+}
+
+extern "C" const char *cia_last_error(void) { return g_last_error.c_str(); }
+
+// Longest missing-link chunk of one lane: longer lists are split into
+// chunks ("virtual rows") whose partial sums Phase B adds in a fixed order.
+static const int64_t kChunk = 64;
+// Most chunks per tile (shared-memory partial sums of one consumer group).
+static const int64_t kMaxChunks = 512;
+
+// Scratch of schedule_missing (one per planning thread).
+struct MissScheduler {
+    std::vector<int32_t> bucket[32][16];   // remaining entries of each lane by bank pair
+};
+
+// Fill the missing-link vectors of one slice (32 lanes, nvm vectors of 8
+// entries each).  Lane l sums the entries ent[l][0..len[l]); their order is
+// free, so it is chosen such that at every entry position the live lanes of
+// each half-warp use distinct shared-memory bank pairs (community-local index
+// mod 16) whenever their remaining entries allow -- the gathers of one step
+// are then free of bank conflicts.  Lanes with fewer remaining entries pick
+// first, each taking an unused bank pair from its largest bucket.
+static void schedule_missing(const int32_t *const ent[32], const int64_t len[32], int64_t nvm,
+                             uint16_t sentinel, uint16_t *out, MissScheduler &sc) {
+    int remaining[32];
+    for (int lane = 0; lane < 32; ++lane) {
+        for (auto &b : sc.bucket[lane]) b.clear();
+        for (int64_t e = 0; e < len[lane]; ++e) sc.bucket[lane][ent[lane][e] & 15].push_back(ent[lane][e]);
+        remaining[lane] = (int)len[lane];
+    }
+    for (int64_t pos = 0; pos < 8 * nvm; ++pos) {
+        const int64_t j = pos / 8, h = pos % 8;
+        for (int half = 0; half < 2; ++half) {
+            int order[16];
+            for (int q = 0; q < 16; ++q) order[q] = 16 * half + q;
+            std::stable_sort(order, order + 16, [&](int x, int y) { return remaining[x] < remaining[y]; });
+            unsigned used = 0;
+            for (int q = 0; q < 16; ++q) {
+                const int lane = order[q];
+                uint16_t v = sentinel;
+                if (remaining[lane] > 0) {
+                    int best = -1;
+                    for (int pass = 0; pass < 2 && best < 0; ++pass)
+                        for (int c = 0; c < 16; ++c) {
+                            if (sc.bucket[lane][c].empty() || (pass == 0 && (used >> c & 1u))) continue;
+                            if (best < 0 || sc.bucket[lane][c].size() > sc.bucket[lane][best].size()) best = c;
+                        }
+                    v = (uint16_t)sc.bucket[lane][best].back();
+                    sc.bucket[lane][best].pop_back();
+                    --remaining[lane];
+                    used |= 1u << best;
+                }
+                out[8 * (32 * j + lane) + h] = v;
+            }
+        }
+    }
+}
+
+// One tile's blob (see cia::DeviceBuffers): slice descriptors, row maps, the
+// row -> chunk table, missing vectors over chunks, inter vectors over rows.
+struct TileBlob {
+    std::vector<unsigned char> bytes;
+    int32_t nsl = 0;
+    uint32_t vtab_off = 0, mvec_off = 0, ivec_off = 0;
+};
+
+static int64_t chunks_of(int64_t entries) { return std::max<int64_t>(1, (entries + kChunk - 1) / kChunk); }
+
+static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inter_sent,
+                            const std::vector<int64_t> &miss_cnt, const std::vector<int64_t> &miss_off,
+                            const std::vector<int32_t> &miss_local, const std::vector<int64_t> &inter_cnt,
+                            const std::vector<int64_t> &inter_off, const std::vector<int32_t> &inter_col,
+                            TileBlob &tb, MissScheduler &sc) {
+    // chunks: row r's missing list in v_r nearly equal contiguous pieces,
+    // numbered vbase_r .. vbase_r + v_r - 1
+    struct Chunk { int32_t row, vidx; int64_t e0, len; };
+    std::vector<Chunk> ch;
+    std::vector<uint32_t> vtab(cnt);
+    for (int64_t r = 0; r < cnt; ++r) {
+        const int64_t E = miss_cnt[f + r], v = chunks_of(E);
+        vtab[r] = (uint32_t)ch.size() | ((uint32_t)v << 16);
+        int64_t e = 0;
+        for (int64_t c = 0; c < v; ++c) {
+            const int64_t len = E / v + (c < E % v ? 1 : 0);
+            ch.push_back({(int32_t)r, (int32_t)ch.size(), e, len});
+            e += len;
+        }
+    }
+    const int64_t V = (int64_t)ch.size();
+    std::vector<int32_t> mo(V), io(cnt);
+    for (int64_t q = 0; q < V; ++q) mo[q] = (int32_t)q;
+    for (int64_t r = 0; r < cnt; ++r) io[r] = (int32_t)r;
+    std::stable_sort(mo.begin(), mo.end(), [&](int32_t x, int32_t y) { return ch[x].len > ch[y].len; });
+    std::stable_sort(io.begin(), io.end(), [&](int32_t x, int32_t y) { return inter_cnt[f + x] > inter_cnt[f + y]; });
+    const int64_t nsm = (V + 31) / 32, nsi = (cnt + 31) / 32, nsl = std::max(nsm, nsi);
+    std::vector<int64_t> nvm(nsl, 0), nvi(nsl, 0);
+    int64_t mv = 0, iv = 0;
+    for (int64_t s = 0; s < nsl; ++s) {
+        if (s < nsm) nvm[s] = (ch[mo[32 * s]].len + 7) / 8;
+        if (s < nsi) nvi[s] = (inter_cnt[f + io[32 * s]] + 3) / 4;
+        mv += 32 * nvm[s];
+        iv += 32 * nvi[s];
+    }
+    tb.nsl = (int32_t)nsl;
+    tb.vtab_off = (uint32_t)(144 * nsl);
+    tb.mvec_off = tb.vtab_off + (uint32_t)((4 * cnt + 15) & ~(int64_t)15);
+    tb.ivec_off = tb.mvec_off + (uint32_t)(16 * mv);
+    tb.bytes.assign(tb.ivec_off + 16 * iv, 0);
+    uint32_t *desc = reinterpret_cast<uint32_t *>(tb.bytes.data());
+    uint32_t *rows = reinterpret_cast<uint32_t *>(tb.bytes.data() + 16 * nsl);
+    std::memcpy(tb.bytes.data() + tb.vtab_off, vtab.data(), 4 * cnt);
+    uint16_t *mvec = reinterpret_cast<uint16_t *>(tb.bytes.data() + tb.mvec_off);
+    int32_t *ivec = reinterpret_cast<int32_t *>(tb.bytes.data() + tb.ivec_off);
+    mv = iv = 0;
+    for (int64_t s = 0; s < nsl; ++s) {
+        desc[4 * s + 0] = (uint32_t)mv;
+        desc[4 * s + 1] = (uint32_t)nvm[s];
+        desc[4 * s + 2] = (uint32_t)iv;
+        desc[4 * s + 3] = (uint32_t)nvi[s];
+        const int32_t *ent[32];
+        int64_t len[32];
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t ms = 32 * s + lane;
+            const bool mlive = ms < V, ilive = ms < cnt;
+            const Chunk *c = mlive ? &ch[mo[ms]] : nullptr;
+            ent[lane] = mlive ? miss_local.data() + miss_off[f + c->row] + c->e0 : nullptr;
+            len[lane] = mlive ? c->len : 0;
+            const int32_t ir = ilive ? io[ms] : -1;
+            rows[32 * s + lane] = (uint32_t)(mlive ? c->vidx : 0xffff) | ((uint32_t)(ilive ? ir : 0xffff) << 16);
+            for (int64_t j = 0; j < nvi[s]; ++j)
+                for (int h = 0; h < 4; ++h) {
+                    const int64_t e = 4 * j + h;
+                    const bool has = ilive && e < inter_cnt[f + ir];
+                    ivec[4 * (iv + 32 * j + lane) + h] = has ? inter_col[inter_off[f + ir] + e] : inter_sent;
+                }
+        }
+        schedule_missing(ent, len, nvm[s], msent, mvec + 8 * mv, sc);
+        mv += 32 * nvm[s];
+        iv += 32 * nvi[s];
+    }
+}
+
+static cia_status build_plan(const cia_graph *g, const int32_t *community, const double *omega,
+                             const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
+    const int64_t n = g->n;
+    // ---- options and model
+    pl->precision = opt ? opt->precision : CIA_FP64;
+    if (pl->precision != CIA_FP64 && pl->precision != CIA_FP32)
+        return fail(CIA_ERR_INVALID_ARG, "unknown precision");
+    pl->has_direct = opt ? (opt->build_direct != 0) : 0;
+    pl->tile_nodes = (opt && opt->tile_nodes) ? opt->tile_nodes : 256;
+    if (pl->tile_nodes < 32 || pl->tile_nodes > 1024 || pl->tile_nodes % 32)
+        return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024]");
+    pl->tile_index_bytes = (opt && opt->tile_index_bytes) ? opt->tile_index_bytes : 24576;
+    if (pl->tile_index_bytes < 256 || pl->tile_index_bytes % 16)
+        return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
+    pl->staging = opt ? opt->staging : 0;
+    if (pl->staging != 0 && pl->staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
+    if (cp->model != CIA_MODEL_KURAMOTO) return fail(CIA_ERR_UNSUPPORTED, "unknown model");
+    if (cp->p < 1 || cp->p > CIA_MAX_HARMONICS)
+        return fail(CIA_ERR_INVALID_ARG, "p must be in [1, CIA_MAX_HARMONICS]");
+    pl->model = cp->model;
+    pl->p = cp->p;
+    pl->K = cp->K;
+    if (!std::isfinite(cp->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
+    for (int k = 0; k < cp->p; ++k) {
+        if (!std::isfinite(cp->d_sin[k]) || !std::isfinite(cp->d_cos[k]))
+            return fail(CIA_ERR_NUMERIC, "coupling coefficient is not finite");
+        pl->d_sin[k] = cp->d_sin[k];
+        pl->d_cos[k] = cp->d_cos[k];
+    }
+    if (omega)
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(omega[i]))
+                return fail(CIA_ERR_NUMERIC, "omega[" + std::to_string(i) + "] is not finite");
+
+    // ---- validate A
+    cia_status st = validate_graph(g);
+    if (st != CIA_OK) return st;
+    pl->n = n;
+    pl->nnz_graph = g->rowptr[n];
+    pl->ph_stride = (n + 2) & ~(int64_t)1;
+
+    // ---- labels, kappa (stable counting sort by label, unlabelled last)
+    int64_t M = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (community[i] < -1)
+            return fail(CIA_ERR_INVALID_ARG, "community label below -1 at node " + std::to_string(i));
+        M = std::max<int64_t>(M, (int64_t)community[i] + 1);
+    }
+    pl->M = M;
+    std::vector<int64_t> cnt(M + 2, 0);
+    for (int64_t i = 0; i < n; ++i) cnt[(community[i] < 0 ? M : community[i]) + 1]++;
+    for (int64_t c = 0; c <= M; ++c) cnt[c + 1] += cnt[c];
+    pl->off.assign(cnt.begin(), cnt.begin() + M + 1);
+    pl->n_free = n - pl->off[M];
+    pl->perm.assign(n, 0);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < n; ++i) pl->perm[pos[community[i] < 0 ? M : community[i]]++] = (int32_t)i;
+    }
+    std::vector<int32_t> iperm(n);
+    for (int64_t m = 0; m < n; ++m) iperm[pl->perm[m]] = (int32_t)m;
+    pl->max_comm = 0;
+    for (int64_t c = 0; c < M; ++c) pl->max_comm = std::max(pl->max_comm, pl->off[c + 1] - pl->off[c]);
+    pl->miss_idx_bytes = pl->max_comm <= 65535 ? 2 : 4;
+    std::vector<int32_t> comm_of(n, -1);
+    for (int64_t c = 0; c < M; ++c)
+        for (int64_t m = pl->off[c]; m < pl->off[c + 1]; ++m) comm_of[m] = (int32_t)c;
+
+    // ---- pass 1: per-row counts of missing and inter links
+    std::vector<int64_t> miss_cnt(n, 0), inter_cnt(n, 0);
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t m = 0; m < n; ++m) {
+        int32_t i = pl->perm[m];
+        int32_t c = comm_of[m];
+        int64_t inside = 0, deg = g->rowptr[i + 1] - g->rowptr[i];
+        if (c >= 0) {
+            int64_t lo = pl->off[c], hi = pl->off[c + 1];
+            for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) {
+                int64_t pm = iperm[g->col[e]];
+                inside += (pm >= lo && pm < hi);
+            }
+            miss_cnt[m] = (hi - lo - 1) - inside;
+        }
+        inter_cnt[m] = deg - inside;
+    }
+    auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
+    auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
+    std::vector<int64_t> miss_off(n + 1, 0), inter_off(n + 1, 0), full_rp;
+    for (int64_t m = 0; m < n; ++m) {
+        miss_off[m + 1] = miss_off[m] + miss_cnt[m];
+        inter_off[m + 1] = inter_off[m] + inter_cnt[m];
+    }
+    pl->nnz_missing = miss_off[n];
+    pl->nnz_inter = inter_off[n];
+    if (pl->has_direct) {
+        full_rp.assign(n + 1, 0);
+        for (int64_t m = 0; m < n; ++m) {
+            int32_t i = pl->perm[m];
+            full_rp[m + 1] = full_rp[m] + pad4(g->rowptr[i + 1] - g->rowptr[i]);
+        }
+    }
+
+    // ---- pass 2: the lists themselves (missing as community-local indices),
+    // ascending within each row
+    std::vector<int32_t> miss_local(miss_off[n]), inter_col(inter_off[n]);
+    std::vector<int32_t> full_col(pl->has_direct ? full_rp[n] : 0);
+#pragma omp parallel
+    {
+        std::vector<unsigned char> mark(pl->max_comm + 1, 0);
+        std::vector<int32_t> outside;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t m = 0; m < n; ++m) {
+            int32_t i = pl->perm[m];
+            int32_t c = comm_of[m];
+            int64_t lo = c >= 0 ? pl->off[c] : 0, hi = c >= 0 ? pl->off[c + 1] : 0;
+            outside.clear();
+            for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) {
+                int64_t pm = iperm[g->col[e]];
+                if (c >= 0 && pm >= lo && pm < hi) mark[pm - lo] = 1;
+                else outside.push_back((int32_t)pm);
+            }
+            std::sort(outside.begin(), outside.end());
+            std::copy(outside.begin(), outside.end(), inter_col.begin() + inter_off[m]);
+            int64_t w = miss_off[m];
+            int64_t f = pl->has_direct ? full_rp[m] : 0;
+            size_t oi = 0;
+            if (c >= 0) {
+                for (int64_t u = 0; u < hi - lo; ++u) {
+                    if (mark[u]) {
+                        if (pl->has_direct) {
+                            while (oi < outside.size() && outside[oi] < lo + u) full_col[f++] = outside[oi++];
+                            full_col[f++] = (int32_t)(lo + u);
+                        }
+                        mark[u] = 0;
+                    } else if (lo + u != m) {
+                        miss_local[w++] = (int32_t)u;
+                    }
+                }
+            }
+            if (pl->has_direct) {
+                while (oi < outside.size()) full_col[f++] = outside[oi++];
+                while (f < full_rp[m + 1]) full_col[f++] = (int32_t)n;
+            }
+        }
+    }
+
+    // ---- tiles: runs of consecutive rows of one community, cut at tile_nodes
+    // rows or when the rows' sparse indices (padded to 16-byte vectors) would
+    // exceed tile_index_bytes; a single longer row forms a tile of its own
+    std::vector<int32_t> tile_comm, tile_first, tile_count, comm_tile_begin(M + 1, 0);
+    auto cut = [&](int32_t c, int64_t b, int64_t e) {
+        int64_t s = b;
+        while (s < e) {
+            int64_t rows = 0, bytes = 0, r = s;
+            int64_t chunks = 0;
+            while (r < e && rows < pl->tile_nodes) {
+                int64_t rb = pad8(miss_cnt[r]) * 2 + pad4(inter_cnt[r]) * 4;
+                int64_t rc = chunks_of(miss_cnt[r]);
+                if (rows > 0 && (bytes + rb > pl->tile_index_bytes || chunks + rc > kMaxChunks)) break;
+                bytes += rb;
+                chunks += rc;
+                ++rows;
+                ++r;
+            }
+            tile_comm.push_back(c);
+            tile_first.push_back((int32_t)s);
+            tile_count.push_back((int32_t)rows);
+            s = r;
+        }
+    };
+    for (int64_t c = 0; c < M; ++c) {
+        comm_tile_begin[c] = (int32_t)tile_comm.size();
+        cut((int32_t)c, pl->off[c], pl->off[c + 1]);
+    }
+    comm_tile_begin[M] = (int32_t)tile_comm.size();
+    cut(-1, pl->off[M], n);
+    const int64_t T = (int64_t)tile_comm.size();
+    pl->n_tiles = T;
+
+    // ---- sliced ELL per tile, one blob per tile (only with 16-bit
+    // community-local indices; larger communities have no CIA layout)
+    std::vector<TileDesc> tdesc(T);
+    std::vector<unsigned char> blob;
+    pl->max_tile_idx_bytes = 0;
+    std::vector<int64_t> tile_bytes(T, 0);
+    if (pl->miss_idx_bytes == 2) {
+        std::vector<TileBlob> tbs(T);
+#pragma omp parallel
+        {
+            MissScheduler sched;
+#pragma omp for schedule(dynamic, 8)
+            for (int64_t t = 0; t < T; ++t) {
+                const int32_t c = tile_comm[t];
+                const uint16_t msent = c >= 0 ? (uint16_t)(pl->off[c + 1] - pl->off[c]) : 0;
+                build_tile_blob(tile_first[t], tile_count[t], msent, (int32_t)n, miss_cnt, miss_off, miss_local,
+                                inter_cnt, inter_off, inter_col, tbs[t], sched);
+            }
+        }
+        std::vector<int64_t> blob_off(T + 1, 0);
+        for (int64_t t = 0; t < T; ++t) blob_off[t + 1] = blob_off[t] + (int64_t)tbs[t].bytes.size();
+        blob.assign(blob_off[T], 0);
+        const int64_t per16 = pl->precision == CIA_FP64 ? 1 : 2;
+        pl->n_slices = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t t = 0; t < T; ++t) {
+            std::memcpy(blob.data() + blob_off[t], tbs[t].bytes.data(), tbs[t].bytes.size());
+            TileDesc &d = tdesc[t];
+            d.comm = tile_comm[t];
+            d.first = tile_first[t];
+            d.count = tile_count[t];
+            d.nsl = tbs[t].nsl;
+            d.blob_bytes = (uint32_t)tbs[t].bytes.size();
+            d.mvec_off = tbs[t].mvec_off;
+            d.ivec_off = tbs[t].ivec_off;
+            d.lam = d.comm >= 0 ? (uint32_t)(pl->off[d.comm + 1] - pl->off[d.comm]) : 0u;
+            d.blob_off = blob_off[t];
+            d.lo = d.comm >= 0 ? pl->off[d.comm] : 0;
+            d.run = -1;
+            d.pbuf = 0;
+            d.shift = (int32_t)(d.lo - (d.lo & ~(per16 - 1)));
+            d.vtab_off = tbs[t].vtab_off;
+        }
+        for (int64_t t = 0; t < T; ++t) {
+            tile_bytes[t] = (int64_t)tbs[t].bytes.size();
+            pl->max_tile_idx_bytes = std::max<int64_t>(pl->max_tile_idx_bytes, tile_bytes[t]);
+            pl->n_slices += tbs[t].nsl;
+        }
+        pl->blob_bytes = blob_off[T];
+    }
+
+    // ---- default threads per row of the direct method (16-byte vectors;
+    // about two vectors per thread)
+    const int gs = opt ? opt->group_size : 0;
+    if (gs != 0 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
+        return fail(CIA_ERR_INVALID_ARG, "group_size must be 0, 4, 8, 16 or 32");
+    pl->group_size = 32;
+    if (pl->has_direct) {
+        double mean_vec_direct = (double)(full_rp[n] / 4) / (double)std::max<int64_t>(1, n);
+        int gd = 4;
+        while (gd < 32 && 2.0 * gd < mean_vec_direct) gd *= 2;
+        pl->group_size_direct = gs ? gs : gd;
+    }
+
+    // ---- upload
+    CIA_CUDA_TRY(cudaGetDevice(&pl->device));
+    auto &d = pl->d;
+#define UP(dst, src, cnt)                                  \
+    do {                                                   \
+        cia_status _s = upload(pl, &(dst), (src), (cnt));  \
+        if (_s != CIA_OK) return _s;                       \
+    } while (0)
+    UP(d.perm, pl->perm.data(), (size_t)n);
+    UP(d.off, pl->off.data(), (size_t)M + 1);
+    UP(d.tile_comm, tile_comm.data(), tile_comm.size());
+    UP(d.tile_first, tile_first.data(), tile_first.size());
+    UP(d.tile_count, tile_count.data(), tile_count.size());
+    UP(d.comm_tile_begin, comm_tile_begin.data(), comm_tile_begin.size());
+    UP(d.blob, blob.data(), blob.size());
+    if (pl->has_direct) {
+        UP(d.full_rowptr, full_rp.data(), full_rp.size());
+        UP(d.full_col, full_col.data(), full_col.size());
+    }
+    const size_t rb = pl->precision == CIA_FP64 ? sizeof(double) : sizeof(float);
+    {
+        std::vector<unsigned char> om(n * rb, 0);
+        for (int64_t m = 0; m < n; ++m) {
+            double w = omega ? omega[pl->perm[m]] : 0.0;
+            if (rb == sizeof(double)) std::memcpy(&om[m * rb], &w, rb);
+            else {
+                float wf = (float)w;
+                std::memcpy(&om[m * rb], &wf, rb);
+            }
+        }
+        unsigned char *po = nullptr;
+        UP(po, om.data(), om.size());
+        d.omega = po;
+    }
+    cia_status s2;
+    if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
+    if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
+    for (int b = 0; b < 2; ++b) {
+        if ((s2 = alloc_bytes(pl, &d.ph[b], (size_t)pl->p * pl->ph_stride * 2 * rb)) != CIA_OK) return s2;
+        if ((s2 = upload<double>(pl, &d.part[b], nullptr, (size_t)pl->n_tiles * pl->p * 2)) != CIA_OK)
+            return s2;
+    }
+    if ((s2 = alloc_bytes(pl, &d.wdt_half, n * rb)) != CIA_OK) return s2;
+    if ((s2 = alloc_bytes(pl, &d.wdt_full, n * rb)) != CIA_OK) return s2;
+    if ((s2 = upload<double>(pl, &d.wdt_full64, nullptr, n)) != CIA_OK) return s2;
+    if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, n)) != CIA_OK) return s2;
+    if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, n)) != CIA_OK) return s2;
+    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
+    // The persistent TMA pipeline needs a ring of at least two tile buffers
+    // plus two community phasor windows in shared memory, and at most 256
+    // nodes per tile (one consumer thread per node); otherwise plain loads.
+    pl->ring_stages = 0;
+    if (pl->staging == 0 && pl->miss_idx_bytes == 2 && pl->tile_nodes <= 256) {
+        int optin = 0;
+        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+        // a multiple of the two consumer groups, so that each ring buffer is
+        // only ever consumed by one group (its waits can then never see a
+        // barrier two phases ahead)
+        for (int st = 4; st >= 2 && pl->ring_stages == 0; st -= 2)
+            if (pipeline_smem_bytes(pl, st) <= (size_t)optin - 1024) pl->ring_stages = st;
+    }
+    if (pl->ring_stages == 0) pl->staging = 1;
+    if (pl->staging == 0) {
+        // contiguous tile ranges, one per SM, balanced by the bytes each tile
+        // moves (index vectors, per-node state, community phasor windows)
+        int sms = 0;
+        CIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
+        const int64_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (int64_t)pl->p;
+        std::vector<double> cost(T);
+        double total = 0.0;
+        for (int64_t t = 0; t < T; ++t) {
+            const bool first_of_run = t == 0 || tile_comm[t] != tile_comm[t - 1];
+            const int64_t lam = tile_comm[t] >= 0 ? pl->off[tile_comm[t] + 1] - pl->off[tile_comm[t]] : 0;
+            cost[t] = (double)tile_bytes[t] + 48.0 * tile_count[t] + (first_of_run ? (double)(cb * lam) : 0.0) + 256.0;
+            total += cost[t];
+        }
+        const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(sms, T));
+        std::vector<int32_t> ctb(nc + 1, 0);
+        double acc = 0.0;
+        int64_t t = 0;
+        for (int c = 0; c < nc; ++c) {
+            ctb[c] = (int32_t)t;
+            const double target = total * (double)(c + 1) / nc;
+            while (t < T && (acc + 0.5 * cost[t] <= target || c == nc - 1)) acc += cost[t++];
+        }
+        ctb[nc] = (int32_t)T;
+        std::vector<int32_t> runs(nc, 0);
+        for (int c = 0; c < nc; ++c)
+            for (int64_t u = ctb[c]; u < ctb[c + 1]; ++u)
+                if (tile_comm[u] >= 0 && (u == ctb[c] || tile_comm[u] != tile_comm[u - 1])) ++runs[c];
+        pl->n_ctas = nc;
+        pl->max_cta_tiles = 0;
+        for (int c = 0; c < nc; ++c) {
+            pl->max_cta_tiles = std::max<int64_t>(pl->max_cta_tiles, ctb[c + 1] - ctb[c]);
+            int r = -1;
+            for (int64_t u = ctb[c]; u < ctb[c + 1]; ++u) {
+                if (tile_comm[u] >= 0 && (u == ctb[c] || tile_comm[u] != tile_comm[u - 1])) ++r;
+                tdesc[u].run = tile_comm[u] >= 0 ? r : -1;
+                tdesc[u].pbuf = tile_comm[u] >= 0 ? (r & 1) : 0;
+            }
+        }
+        UP(d.cta_tile_begin, ctb.data(), ctb.size());
+        UP(d.cta_runs, runs.data(), runs.size());
+    }
+    UP(d.tile_desc, tdesc.data(), tdesc.size());
+#undef UP
+    CIA_CUDA_TRY(cudaDeviceSynchronize());
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_create(const cia_graph *g, const int32_t *community,
+                                      const double *omega, const cia_coupling *coupling,
+                                      const cia_options *opt, cia_plan_t **out) {
+    clear_error();
+    if (!out) return fail(CIA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !coupling || !community) return fail(CIA_ERR_INVALID_ARG, "graph, community or coupling is NULL");
+    if (g->n < 1 || g->n > (int64_t)INT32_MAX - 1) return fail(CIA_ERR_INVALID_ARG, "n out of range");
+    if (!g->rowptr || (!g->col && g->rowptr[g->n] > 0))
+        return fail(CIA_ERR_INVALID_ARG, "rowptr or col is NULL");
+    cia_plan *pl = new (std::nothrow) cia_plan();
+    if (!pl) return fail(CIA_ERR_OOM, "host allocation of the plan failed");
+    cia_status st;
+    try {
+        st = build_plan(g, community, omega, coupling, opt, pl);
+    } catch (const std::bad_alloc &) {
+        st = fail(CIA_ERR_OOM, "host allocation failed while planning");
+    } catch (const std::exception &e) {
+        st = fail(CIA_ERR_INVALID_ARG, std::string("planning failed: ") + e.what());
+    }
+    if (st != CIA_OK) {
+        free_all(pl);
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_destroy(cia_plan_t *plan) {
+    clear_error();
+    if (!plan) return CIA_OK;
+    free_all(plan);
+    delete plan;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *info) {
+    clear_error();
+    if (!pl || !info) return fail(CIA_ERR_INVALID_ARG, "plan or info is NULL");
+    info->n = pl->n;
+    info->M = pl->M;
+    info->n_free = pl->n_free;
+    info->max_community = pl->max_comm;
+    info->nnz_graph = pl->nnz_graph;
+    info->nnz_missing = pl->nnz_missing;
+    info->nnz_inter = pl->nnz_inter;
+    info->n_tiles = pl->n_tiles;
+    info->device_bytes = pl->device_bytes;
+    info->precision = pl->precision;
+    info->group_size = pl->group_size;
+    info->tile_nodes = pl->tile_nodes;
+    info->missing_index_bytes = pl->miss_idx_bytes;
+    info->staging = pl->staging;
+    info->group_size_direct = pl->group_size_direct;
+    info->max_tile_index_bytes = pl->max_tile_idx_bytes;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_get_permutation(const cia_plan_t *pl, int32_t *perm, int64_t *offsets) {
+    clear_error();
+    if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
+    if (perm) std::memcpy(perm, pl->perm.data(), pl->perm.size() * sizeof(int32_t));
+    if (offsets) std::memcpy(offsets, pl->off.data(), pl->off.size() * sizeof(int64_t));
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_get_split(const cia_plan_t *pl, int64_t *miss_rowptr, int32_t *miss_col,
+                                         int64_t *inter_rowptr, int32_t *inter_col) {
+    clear_error();
+    if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->miss_idx_bytes != 2)
+        return fail(CIA_ERR_UNSUPPORTED, "communities above 65535 nodes have no CIA layout");
+    const int64_t n = pl->n, T = pl->n_tiles;
+    // decode the device's sliced-ELL blobs back into plain CSRs
+    std::vector<TileDesc> td(T);
+    std::vector<unsigned char> blob(pl->blob_bytes);
+    CIA_CUDA_TRY(cudaMemcpy(td.data(), pl->d.tile_desc, T * sizeof(TileDesc), cudaMemcpyDeviceToHost));
+    if (pl->blob_bytes)
+        CIA_CUDA_TRY(cudaMemcpy(blob.data(), pl->d.blob, pl->blob_bytes, cudaMemcpyDeviceToHost));
+    std::vector<std::vector<int32_t>> mrow(n), irow(n);
+    for (int64_t t = 0; t < T; ++t) {
+        const TileDesc &d = td[t];
+        const unsigned char *b = blob.data() + d.blob_off;
+        const uint32_t *desc = reinterpret_cast<const uint32_t *>(b);
+        const uint32_t *rows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
+        const uint32_t *vtab = reinterpret_cast<const uint32_t *>(b + d.vtab_off);
+        std::vector<int32_t> chunk_row;          // chunk -> tile row
+        for (int32_t r = 0; r < d.count; ++r)
+            for (uint32_t c = 0; c < (vtab[r] >> 16); ++c) chunk_row.push_back(r);
+        const uint16_t *sm = reinterpret_cast<const uint16_t *>(b + d.mvec_off);
+        const int32_t *si = reinterpret_cast<const int32_t *>(b + d.ivec_off);
+        for (int64_t sl = 0; sl < d.nsl; ++sl) {
+            const uint32_t moff = desc[4 * sl], nvm = desc[4 * sl + 1], ioff = desc[4 * sl + 2], nvi = desc[4 * sl + 3];
+            for (int lane = 0; lane < 32; ++lane) {
+                const uint32_t rr = rows[32 * sl + lane];
+                const uint32_t mr = rr & 0xffffu, ir = rr >> 16;
+                if (mr != 0xffffu)
+                    for (uint32_t j = 0; j < nvm; ++j)
+                        for (int h = 0; h < 8; ++h) {
+                            const uint16_t v = sm[8 * (moff + 32 * j + lane) + h];
+                            if (v != d.lam) mrow[d.first + chunk_row[mr]].push_back((int32_t)(d.lo + v));
+                        }
+                if (ir != 0xffffu)
+                    for (uint32_t j = 0; j < nvi; ++j)
+                        for (int h = 0; h < 4; ++h) {
+                            const int32_t v = si[4 * (ioff + 32 * j + lane) + h];
+                            if (v != n) irow[d.first + ir].push_back(v);
+                        }
+            }
+        }
+    }
+    int64_t wm = 0, wi = 0;
+    if (miss_rowptr) miss_rowptr[0] = 0;
+    if (inter_rowptr) inter_rowptr[0] = 0;
+    for (int64_t m = 0; m < n; ++m) {
+        std::sort(mrow[m].begin(), mrow[m].end());   // device order is bank-scheduled
+        for (int32_t v : mrow[m]) {
+            if (miss_col) miss_col[wm] = v;
+            ++wm;
+        }
+        for (int32_t v : irow[m]) {
+            if (inter_col) inter_col[wi] = v;
+            ++wi;
+        }
+        if (miss_rowptr) miss_rowptr[m + 1] = wm;
+        if (inter_rowptr) inter_rowptr[m + 1] = wi;
+    }
+    return CIA_OK;
+}

@@ -1,0 +1,82 @@
+"""The C ABI without a GPU: the library builds, loads, exports every entry
+point that include/*.h declares, and rejects bad input on the host before
+any CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_16657_gb300 import build
+    build.build()
+    import paper_2203_16657_gb300 as P
+    return P
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cia_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "cia_plan_create" in names and "cia_integrate" in names
+    so = ctypes.CDLL(lib._abi.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each of them
+    assert set(names) <= set(lib._abi.SIGNATURES), set(names) - set(lib._abi.SIGNATURES)
+
+
+def test_status_strings(lib):
+    for code, name in lib._abi.STATUS.items():
+        assert lib.status_string(code) == name
+
+
+def _plan(lib, rowptr, col, labels, omega=None, **kw):
+    return lib.Plan(np.array(rowptr), np.array(col), np.array(labels), omega, **kw)
+
+
+@pytest.mark.parametrize("rowptr,col,why", [
+    ([0, 1, 1], [1], "asymmetric"),
+    ([0, 1, 2], [0, 0], "self loop"),
+    ([0, 2, 3, 4], [2, 1, 0, 0], "not strictly increasing"),
+    ([0, 1, 2], [5, 0], "out of range"),
+    ([0, 2, 2], [1, 1], "not strictly increasing"),
+])
+def test_invalid_graphs_rejected(lib, rowptr, col, why):
+    n = len(rowptr) - 1
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, rowptr, col, [0] * n)
+    assert e.value.status_name == "CIA_ERR_INVALID_GRAPH"
+    assert why in str(e.value)
+
+
+def test_non_finite_inputs_rejected(lib):
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], np.array([0.0, np.nan]))
+    assert e.value.status_name == "CIA_ERR_NUMERIC"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], K=float("inf"))
+    assert e.value.status_name == "CIA_ERR_NUMERIC"
+
+
+def test_bad_options_rejected(lib):
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], tile_nodes=100)
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, -3])
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
