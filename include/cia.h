@@ -241,6 +241,36 @@ cia_status cia_profile_end(cia_plan_t *plan, cia_profile *out);
  * then invalid. */
 cia_status cia_sync(cia_plan_t *plan, void *stream);
 
+/* ---- right-hand side without device allocation --------------------------- */
+
+/* The FP64 Kuramoto CIA right-hand side of cia_rhs, for callers that may not
+ * have the library allocate device memory (a host application that owns the
+ * device-memory budget through its own pool allocator, or a latency-critical
+ * loop where cudaMalloc, which may synchronise the device, is not allowed).
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (phasors and community observables) is one fixed 5 MiB array in device
+ * memory, held by every GPU that loads this library until the process exits.
+ * The paper has no counterpart of this entry point.
+ *
+ * Everything is in PERMUTED node order (communities contiguous, unlabelled
+ * nodes last), as a plan reports it:
+ *   offsets: device, M + 1 entries (cia_plan_get_permutation);
+ *   miss_rowptr/miss_col, inter_rowptr/inter_col: device CSRs of the missing
+ *     and inter-community links over permuted ids (cia_plan_get_split);
+ *     the column arrays may be NULL when they have no entries;
+ *   x, omega, dxdt: device, n doubles (omega may be NULL = 0);
+ *   coupling: host, CIA_MODEL_KURAMOTO with p harmonics.
+ * Limit: p * (n + M) <= 327680, otherwise CIA_ERR_INVALID_ARG and nothing runs.
+ * The first call on a device resolves the scratch array's device address
+ * (with that device current); make that first call before any stream capture.
+ * All calls share the scratch array: calls that can overlap on the GPU (e.g.
+ * on unordered streams) race with each other. */
+cia_status cia_rhs_kuramoto_static(int64_t n, int64_t M, const int64_t *offsets,
+                                   const int64_t *miss_rowptr, const int32_t *miss_col,
+                                   const int64_t *inter_rowptr, const int32_t *inter_col,
+                                   const double *x, const double *omega,
+                                   const cia_coupling *coupling, double *dxdt, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,8 @@ SIGNATURES = {
     "cia_advance": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _P, _P]),
     "cia_profile_begin": (ctypes.c_int, [_P, ctypes.c_int64]),
     "cia_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "cia_rhs_kuramoto_static": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                               _P, _P, ctypes.POINTER(Coupling), _P, _P]),
 }
 
 _lib = None
