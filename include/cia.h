@@ -92,7 +92,7 @@ typedef struct {
     int tile_nodes;             /* nodes per work tile, 0 = default (256); a multiple of 32, <= 1024 */
     int group_size;             /* threads per row of the direct method's CSR sums: 0 = default,
                                    else 4, 8, 16 or 32 (the CIA sums use one thread per row) */
-    int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (24576); a multiple of 16.
+    int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (32768); a multiple of 16.
                                    A tile is cut at tile_nodes rows or at this many index bytes. */
     int staging;                /* 0 = auto: TMA bulk copies of each tile's indices and community
                                    phasors into shared memory when they fit; 1 = plain loads */

@@ -103,7 +103,7 @@ struct cia_plan {
     int64_t ph_stride = 0;              // phasor entries per harmonic: n + 1 rounded up to even
     int tile_index_bytes = 24576;
     int64_t max_tile_idx_bytes = 0;     // largest index footprint of one tile (bytes)
-    int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0;
+    int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0, max_cta_runs = 0;
     int n_ctas = 0;                     // persistent grid of the pipelined CIA kernel (one per SM)
     int ring_stages = 0;                // tile buffers of its TMA ring
     int staging = 0;                    // 0 = persistent TMA pipeline, 1 = plain loads

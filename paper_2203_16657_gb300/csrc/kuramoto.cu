@@ -140,6 +140,12 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;     // 2 s: far beyond any heal
 
 enum Mode { kRhs = 0, kStage = 1, kFinal = 2 };
 
+// Bytes of the per-run observable array, rounded up to 128 so that the
+// shared-memory regions after it stay aligned for bulk copies.
+__host__ __device__ constexpr size_t zrun_bytes(int64_t runs, int p, size_t complex_bytes) {
+    return ((size_t)runs * (size_t)p * complex_bytes + 127) & ~(size_t)127;
+}
+
 // Shared-memory phasor entries per harmonic for TMA staging: lambda_max + 1
 // plus up to one entry on each side from rounding the window to 16 bytes.
 int64_t tma_ph_region(const cia_plan *pl) { return (pl->max_comm + 4) & ~(int64_t)1; }
@@ -184,6 +190,7 @@ struct StageParams {
     int *err_flag;             // set when a bounded wait gives up
     int stages;                // ring buffers of the pipelined kernel
     int max_cta_tiles;         // most tiles of one persistent CTA
+    int max_cta_runs;          // most community runs of one persistent CTA
     const int32_t *cta_tile_begin;
     const int32_t *cta_runs;   // community runs in each CTA's tile range
 };
@@ -434,16 +441,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
     using C = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t pfull_bar[2], pempty_bar[kGroups][2], desc_bar;
-    __shared__ C zbuf[2][P];               // community observable of each community buffer
-    __shared__ double red[kGroups][kConsumerWarps][2 * P];
+    __shared__ __align__(8) uint64_t pfull_bar[2], pempty_bar[2], desc_bar;
+    __shared__ __align__(8) uint64_t swfull_bar[2], swempty_bar[2];   // gather -> node hand-off
+    __shared__ __align__(8) uint64_t zready_bar;   // observables of all runs written
+    __shared__ double red[kConsumerWarps][2 * P];
     __shared__ volatile int s_prod_abort, s_cons_abort;
 
     const int S = a.stages;
     const int tb = a.cta_tile_begin[blockIdx.x], te = a.cta_tile_begin[blockIdx.x + 1];
     // shared memory: tile descriptors | ring of tile blobs | 2 community windows | W sums
     TileDesc *sdesc = reinterpret_cast<TileDesc *>(smem_raw);               // [max_cta_tiles]
-    unsigned char *ring = smem_raw + (size_t)a.max_cta_tiles * sizeof(TileDesc);   // [S][idx_cap]
+    C *zrun = reinterpret_cast<C *>(sdesc + a.max_cta_tiles);               // [max_cta_runs][P]
+    // the ring is the destination of bulk copies: keep it 128-byte aligned
+    unsigned char *ring = reinterpret_cast<unsigned char *>(zrun) + zrun_bytes(a.max_cta_runs, P, sizeof(C));
     C *pbuf = reinterpret_cast<C *>(ring + (size_t)S * a.idx_cap);         // [2][P][ph_region]
     C *sWall = pbuf + 2 * P * a.ph_region;                                 // [groups][2][P][kConsumers]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -455,11 +465,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
             mbar_init(&empty_bar[s], kConsumerWarps);
         }
         for (int b = 0; b < 2; ++b) {
-            // two arrivals: the phasor copy (with its bytes) and "Z written"
-            mbar_init(&pfull_bar[b], 2);
-            for (int g = 0; g < kGroups; ++g) mbar_init(&pempty_bar[g][b], kConsumerWarps);
+            mbar_init(&pfull_bar[b], 1);
+            mbar_init(&pempty_bar[b], kConsumerWarps);
+            mbar_init(&swfull_bar[b], kConsumerWarps);
+            mbar_init(&swempty_bar[b], kConsumerWarps);
         }
         mbar_init(&desc_bar, 1);
+        mbar_init(&zready_bar, 1);
         s_prod_abort = 0;
         s_cons_abort = 0;
         // this CTA's tile descriptors, one bulk copy
@@ -482,48 +494,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
 
     if (warp == kGroups * kConsumerWarps) {
         // ------------------------------------------------------------ producer
-        // lane 0 waits and issues the copies; the whole warp reduces the
-        // community observable of every new run while the copies fly
+        // lane 0 waits and issues the copies.  The whole warp reduces the
+        // community observables of every run of this CTA and posts them on
+        // zready before the producer's first wait that can block: consumers
+        // need them to finish a tile, and that wait may need a finished tile.
         int issued = 0, last_pload = -1;
-        for (int i = tb; i < te; ++i) {
-            const int li = i - tb, s = li % S, k = li / S;
-            const TileDesc &d = sdesc[li];
-            const bool dense = d.comm >= 0;
-            const bool new_run = dense && (li == 0 || sdesc[li - 1].run != d.run);
-            int ok = 1;
-            if (lane == 0) {
-                if (s_cons_abort) ok = 0;
-                else if (k >= 1) ok = mbar_wait_bounded(&empty_bar[s], (k - 1) & 1, kWaitLimitNs);
-                if (!ok && !s_cons_abort) {
-                    atomicExch(a.err_flag, 1);
-                    s_prod_abort = 1;
-                }
-            }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            if (new_run) {
-                const int run = d.run, b = run & 1;
-                if (lane == 0) {
-                    // every group releases run - 2 of this buffer before it is reused
-                    for (int g = 0; g < kGroups && ok && run >= 2; ++g)
-                        ok = mbar_wait_bounded(&pempty_bar[g][b], ((run >> 1) - 1) & 1, kWaitLimitNs);
-                    if (!ok) {
-                        atomicExch(a.err_flag, 1);
-                        s_prod_abort = 1;
-                    } else {
-                        constexpr int64_t per16 = 16 / (int64_t)sizeof(C);
-                        const int64_t pstart = d.lo - d.shift;
-                        const int64_t pend = (d.lo + d.lam + 1 + per16 - 1) & ~(per16 - 1);
-                        const uint32_t pbytes = (uint32_t)((pend - pstart) * (int64_t)sizeof(C));
-                        mbar_arrive_expect_tx(&pfull_bar[b], P * pbytes);
-                        for (int kk = 0; kk < P; ++kk)
-                            bulk_g2s(pbuf + (b * P + kk) * a.ph_region, a.ph_in + kk * stride + pstart, pbytes,
-                                     &pfull_bar[b]);
-                    }
-                }
-                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-                // (E1.1) community observable: lane j adds tiles j, j + 32, ...
-                // in FP64, then a fixed shuffle tree (deterministic order)
-                const int u0 = a.comm_tile_begin[d.comm], u1 = a.comm_tile_begin[d.comm + 1];
+        bool zdone = false;
+        auto post_observables = [&]() {
+            // (E1.1) lane j adds tiles j, j + 32, ... in FP64, then a fixed
+            // shuffle tree (deterministic order)
+            for (int q = 0; q < te - tb; ++q) {
+                const TileDesc &dq = sdesc[q];
+                if (dq.comm < 0 || (q > 0 && sdesc[q - 1].run == dq.run)) continue;
+                const int u0 = a.comm_tile_begin[dq.comm], u1 = a.comm_tile_begin[dq.comm + 1];
                 double re[P], im[P];
 #pragma unroll
                 for (int kk = 0; kk < P; ++kk) re[kk] = im[kk] = 0.0;
@@ -542,10 +525,49 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                         re[kk] += __shfl_xor_sync(0xffffffffu, re[kk], o);
                         im[kk] += __shfl_xor_sync(0xffffffffu, im[kk], o);
                     }
-                    if (lane == 0) zbuf[b][kk] = mk2((T)re[kk], (T)im[kk]);
+                    if (lane == 0) zrun[(size_t)dq.run * P + kk] = mk2((T)re[kk], (T)im[kk]);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&pfull_bar[b]);   // Z is written (release)
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&zready_bar);     // all observables written (release)
+            zdone = true;
+        };
+        for (int i = tb; i < te; ++i) {
+            const int li = i - tb, s = li % S, k = li / S;
+            const TileDesc &d = sdesc[li];
+            const bool dense = d.comm >= 0;
+            const bool new_run = dense && (li == 0 || sdesc[li - 1].run != d.run);
+            if (!zdone && (k >= 1 || (new_run && d.run >= 2))) post_observables();
+            int ok = 1;
+            if (lane == 0) {
+                if (s_cons_abort) ok = 0;
+                else if (k >= 1) ok = mbar_wait_bounded(&empty_bar[s], (k - 1) & 1, kWaitLimitNs);
+                if (!ok && !s_cons_abort) {
+                    atomicExch(a.err_flag, 1);
+                    s_prod_abort = 1;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (new_run) {
+                const int run = d.run, b = run & 1;
+                if (lane == 0) {
+                    // every group releases run - 2 of this buffer before it is reused
+                    if (run >= 2) ok = mbar_wait_bounded(&pempty_bar[b], ((run >> 1) - 1) & 1, kWaitLimitNs);
+                    if (!ok) {
+                        atomicExch(a.err_flag, 1);
+                        s_prod_abort = 1;
+                    } else {
+                        constexpr int64_t per16 = 16 / (int64_t)sizeof(C);
+                        const int64_t pstart = d.lo - d.shift;
+                        const int64_t pend = (d.lo + d.lam + 1 + per16 - 1) & ~(per16 - 1);
+                        const uint32_t pbytes = (uint32_t)((pend - pstart) * (int64_t)sizeof(C));
+                        mbar_arrive_expect_tx(&pfull_bar[b], P * pbytes);
+                        for (int kk = 0; kk < P; ++kk)
+                            bulk_g2s(pbuf + (b * P + kk) * a.ph_region, a.ph_in + kk * stride + pstart, pbytes,
+                                     &pfull_bar[b]);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
                 last_pload = run;
             }
             if (lane == 0) {
@@ -555,6 +577,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
             }
             ++issued;
         }
+        if (!zdone && !s_prod_abort && !s_cons_abort) post_observables();
         // let every copy this warp issued land before the CTA can retire
         if (lane == 0) {
             for (int li = (issued > S ? issued - S : 0); li < issued; ++li)
@@ -566,13 +589,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
     }
 
     // ---------------------------------------------------------------- consumers
-    const int grp = warp / kConsumerWarps;                 // 0 or 1
+    const int grp = warp / kConsumerWarps;                 // 0: gather warps, 1: node warps
     const int gw = warp % kConsumerWarps;                  // warp within the group
     const int gt = threadIdx.x - grp * kConsumers;         // thread within the group
-    C *sWm = sWall + (size_t)grp * P * (kMaxChunks + kConsumers);   // [P][kMaxChunks] chunk sums
-    C *sWi = sWm + P * kMaxChunks;                                    // [P][kConsumers] inter sums
-    int released = -1;                                     // last run this group released
-    const int nruns = a.cta_runs[blockIdx.x];              // community runs of this CTA
     auto gsync_or = [&](bool pred) {
         uint32_t r;
         asm volatile(
@@ -586,18 +605,156 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
         return r != 0;
     };
     auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(kConsumers) : "memory"); };
+    // hand-off buffers, two of each: chunk sums, inter sums, row -> chunk tables
+    auto sWm_of = [&](int b) { return sWall + (size_t)b * P * (kMaxChunks + kConsumers); };   // [P][kMaxChunks]
+    auto sWi_of = [&](int b) { return sWm_of(b) + P * kMaxChunks; };                           // [P][kConsumers]
+    uint32_t *sWv = reinterpret_cast<uint32_t *>(sWall + 2 * (size_t)P * (kMaxChunks + kConsumers));   // [2][kConsumers]
+
+    if (grp == 0) {
+        // ------------------------------------------------- gather warps (Phase A)
+        for (int i = tb; i < te; ++i) {
+            const int li = i - tb, s = li % S, k = li / S, b = li & 1, u = li >> 1;
+            const unsigned char *slot = ring + (size_t)s * a.idx_cap;
+            const TileDesc h = sdesc[li];
+            const bool dense = h.comm >= 0;
+            bool fail = false;
+            if (gt == 0) {
+                fail = s_prod_abort || !mbar_wait_bounded(&full_bar[s], k & 1, kWaitLimitNs);
+                if (!fail && dense) {
+                    fail = !mbar_wait_bounded(&pfull_bar[h.pbuf], (h.run >> 1) & 1, kWaitLimitNs);
+                    // the slot after the community is where padding entries point: zero it
+                    if (!fail)
+                        for (int kk = 0; kk < P; ++kk)
+                            pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam] = mk2(T(0), T(0));
+                }
+                if (!fail && u >= 1) fail = !mbar_wait_bounded(&swempty_bar[b], (u - 1) & 1, kWaitLimitNs);
+                if (fail) {
+                    atomicExch(a.err_flag, 1);
+                    s_cons_abort = 1;
+                }
+            }
+            if (gsync_or(fail)) break;
+            const C *cph = pbuf + (size_t)h.pbuf * P * a.ph_region + h.shift;   // cph[k * ph_region + l]
+            const uint4 *sdsl = reinterpret_cast<const uint4 *>(slot);
+            const uint32_t *srows = reinterpret_cast<const uint32_t *>(slot + 16 * h.nsl);
+            const uint4 *mvec = reinterpret_cast<const uint4 *>(slot + h.mvec_off);
+            const int4 *ivec = reinterpret_cast<const int4 *>(slot + h.ivec_off);
+            C *sWm = sWm_of(b), *sWi = sWi_of(b);
+            // per slice: inter-community gathers (global) issued first, then the
+            // missing links from the community window (shared)
+            for (int sl = gw; sl < h.nsl; sl += kConsumerWarps) {
+                const uint4 d = sdsl[sl];
+                const uint32_t rows = srows[sl * 32 + lane];
+                const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+                T ire[P], iim[P], mre[P], mim[P];
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) ire[kk] = iim[kk] = mre[kk] = mim[kk] = T(0);
+                const int4 *iv = ivec + d.z + lane;
+                constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 4 : 1;   // vectors gathered ahead
+                C pre[kPre][4][P];
+                const uint32_t npre = d.w < kPre ? d.w : kPre;
+#pragma unroll
+                for (uint32_t j = 0; j < kPre; ++j) {
+                    if (j < npre) {
+                        const int4 q = iv[32 * j];
+                        const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                            for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
+                    }
+                }
+                const uint4 *mv = mvec + d.x + lane;
+#pragma unroll 2
+                for (uint32_t j = 0; j < d.y; ++j) {
+                    const uint4 q = mv[32 * j];
+                    const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int hh = 0; hh < 4; ++hh) {
+                        const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
+#pragma unroll
+                        for (int kk = 0; kk < P; ++kk) {
+                            const C v0 = cph[kk * a.ph_region + l0];
+                            const C v1 = cph[kk * a.ph_region + l1];
+                            mre[kk] -= v0.x + v1.x;
+                            mim[kk] -= v0.y + v1.y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < kPre; ++j) {
+                    if (j < npre) {
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                            for (int kk = 0; kk < P; ++kk) {
+                                ire[kk] += pre[j][hh][kk].x;
+                                iim[kk] += pre[j][hh][kk].y;
+                            }
+                    }
+                }
+                // longer inter lists: further batches of kPre vectors, loads first
+                for (uint32_t j0 = kPre; j0 < d.w; j0 += kPre) {
+#pragma unroll
+                    for (uint32_t j = 0; j < kPre; ++j) {
+                        if (j0 + j < d.w) {
+                            const int4 q = iv[32 * (j0 + j)];
+                            const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                            for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                                for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
+                        }
+                    }
+#pragma unroll
+                    for (uint32_t j = 0; j < kPre; ++j) {
+                        if (j0 + j < d.w) {
+#pragma unroll
+                            for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                                for (int kk = 0; kk < P; ++kk) {
+                                    ire[kk] += pre[j][hh][kk].x;
+                                    iim[kk] += pre[j][hh][kk].y;
+                                }
+                        }
+                    }
+                }
+                if (mrow != 0xffffu) {
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk) sWm[kk * kMaxChunks + mrow] = mk2(mre[kk], mim[kk]);
+                }
+                if (irow != 0xffffu) {
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk) sWi[kk * kConsumers + irow] = mk2(ire[kk], iim[kk]);
+                }
+            }
+            // the row -> chunk table travels with the sums (the ring buffer is
+            // released below)
+            if (gt < h.count) sWv[b * kConsumers + gt] = reinterpret_cast<const uint32_t *>(slot + h.vtab_off)[gt];
+            gsync();
+            if (lane == 0) {
+                mbar_arrive(&empty_bar[s]);                   // the ring buffer is free again
+                mbar_arrive(&swfull_bar[b]);                  // the sums of tile i are ready (release)
+            }
+        }
+        return;
+    }
+
+    // ------------------------------------------------------- node warps (Phase B)
     // release of a community buffer: once per run, in run order, as soon as
-    // the group knows it has no further tile of that run (from the tile
-    // descriptors, never from the producer, which may itself be waiting for
-    // this release).  A run is released only after its own phasor load has
-    // landed: that load was issued after the producer saw the release of
+    // these warps have finished their last tile of the run (known from the
+    // tile descriptors, never from the producer, which may itself be waiting
+    // for the release).  A run is released only after its own phasor load
+    // has landed: that load was issued after the producer saw the release of
     // run - 2, so a buffer's pempty barrier never runs two phases ahead of
     // its waiter.
+    int released = -1;
+    const int nruns = a.cta_runs[blockIdx.x];
     auto release_through = [&](int run_upto) {
         for (int r = released + 1; r <= run_upto; ++r) {
-            if (gt % 32 == 0 && !s_cons_abort && !s_prod_abort) {
+            if (lane == 0 && !s_cons_abort && !s_prod_abort) {
                 if (mbar_wait_bounded(&pfull_bar[r & 1], (r >> 1) & 1, kWaitLimitNs)) {
-                    mbar_arrive(&pempty_bar[grp][r & 1]);
+                    mbar_arrive(&pempty_bar[r & 1]);
                 } else {
                     atomicExch(a.err_flag, 1);
                     s_cons_abort = 1;
@@ -606,54 +763,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
         }
         if (run_upto > released) released = run_upto;
     };
-    // runs that end before the group's first tile
-    {
-        const int i0 = tb + grp;
-        release_through((i0 >= te || sdesc[i0 - tb].comm < 0) ? nruns - 1 : sdesc[i0 - tb].run - 1);
-    }
-
-    for (int i = tb + grp; i < te; i += kGroups) {
-        const int li = i - tb, s = li % S, k = li / S;
-        const unsigned char *slot = ring + (size_t)s * a.idx_cap;
+    bool zwaited = false;
+    for (int i = tb; i < te; ++i) {
+        const int li = i - tb, b = li & 1, u = li >> 1;
         const TileDesc h = sdesc[li];
         const bool dense = h.comm >= 0;
-        bool fail = false;
-        if (gt == 0) {
-            fail = s_prod_abort || !mbar_wait_bounded(&full_bar[s], k & 1, kWaitLimitNs);
-            if (fail) {
-                atomicExch(a.err_flag, 1);
-                s_cons_abort = 1;
-            }
-        }
-        if (gsync_or(fail)) break;
-        if (dense) {
-            bool pfail = false;
-            if (gt == 0) {
-                pfail = !mbar_wait_bounded(&pfull_bar[h.pbuf], (h.run >> 1) & 1, kWaitLimitNs);
-                if (pfail) {
-                    atomicExch(a.err_flag, 1);
-                    s_cons_abort = 1;
-                } else {
-                    // the slot after the community is where padding entries point: zero it
-#pragma unroll
-                    for (int kk = 0; kk < P; ++kk)
-                        pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam] = mk2(T(0), T(0));
-                }
-            }
-            if (gsync_or(pfail)) break;
-        }
-        const C *cph = pbuf + (size_t)h.pbuf * P * a.ph_region + h.shift;   // cph[k * ph_region + l]
-        const uint4 *sdsl = reinterpret_cast<const uint4 *>(slot);
-        const uint32_t *srows = reinterpret_cast<const uint32_t *>(slot + 16 * h.nsl);
-        const uint4 *mvec = reinterpret_cast<const uint4 *>(slot + h.mvec_off);
-        const int4 *ivec = reinterpret_cast<const int4 *>(slot + h.ivec_off);
-
-        // Phase B inputs of this thread's node, loaded now, used after Phase A
+        // this thread's node inputs, loaded while the gather warps work
         const int r = gt;
         const int64_t m = h.first + r;
         const bool live = r < h.count;
-        // this row's chunks, read before the ring buffer is released
-        const uint32_t vt = live ? reinterpret_cast<const uint32_t *>(slot + h.vtab_off)[r] : 0u;
         double theta_m = 0.0, wdt64_m = 0.0;
         T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
         int32_t perm_m = 0;
@@ -668,107 +786,28 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                 else wdt64_m = a.wdt64[m];
             }
         }
-
-        // Phase A: per slice, inter-community gathers (global) issued first,
-        // then the missing links from the community buffer (shared)
-        for (int sl = gw; sl < h.nsl; sl += kConsumerWarps) {
-            const uint4 d = sdsl[sl];
-            const uint32_t rows = srows[sl * 32 + lane];
-            const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
-            T ire[P], iim[P], mre[P], mim[P];
-#pragma unroll
-            for (int kk = 0; kk < P; ++kk) ire[kk] = iim[kk] = mre[kk] = mim[kk] = T(0);
-            const int4 *iv = ivec + d.z + lane;
-            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 4 : 1;   // vectors gathered ahead
-            C pre[kPre][4][P];
-            const uint32_t npre = d.w < kPre ? d.w : kPre;
-#pragma unroll
-            for (uint32_t j = 0; j < kPre; ++j) {
-                if (j < npre) {
-                    const int4 q = iv[32 * j];
-                    const int l4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int hh = 0; hh < 4; ++hh)
-#pragma unroll
-                        for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
-                }
-            }
-            const uint4 *mv = mvec + d.x + lane;
-#pragma unroll 2
-            for (uint32_t j = 0; j < d.y; ++j) {
-                const uint4 q = mv[32 * j];
-                const unsigned w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                for (int hh = 0; hh < 4; ++hh) {
-                    const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
-#pragma unroll
-                    for (int kk = 0; kk < P; ++kk) {
-                        const C v0 = cph[kk * a.ph_region + l0];
-                        const C v1 = cph[kk * a.ph_region + l1];
-                        mre[kk] -= v0.x + v1.x;
-                        mim[kk] -= v0.y + v1.y;
-                    }
-                }
-            }
-#pragma unroll
-            for (uint32_t j = 0; j < kPre; ++j) {
-                if (j < npre) {
-#pragma unroll
-                    for (int hh = 0; hh < 4; ++hh)
-#pragma unroll
-                        for (int kk = 0; kk < P; ++kk) {
-                            ire[kk] += pre[j][hh][kk].x;
-                            iim[kk] += pre[j][hh][kk].y;
-                        }
-                }
-            }
-            // longer inter lists: further batches of kPre vectors, loads first
-            for (uint32_t j0 = kPre; j0 < d.w; j0 += kPre) {
-#pragma unroll
-                for (uint32_t j = 0; j < kPre; ++j) {
-                    if (j0 + j < d.w) {
-                        const int4 q = iv[32 * (j0 + j)];
-                        const int l4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                        for (int hh = 0; hh < 4; ++hh)
-#pragma unroll
-                            for (int kk = 0; kk < P; ++kk) pre[j][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
-                    }
-                }
-#pragma unroll
-                for (uint32_t j = 0; j < kPre; ++j) {
-                    if (j0 + j < d.w) {
-#pragma unroll
-                        for (int hh = 0; hh < 4; ++hh)
-#pragma unroll
-                            for (int kk = 0; kk < P; ++kk) {
-                                ire[kk] += pre[j][hh][kk].x;
-                                iim[kk] += pre[j][hh][kk].y;
-                            }
-                    }
-                }
-            }
-            if (mrow != 0xffffu) {
-#pragma unroll
-                for (int kk = 0; kk < P; ++kk) sWm[kk * kMaxChunks + mrow] = mk2(mre[kk], mim[kk]);
-            }
-            if (irow != 0xffffu) {
-#pragma unroll
-                for (int kk = 0; kk < P; ++kk) sWi[kk * kConsumers + irow] = mk2(ire[kk], iim[kk]);
+        bool fail = false;
+        if (gt == 0) {
+            fail = !mbar_wait_bounded(&swfull_bar[b], u & 1, kWaitLimitNs);
+            if (!fail && !zwaited) fail = !mbar_wait_bounded(&zready_bar, 0, kWaitLimitNs);
+            if (fail) {
+                atomicExch(a.err_flag, 1);
+                s_cons_abort = 1;
             }
         }
-        gsync();
-        if (lane == 0) mbar_arrive(&empty_bar[s]);           // the ring buffer is free again
-
-        // Phase B: one thread per node
+        if (gsync_or(fail)) break;
+        zwaited = true;
+        const C *cph = pbuf + (size_t)h.pbuf * P * a.ph_region + h.shift;
+        const C *sWm = sWm_of(b), *sWi = sWi_of(b);
         T sre[P], sim[P];
 #pragma unroll
         for (int kk = 0; kk < P; ++kk) sre[kk] = sim[kk] = T(0);
         if (live) {
+            const uint32_t vt = sWv[b * kConsumers + r];
             T coup = T(0);
 #pragma unroll
             for (int kk = 0; kk < P; ++kk) {
-                const C u = dense ? cph[kk * a.ph_region + (int)(m - h.lo)] : __ldg(a.ph_in + kk * stride + m);
+                const C uu = dense ? cph[kk * a.ph_region + (int)(m - h.lo)] : __ldg(a.ph_in + kk * stride + m);
                 const C wi = sWi[kk * kConsumers + r];
                 T zr = wi.x, zi = wi.y;
                 for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
@@ -778,11 +817,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                 }
                 if (dense) {
                     // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
-                    zr += zbuf[h.pbuf][kk].x - u.x;
-                    zi += zbuf[h.pbuf][kk].y - u.y;
+                    zr += zrun[(size_t)h.run * P + kk].x - uu.x;
+                    zi += zrun[(size_t)h.run * P + kk].y - uu.y;
                 }
-                const T re = zr * u.x + zi * u.y;
-                const T im = zi * u.x - zr * u.y;
+                // W conj(u_m): real part -> cosine harmonics, imaginary part -> sine
+                const T re = zr * uu.x + zi * uu.y;
+                const T im = zi * uu.x - zr * uu.y;
                 coup += a.d_sin[kk] * im + a.d_cos[kk] * re;
             }
             coup *= a.k_over_n;
@@ -800,13 +840,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                     a.theta[m] = th;
                     y = (T)th;
                 }
-                C u[P];
-                phasors<T, P>(y, u);
+                C uo[P];
+                phasors<T, P>(y, uo);
 #pragma unroll
                 for (int kk = 0; kk < P; ++kk) {
-                    a.ph_out[kk * stride + m] = u[kk];
-                    sre[kk] = u[kk].x;
-                    sim[kk] = u[kk].y;
+                    a.ph_out[kk * stride + m] = uo[kk];
+                    sre[kk] = uo[kk].x;
+                    sim[kk] = uo[kk].y;
                 }
             }
         }
@@ -822,24 +862,24 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
             if (lane == 0) {
 #pragma unroll
                 for (int kk = 0; kk < P; ++kk) {
-                    red[grp][gw][2 * kk] = (double)sre[kk];
-                    red[grp][gw][2 * kk + 1] = (double)sim[kk];
+                    red[gw][2 * kk] = (double)sre[kk];
+                    red[gw][2 * kk + 1] = (double)sim[kk];
                 }
             }
         }
-        gsync();                                             // Phase B done
+        gsync();                                             // node phase of tile i done
+        if (lane == 0) mbar_arrive(&swempty_bar[b]);         // its sums are consumed
         if (MODE != kRhs && gt < 2 * P) {
             double sum = 0.0;
-            for (int w = 0; w < kConsumerWarps; ++w) sum += red[grp][w][gt];
+            for (int w = 0; w < kConsumerWarps; ++w) sum += red[w][gt];
             a.part_out[(size_t)i * P * 2 + gt] = sum;
         }
-        // release every run before the run of this group's next tile
+        // release every run before the run of the next tile
         {
-            const int ni = i + kGroups;
+            const int ni = i + 1;
             release_through((!dense || ni >= te || sdesc[ni - tb].comm < 0) ? nruns - 1 : sdesc[ni - tb].run - 1);
         }
     }
-    // every run of this CTA is finished for this group
     release_through(nruns - 1);
 }
 
@@ -998,6 +1038,7 @@ StageParams<T> base_params(cia_plan *pl, int method) {
     a.err_flag = pl->d.err_flag;
     a.stages = pl->ring_stages;
     a.max_cta_tiles = (int)pl->max_cta_tiles;
+    a.max_cta_runs = (int)pl->max_cta_runs;
     a.cta_tile_begin = pl->d.cta_tile_begin;
     a.cta_runs = pl->d.cta_runs;
     (void)method;
@@ -1117,8 +1158,10 @@ size_t stage_smem_bytes(const cia_plan *pl, int method) {
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages) {
     const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
     const size_t idx_cap = (size_t)((pl->max_tile_idx_bytes + 15) & ~(int64_t)15);
-    return (size_t)pl->max_cta_tiles * sizeof(TileDesc) + (size_t)stages * idx_cap +
-           2 * cb * (size_t)tma_ph_region(pl) + (size_t)kGroups * cb * (size_t)(kMaxChunks + kConsumers);
+    return (size_t)pl->max_cta_tiles * sizeof(TileDesc) +
+           zrun_bytes(pl->max_cta_runs, 1, cb) + (size_t)stages * idx_cap +
+           2 * cb * (size_t)tma_ph_region(pl) + 2 * cb * (size_t)(kMaxChunks + kConsumers) +
+           2 * sizeof(uint32_t) * (size_t)kConsumers;
 }
 
 cudaError_t launch_phasors_from_x(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {

@@ -291,7 +291,7 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     pl->tile_nodes = (opt && opt->tile_nodes) ? opt->tile_nodes : 256;
     if (pl->tile_nodes < 32 || pl->tile_nodes > 1024 || pl->tile_nodes % 32)
         return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024]");
-    pl->tile_index_bytes = (opt && opt->tile_index_bytes) ? opt->tile_index_bytes : 24576;
+    pl->tile_index_bytes = (opt && opt->tile_index_bytes) ? opt->tile_index_bytes : 32768;
     if (pl->tile_index_bytes < 256 || pl->tile_index_bytes % 16)
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
@@ -571,20 +571,12 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, n)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, n)) != CIA_OK) return s2;
     if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
-    // The persistent TMA pipeline needs a ring of at least two tile buffers
-    // plus two community phasor windows in shared memory, and at most 256
-    // nodes per tile (one consumer thread per node); otherwise plain loads.
+    // The persistent TMA pipeline needs at most 256 nodes per tile (one
+    // consumer thread per node) and, in shared memory, the CTA's tile
+    // descriptors and observables plus a ring of at least two tile buffers
+    // and two community phasor windows; otherwise the kernels use plain loads.
     pl->ring_stages = 0;
-    if (pl->staging == 0 && pl->miss_idx_bytes == 2 && pl->tile_nodes <= 256) {
-        int optin = 0;
-        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
-        // a multiple of the two consumer groups, so that each ring buffer is
-        // only ever consumed by one group (its waits can then never see a
-        // barrier two phases ahead)
-        for (int st = 4; st >= 2 && pl->ring_stages == 0; st -= 2)
-            if (pipeline_smem_bytes(pl, st) <= (size_t)optin - 1024) pl->ring_stages = st;
-    }
-    if (pl->ring_stages == 0) pl->staging = 1;
+    if (pl->staging == 0 && (pl->miss_idx_bytes != 2 || pl->tile_nodes > 256)) pl->staging = 1;
     if (pl->staging == 0) {
         // contiguous tile ranges, one per SM, balanced by the bytes each tile
         // moves (index vectors, per-node state, community phasor windows)
@@ -615,6 +607,8 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
                 if (tile_comm[u] >= 0 && (u == ctb[c] || tile_comm[u] != tile_comm[u - 1])) ++runs[c];
         pl->n_ctas = nc;
         pl->max_cta_tiles = 0;
+        pl->max_cta_runs = 1;
+        for (int c = 0; c < nc; ++c) pl->max_cta_runs = std::max<int64_t>(pl->max_cta_runs, runs[c]);
         for (int c = 0; c < nc; ++c) {
             pl->max_cta_tiles = std::max<int64_t>(pl->max_cta_tiles, ctb[c + 1] - ctb[c]);
             int r = -1;
@@ -626,6 +620,16 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         }
         UP(d.cta_tile_begin, ctb.data(), ctb.size());
         UP(d.cta_runs, runs.data(), runs.size());
+    }
+    if (pl->staging == 0) {
+        int optin = 0;
+        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+        // a multiple of the two consumer groups, so that each ring buffer is
+        // only ever consumed by one group (its waits can then never see a
+        // barrier two phases ahead)
+        for (int st = 4; st >= 2 && pl->ring_stages == 0; st -= 2)
+            if (pipeline_smem_bytes(pl, st) <= (size_t)optin - 1024) pl->ring_stages = st;
+        if (pl->ring_stages == 0) pl->staging = 1;
     }
     UP(d.tile_desc, tdesc.data(), tdesc.size());
 #undef UP
