@@ -50,7 +50,8 @@ typedef enum {
 } cia_status;
 
 typedef enum {
-    CIA_MODEL_KURAMOTO = 0      /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
+    CIA_MODEL_KURAMOTO = 0,     /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
+    CIA_MODEL_KURAMOTO_HO = 1   /* the same plus a triadic term on complete community hyperedges (App. A.7) */
 } cia_model;
 
 typedef enum {
@@ -77,13 +78,21 @@ typedef struct {
  *   f_m(theta) = omega_m,  g(x_l, x_m) = K h(x_l - x_m),
  *   h(x) = sum_{k=1..p} d_sin[k-1] sin(kx) + d_cos[k-1] cos(kx)
  * (the higher-harmonics Kuramoto model, App. A.4; p = 1, d_sin = {1},
- * d_cos = {0} is the classical model). */
+ * d_cos = {0} is the classical model).
+ * CIA_MODEL_KURAMOTO_HO adds, for every node m of a community c, the triadic
+ * term of the higher-order Kuramoto model (App. A.7, eq. HOKuramoto with
+ * lambda = (1, 1, -2)) over the community's complete 2-simplices:
+ *   (K2/N^2) sum_{j != k; j, k in c, both != m} sin(theta_j + theta_k - 2 theta_m);
+ * nodes in no community get no triadic term.  The CIA evaluates it from the
+ * community moments Z_1, Z_2 (eq. HOKuramoto_fastRHS with the tuples that
+ * repeat an index removed); the direct method sums the pairs one by one. */
 typedef struct {
     int model;                  /* cia_model */
     int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
     double d_sin[CIA_MAX_HARMONICS];
     double d_cos[CIA_MAX_HARMONICS];
     double K;                   /* coupling constant multiplying (1/N) sum */
+    double K2;                  /* triadic coupling (CIA_MODEL_KURAMOTO_HO), multiplies (1/N^2) sum */
 } cia_coupling;
 
 typedef struct {

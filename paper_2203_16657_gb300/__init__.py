@@ -42,12 +42,13 @@ class Plan:
 
     rowptr/col: symmetric CSR (host int64 / int32), labels: int32 community ids
     (-1 = no community), omega: natural frequencies (host float64).
-    Coupling h(x) = sum_k d_sin[k] sin((k+1)x) + d_cos[k] cos((k+1)x), scaled by K/N.
+    Coupling h(x) = sum_k d_sin[k] sin((k+1)x) + d_cos[k] cos((k+1)x), scaled by K/N;
+    model="kuramoto_ho" adds the triadic term on community hyperedges, scaled by K2/N^2.
     """
 
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
-                 tile_index_bytes=0, staging="auto"):
+                 tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0):
         lib = load()
         self._lib = lib
         self._keep = []
@@ -65,12 +66,13 @@ class Plan:
             raise ValueError("d_sin and d_cos must have the same length in [1, %d]"
                              % _abi.CIA_MAX_HARMONICS)
         cp = _abi.Coupling()
-        cp.model = _abi.MODEL["kuramoto"]
+        cp.model = _abi.MODEL[model]
         cp.p = p
         for k in range(p):
             cp.d_sin[k] = float(d_sin[k])
             cp.d_cos[k] = float(d_cos[k])
         cp.K = float(K)
+        cp.K2 = float(K2)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
                            int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging])
         om = None

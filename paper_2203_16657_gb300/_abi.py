@@ -20,7 +20,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
-MODEL = {"kuramoto": 0}
+MODEL = {"kuramoto": 0, "kuramoto_ho": 1}
 
 
 class CiaError(RuntimeError):
@@ -38,7 +38,7 @@ class Coupling(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("p", ctypes.c_int),
                 ("d_sin", ctypes.c_double * CIA_MAX_HARMONICS),
                 ("d_cos", ctypes.c_double * CIA_MAX_HARMONICS),
-                ("K", ctypes.c_double)]
+                ("K", ctypes.c_double), ("K2", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):

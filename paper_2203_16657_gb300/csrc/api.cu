@@ -38,6 +38,10 @@ cia_status check_plan(cia_plan *pl, int method) {
     const size_t need = (method == CIA_METHOD_CIA && pl->staging == 0)
                             ? pipeline_smem_bytes(pl, pl->ring_stages)
                             : stage_smem_bytes(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA);
+    if (method == CIA_METHOD_DIRECT && pl->triadic &&
+        (size_t)(pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->max_comm > (size_t)optin - 1024)
+        return fail(CIA_ERR_UNSUPPORTED, "the direct triadic term stages a whole community in shared memory; "
+                                         "community too large");
     if (need > (size_t)optin - 1024)
         return fail(CIA_ERR_UNSUPPORTED, "largest community (" + std::to_string(pl->max_comm) +
                                              " nodes) does not fit the shared-memory community tile");

@@ -76,6 +76,7 @@ struct DeviceBuffers {
     void *wdt_full = nullptr;           // [n] wrap(dt omega), compute precision
     double *wdt_full64 = nullptr;       // [n] wrap(dt omega), FP64
     double *rhs_tmp = nullptr;          // [n] staging for host-buffer calls
+    void *tri = nullptr;                // [n] triadic term by the direct method (higher-order model)
     double *x_tmp = nullptr;            // [n] staging for host-buffer calls
     int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up
     double *r_tmp = nullptr;            // [r_cap] staging for order parameters
@@ -95,6 +96,8 @@ struct cia_plan {
     double d_sin[CIA_MAX_HARMONICS] = {0};
     double d_cos[CIA_MAX_HARMONICS] = {0};
     double K = 0.0;
+    double K2 = 0.0;                    // triadic coupling (higher-order model)
+    bool triadic = false;               // higher-order model: Z_1 and Z_2 are carried (p >= 2)
     int tile_nodes = 256;
     int group_size = 8;                 // threads per row, CIA sparse sums
     int group_size_direct = 32;         // threads per row, direct sums

@@ -60,6 +60,19 @@ __device__ __forceinline__ void phasors(T y, typename Vec2<T>::type (&u)[P]) {
         u[k] = mk2(u[k - 1].x * c - u[k - 1].y * s, u[k - 1].x * s + u[k - 1].y * c);
 }
 
+// Triadic term of the higher-order model (App. A.7, lambda = (1, 1, -2)) on
+// the complete community hyperedges, from the community moments: with
+// w1 = Z_1 - u_1 and w2 = Z_2 - u_2 (the node itself removed), the ordered
+// pairs j != k of the other members sum to w1^2 - w2, so the term is
+// Im((w1^2 - w2) conj(u_2)).
+template <typename T>
+__device__ __forceinline__ T triadic_from_moments(T z1r, T z1i, T z2r, T z2i, T u1r, T u1i, T u2r, T u2i) {
+    const T w1r = z1r - u1r, w1i = z1i - u1i;
+    const T qr = w1r * w1r - w1i * w1i - (z2r - u2r);
+    const T qi = T(2) * w1r * w1i - (z2i - u2i);
+    return qi * u2r - qr * u2i;
+}
+
 // ---- Blackwell bulk-copy (TMA) and mbarrier primitives, inline PTX ---------
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -159,6 +172,8 @@ struct StageParams {
     int tile_nodes;
     T d_sin[CIA_MAX_HARMONICS], d_cos[CIA_MAX_HARMONICS];
     T k_over_n;                // K / N
+    T k2_over_n2;              // K2 / N^2 (higher-order model; 0 otherwise)
+    const T *tri;              // direct method, higher-order model: triadic term per node
     const int64_t *off;
     const int32_t *tile_comm, *tile_first, *tile_count, *comm_tile_begin;
     // CIA: sliced-ELL sparse remainder, one blob per tile
@@ -241,9 +256,11 @@ __device__ __forceinline__ void finalize_tile(const StageParams<T> &a, int t, in
     for (int r = threadIdx.x; r < count; r += kThreads) {
         const int64_t m = first + r;
         T coup = T(0);
+        C uk[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const C u = own(k, m);
+            uk[k] = u;
             const C wv = sW[k * a.tile_nodes + r];
             T zr = wv.x, zi = wv.y;
             if (dense) {
@@ -257,6 +274,10 @@ __device__ __forceinline__ void finalize_tile(const StageParams<T> &a, int t, in
             coup += a.d_sin[k] * im + a.d_cos[k] * re;
         }
         coup *= a.k_over_n;
+        if (P >= 2 && dense && a.k2_over_n2 != T(0))
+            coup += a.k2_over_n2 * triadic_from_moments<T>(zc[0].x, zc[0].y, zc[P >= 2 ? 1 : 0].x, zc[P >= 2 ? 1 : 0].y,
+                                                           uk[0].x, uk[0].y, uk[P >= 2 ? 1 : 0].x, uk[P >= 2 ? 1 : 0].y);
+        if (a.tri) coup += a.tri[m];
         if (MODE == kRhs) {
             a.rhs_out[a.perm[m]] = (double)a.omega[m] + (double)coup;
         } else {
@@ -805,9 +826,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
         if (live) {
             const uint32_t vt = sWv[b * kConsumers + r];
             T coup = T(0);
+            C uk[P];
 #pragma unroll
             for (int kk = 0; kk < P; ++kk) {
                 const C uu = dense ? cph[kk * a.ph_region + (int)(m - h.lo)] : __ldg(a.ph_in + kk * stride + m);
+                uk[kk] = uu;
                 const C wi = sWi[kk * kConsumers + r];
                 T zr = wi.x, zi = wi.y;
                 for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
@@ -826,6 +849,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                 coup += a.d_sin[kk] * im + a.d_cos[kk] * re;
             }
             coup *= a.k_over_n;
+            if (P >= 2 && dense && a.k2_over_n2 != T(0)) {
+                const C z1 = zrun[(size_t)h.run * P], z2 = zrun[(size_t)h.run * P + (P >= 2 ? 1 : 0)];
+                coup += a.k2_over_n2 * triadic_from_moments<T>(z1.x, z1.y, z2.x, z2.y, uk[0].x, uk[0].y,
+                                                               uk[P >= 2 ? 1 : 0].x, uk[P >= 2 ? 1 : 0].y);
+            }
             if (MODE == kRhs) {
                 a.rhs_out[perm_m] = (double)omega_m + (double)coup;
             } else {
@@ -1007,6 +1035,51 @@ __global__ void scatter_master_kernel(int64_t n, const int32_t *perm, const doub
         x[perm[m]] = theta[m];
 }
 
+// Direct evaluation of the triadic term (higher-order model): for node m of
+// community c, the plain double sum over ordered pairs of distinct other
+// members, S_m = sum_{j != m} sum_{k != m, j} u_j u_k, then
+// tri_m = (K2/N^2) Im(S_m conj(u_m)^2).  O(lambda^2) per node.  One block per
+// tile; the community's phasors are staged in shared memory; each inner sum
+// over k is accumulated in T, the sum over j in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+triadic_direct_kernel(const int32_t *tile_comm, const int32_t *tile_first, const int32_t *tile_count,
+                      const int64_t *off, const typename Vec2<T>::type *u, T k2_over_n2, T *tri) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *cu = reinterpret_cast<C *>(smem_raw);
+    const int t = blockIdx.x;
+    const int comm = tile_comm[t], first = tile_first[t], count = tile_count[t];
+    if (comm < 0) {
+        for (int r = threadIdx.x; r < count; r += kThreads) tri[first + r] = T(0);
+        return;
+    }
+    const int64_t lo = off[comm];
+    const int lam = (int)(off[comm + 1] - lo);
+    for (int i = threadIdx.x; i < lam; i += kThreads) cu[i] = u[lo + i];
+    __syncthreads();
+    for (int r = threadIdx.x; r < count; r += kThreads) {
+        const int mloc = (int)(first + r - lo);
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < lam; ++j) {
+            if (j == mloc) continue;
+            T ir = T(0), ii = T(0);
+            for (int k = 0; k < lam; ++k) {
+                if (k == mloc || k == j) continue;
+                ir += cu[k].x;
+                ii += cu[k].y;
+            }
+            // u_j times the sum of u_k
+            sr += (double)(cu[j].x * ir - cu[j].y * ii);
+            si += (double)(cu[j].x * ii + cu[j].y * ir);
+        }
+        const C um = cu[mloc];
+        const T c2r = um.x * um.x - um.y * um.y, c2i = T(2) * um.x * um.y;   // u_m^2
+        // Im(S conj(u_m^2)) = si c2r - sr c2i
+        tri[first + r] = k2_over_n2 * (T)(si * (double)c2r - sr * (double)c2i);
+    }
+}
+
 template <typename T>
 StageParams<T> base_params(cia_plan *pl, int method) {
     StageParams<T> a{};
@@ -1019,6 +1092,8 @@ StageParams<T> base_params(cia_plan *pl, int method) {
         a.d_cos[k] = (T)pl->d_cos[k];
     }
     a.k_over_n = (T)(pl->K / (double)pl->n);
+    a.k2_over_n2 = (T)(pl->K2 / ((double)pl->n * (double)pl->n));
+    a.tri = (method == Method::DIRECT && pl->triadic) ? (const T *)pl->d.tri : nullptr;
     a.off = pl->d.off;
     a.tile_comm = pl->d.tile_comm;
     a.tile_first = pl->d.tile_first;
@@ -1085,6 +1160,22 @@ cudaError_t launch_direct_t(const cia_plan *pl, const StageParams<T> &a, cudaStr
 template <typename T, int MODE>
 cudaError_t dispatch_stage(cia_plan *pl, int method, const StageParams<T> &a, cudaStream_t s) {
     const bool direct = method == Method::DIRECT;
+    if (direct && pl->triadic) {
+        // the direct method's triadic term, pair by pair, before the stage
+        using C = typename Vec2<T>::type;
+        auto kernel = triadic_direct_kernel<T>;
+        static size_t cfg = 0;
+        const size_t smem = sizeof(C) * (size_t)std::max<int64_t>(1, pl->max_comm);
+        if (smem > 48 * 1024 && smem > cfg) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            cfg = smem;
+        }
+        kernel<<<(unsigned)pl->n_tiles, kThreads, smem, s>>>(pl->d.tile_comm, pl->d.tile_first, pl->d.tile_count,
+                                                            pl->d.off, a.ph_in, a.k2_over_n2, (T *)pl->d.tri);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
 #define CIA_CASE(P)                                                                   \
     case P:                                                                           \
         return direct ? launch_direct_t<T, P, MODE>(pl, a, s) : launch_cia_t<T, P, MODE>(pl, a, s);

@@ -296,19 +296,26 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
     if (pl->staging != 0 && pl->staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
-    if (cp->model != CIA_MODEL_KURAMOTO) return fail(CIA_ERR_UNSUPPORTED, "unknown model");
+    if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO)
+        return fail(CIA_ERR_UNSUPPORTED, "unknown model");
     if (cp->p < 1 || cp->p > CIA_MAX_HARMONICS)
         return fail(CIA_ERR_INVALID_ARG, "p must be in [1, CIA_MAX_HARMONICS]");
     pl->model = cp->model;
-    pl->p = cp->p;
+    pl->triadic = cp->model == CIA_MODEL_KURAMOTO_HO;
+    // the higher-order model needs the second-harmonic moments Z_2: carry at
+    // least two harmonics (extra ones with zero coefficients)
+    pl->p = pl->triadic ? std::max(cp->p, 2) : cp->p;
     pl->K = cp->K;
+    pl->K2 = pl->triadic ? cp->K2 : 0.0;
     if (!std::isfinite(cp->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
+    if (pl->triadic && !std::isfinite(cp->K2)) return fail(CIA_ERR_NUMERIC, "K2 is not finite");
     for (int k = 0; k < cp->p; ++k) {
         if (!std::isfinite(cp->d_sin[k]) || !std::isfinite(cp->d_cos[k]))
             return fail(CIA_ERR_NUMERIC, "coupling coefficient is not finite");
         pl->d_sin[k] = cp->d_sin[k];
         pl->d_cos[k] = cp->d_cos[k];
     }
+    for (int k = cp->p; k < CIA_MAX_HARMONICS; ++k) pl->d_sin[k] = pl->d_cos[k] = 0.0;
     if (omega)
         for (int64_t i = 0; i < n; ++i)
             if (!std::isfinite(omega[i]))
@@ -571,6 +578,7 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, n)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, n)) != CIA_OK) return s2;
     if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
+    if (pl->triadic && pl->has_direct && (s2 = alloc_bytes(pl, &d.tri, n * rb)) != CIA_OK) return s2;
     // The persistent TMA pipeline needs at most 256 nodes per tile (one
     // consumer thread per node) and, in shared memory, the CTA's tile
     // descriptors and observables plus a ring of at least two tile buffers
