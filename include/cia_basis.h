@@ -1,0 +1,110 @@
+/*
+ * cia_basis.h -- learned separable coupling basis for the Cucker--Smale model.
+ *
+ * Step P2 of the CIA (Sec. 3.2, App. A.6) expands the coupling weight in a
+ * basis that separates the two agents: the paper uses the Fourier modes
+ * e^{i pi <alpha, s>/L} of the Cucker--Smale weight
+ *     eta(||s_l - s_m||^2) = K (sigma^2 + ||s_l - s_m||^2)^-beta
+ * (eq. Cucker_Smale_etaExpansion).  This library replaces the Fourier modes
+ * by a learned rank-R feature map,
+ *     eta(||s_l - s_m||^2) ~ phi(s_l) . phi(s_m),
+ *     phi(x) = W2 silu(W1 x + b1) + b2,     x in R^2, phi(x) in R^R,
+ * a two-layer perceptron 2 -> 128 -> 64 evaluated with BF16 weights and
+ * activations on the tensor cores (FP32 accumulation).  The same features
+ * feed the community moments U_c, H_c (eq. Cucker_Smale_orderParams) and the
+ * dense evaluation (eq. Cucker_Smale_fast_RHS), so the approximate pair
+ * weight is symmetric and the CIA conserves momentum like the exact model.
+ * Positions enter phi relative to a point common to the community (its
+ * centroid), which leaves every pair difference unchanged.
+ *
+ * A basis object holds the FP32 master parameters and the Adam moments on
+ * the device.  Every evaluation rounds the parameters to BF16 first.
+ * Training minimises the mean squared pair loss
+ *     L = (1/B) sum_b (phi(a_b) . phi(c_b) - t_b)^2
+ * over pairs (a_b, c_b) of positions with target t_b = eta(||a_b - c_b||^2).
+ *
+ * Conventions of include/cia.h apply (status codes, stream, ownership).
+ */
+#ifndef CIA_BASIS_H
+#define CIA_BASIS_H
+
+#include "cia.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CIA_BASIS_IN 2
+#define CIA_BASIS_HIDDEN 128
+#define CIA_BASIS_RANK 64
+/* Packed parameter vector, FP32, in this order:
+ *   W1 [HIDDEN][IN] row-major, b1 [HIDDEN], W2 [RANK][HIDDEN] row-major, b2 [RANK]. */
+#define CIA_BASIS_PARAMS (CIA_BASIS_HIDDEN * CIA_BASIS_IN + CIA_BASIS_HIDDEN + \
+                          CIA_BASIS_RANK * CIA_BASIS_HIDDEN + CIA_BASIS_RANK)
+
+typedef struct cia_basis cia_basis_t;
+
+/* Adam (Kingma & Ba) on the FP32 master parameters. */
+typedef struct {
+    double lr;                  /* step size, e.g. 1e-3 */
+    double beta1, beta2;        /* moment decay rates, e.g. 0.9 and 0.999 */
+    double eps;                 /* e.g. 1e-8 */
+} cia_adam_options;
+
+typedef struct {
+    int64_t batch;              /* pairs per optimiser step, a multiple of 64 (e.g. 16384) */
+    int64_t epochs;             /* passes over the pair array */
+    cia_adam_options adam;
+} cia_fit_options;
+
+typedef struct {
+    int64_t steps;              /* optimiser steps taken */
+    double first_loss;          /* loss of the first batch (before its update) */
+    double last_epoch_loss;     /* mean batch loss over the last epoch */
+} cia_fit_report;
+
+/* Create a basis on the current device from host parameters (packed as
+ * above, CIA_BASIS_PARAMS floats); Adam moments start at zero. */
+cia_status cia_basis_create(const float *params, cia_basis_t **out);
+
+/* Release the basis (NULL is a no-op). */
+cia_status cia_basis_destroy(cia_basis_t *basis);
+
+/* Copy the FP32 master parameters to params (host, CIA_BASIS_PARAMS floats). */
+cia_status cia_basis_get_params(const cia_basis_t *basis, float *params);
+
+/* phi(x) for `count` inputs.  x: device, count x 2 floats; phi: device,
+ * count x RANK floats (row b = phi(x_b), before any rounding of the output).
+ * Hidden activations are rounded to BF16 before the second layer. */
+cia_status cia_basis_features(cia_basis_t *basis, const float *x, int64_t count, float *phi,
+                              void *stream);
+
+/* Gradient of the pair loss L over `count` pairs (count > 0, any size).
+ * pairs: device, count x 5 floats (a_x, a_y, c_x, c_y, t) per pair.
+ * grad: device, CIA_BASIS_PARAMS floats (same packing as the parameters).
+ * loss: device, one double (L of the evaluated model), or NULL.
+ * The backward products run on the tensor cores with BF16 operands. */
+cia_status cia_basis_pair_grad(cia_basis_t *basis, const float *pairs, int64_t count, float *grad,
+                               double *loss, void *stream);
+
+/* One Adam step on the master parameters with gradient grad (device,
+ * CIA_BASIS_PARAMS floats). */
+cia_status cia_basis_adam_step(cia_basis_t *basis, const float *grad, const cia_adam_options *opt,
+                               void *stream);
+
+/* Fit the basis to `count` pairs (device, layout of cia_basis_pair_grad):
+ * opt->epochs passes, each cutting the array into consecutive batches of
+ * opt->batch pairs (a last partial batch is used as it is), one Adam step per
+ * batch.  Synchronises the stream and fills *report (may be NULL). */
+cia_status cia_basis_fit(cia_basis_t *basis, const float *pairs, int64_t count,
+                         const cia_fit_options *opt, cia_fit_report *report, void *stream);
+
+/* Wait for the basis' work on `stream`; CIA_ERR_TIMEOUT (flag cleared) if a
+ * bounded tensor-core wait of its kernels gave up since the last check. */
+cia_status cia_basis_sync(cia_basis_t *basis, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CIA_BASIS_H */

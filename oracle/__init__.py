@@ -332,12 +332,13 @@ def angle_diff(a, b) -> np.ndarray:
 
 
 from .mlp import (mlp_forward, mlp_backward, pair_loss, pair_loss_grad,  # noqa: E402
-                  silu, silu_grad, cs_kernel_weight)
+                  silu, silu_grad, cs_kernel_weight, bf16_round, unpack_params, pack_params)
 
 __all__ = [
     "build", "num_threads", "set_num_threads", "Split", "split", "rebuild_b",
     "kuramoto_direct", "kuramoto_cia", "ho_triadic_direct", "ho_triadic_cia",
     "cs_direct", "cs_cia", "rk4_step", "euler_step", "wrap_phase", "order_parameter",
     "integrate", "angle_diff", "mlp_forward", "mlp_backward", "pair_loss",
-    "pair_loss_grad", "silu", "silu_grad", "cs_kernel_weight",
+    "pair_loss_grad", "silu", "silu_grad", "cs_kernel_weight", "bf16_round",
+    "unpack_params", "pack_params",
 ]

@@ -24,6 +24,32 @@ from __future__ import annotations
 import numpy as np
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 value, ties to even (the 8-bit-significand
+    format the tensor cores read), returned as float64.  Values are first
+    rounded to float32, as the device holds them."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unpack_params(vec) -> dict:
+    """Split a packed parameter vector (W1 [H, 2], b1 [H], W2 [R, H], b2 [R],
+    in that order, H = 128, R = 64) into arrays of float64."""
+    v = np.asarray(vec, dtype=np.float64)
+    H, R = 128, 64
+    o1 = 2 * H
+    o2 = o1 + H
+    o3 = o2 + R * H
+    assert v.shape == (o3 + R,)
+    return {"W1": v[:o1].reshape(H, 2), "b1": v[o1:o2], "W2": v[o2:o3].reshape(R, H),
+            "b2": v[o3:]}
+
+
+def pack_params(p: dict) -> np.ndarray:
+    return np.concatenate([p["W1"].reshape(-1), p["b1"], p["W2"].reshape(-1), p["b2"]])
+
+
 def silu(z):
     return z / (1.0 + np.exp(-z))
 

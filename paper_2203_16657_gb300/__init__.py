@@ -14,7 +14,7 @@ import numpy as np
 from . import _abi
 from ._abi import CiaError, load
 
-__all__ = ["Plan", "CiaError", "load", "status_string"]
+__all__ = ["Plan", "Basis", "CiaError", "load", "status_string"]
 
 
 def status_string(status: int) -> str:
@@ -190,3 +190,85 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Basis:
+    """Learned separable basis phi of the Cucker--Smale weight (include/cia_basis.h).
+
+    params: host float32 vector of CIA_BASIS_PARAMS entries packed as
+    W1 [128, 2], b1 [128], W2 [64, 128], b2 [64].
+    """
+
+    PARAMS = _abi.CIA_BASIS_PARAMS
+    HIDDEN = _abi.CIA_BASIS_HIDDEN
+    RANK = _abi.CIA_BASIS_RANK
+
+    def __init__(self, params):
+        lib = load()
+        self._lib = lib
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.shape != (self.PARAMS,):
+            raise ValueError("params must have %d entries" % self.PARAMS)
+        handle = ctypes.c_void_p()
+        _abi.check(lib.cia_basis_create(params.ctypes.data, ctypes.byref(handle)))
+        self._h = handle
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.PARAMS, dtype=np.float32)
+        _abi.check(self._lib.cia_basis_get_params(self._h, out.ctypes.data))
+        return out
+
+    def features(self, x, out=None, stream=None):
+        """phi(x) for x (CUDA float32, [B, 2]); returns [B, 64] float32."""
+        import torch
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, self.RANK), dtype=torch.float32, device=x.device)
+        _abi.check(self._lib.cia_basis_features(self._h, _dev_ptr(x, "float32", 2 * B), B,
+                                                _dev_ptr(out, "float32", self.RANK * B),
+                                                _stream_handle(stream)))
+        return out
+
+    def pair_grad(self, pairs, grad=None, loss=None, stream=None):
+        """Gradient of the mean squared pair loss over pairs (CUDA float32, [B, 5])."""
+        import torch
+        B = pairs.shape[0]
+        if grad is None:
+            grad = torch.empty(self.PARAMS, dtype=torch.float32, device=pairs.device)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=pairs.device)
+        _abi.check(self._lib.cia_basis_pair_grad(self._h, _dev_ptr(pairs, "float32", 5 * B), B,
+                                                 _dev_ptr(grad, "float32", self.PARAMS),
+                                                 _dev_ptr(loss, "float64", 1),
+                                                 _stream_handle(stream)))
+        return grad, loss
+
+    def adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        o = _abi.AdamOptions(lr, beta1, beta2, eps)
+        _abi.check(self._lib.cia_basis_adam_step(self._h, _dev_ptr(grad, "float32", self.PARAMS),
+                                                 ctypes.byref(o), _stream_handle(stream)))
+
+    def fit(self, pairs, batch=16384, epochs=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+            stream=None) -> dict:
+        B = pairs.shape[0]
+        o = _abi.FitOptions(int(batch), int(epochs), _abi.AdamOptions(lr, beta1, beta2, eps))
+        rep = _abi.FitReport()
+        _abi.check(self._lib.cia_basis_fit(self._h, _dev_ptr(pairs, "float32", 5 * B), B,
+                                           ctypes.byref(o), ctypes.byref(rep),
+                                           _stream_handle(stream)))
+        return {"steps": rep.steps, "first_loss": rep.first_loss,
+                "last_epoch_loss": rep.last_epoch_loss}
+
+    def sync(self, stream=None):
+        _abi.check(self._lib.cia_basis_sync(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cia_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

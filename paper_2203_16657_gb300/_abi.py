@@ -63,6 +63,25 @@ class Profile(ctypes.Structure):
                 ("other_launches", ctypes.c_int64)]
 
 
+CIA_BASIS_IN, CIA_BASIS_HIDDEN, CIA_BASIS_RANK = 2, 128, 64
+CIA_BASIS_PARAMS = (CIA_BASIS_HIDDEN * CIA_BASIS_IN + CIA_BASIS_HIDDEN
+                    + CIA_BASIS_RANK * CIA_BASIS_HIDDEN + CIA_BASIS_RANK)
+
+
+class AdamOptions(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class FitOptions(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int64), ("adam", AdamOptions)]
+
+
+class FitReport(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("first_loss", ctypes.c_double),
+                ("last_epoch_loss", ctypes.c_double)]
+
+
 # exported symbol -> (restype, argtypes)
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -87,6 +106,16 @@ SIGNATURES = {
     "cia_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cia_rhs_kuramoto_static": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                                _P, _P, ctypes.POINTER(Coupling), _P, _P]),
+    # include/cia_basis.h
+    "cia_basis_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "cia_basis_destroy": (ctypes.c_int, [_P]),
+    "cia_basis_get_params": (ctypes.c_int, [_P, _P]),
+    "cia_basis_features": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cia_basis_pair_grad": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "cia_basis_adam_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(AdamOptions), _P]),
+    "cia_basis_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(FitOptions),
+                                     ctypes.POINTER(FitReport), _P]),
+    "cia_basis_sync": (ctypes.c_int, [_P, _P]),
 }
 
 _lib = None

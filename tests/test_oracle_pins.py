@@ -298,3 +298,28 @@ def test_mlp_gradient_central_differences(oracle_mod):
             flat[idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - grads[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), (k, idx)
+
+
+def test_bf16_round_ties_to_even(oracle_mod):
+    """bfloat16 keeps 8 significand bits: the spacing at 1 is 2^-7.  Halfway
+    cases go to the even neighbour; other values to the nearest."""
+    r = oracle_mod.bf16_round
+    cases = [(1.0, 1.0), (1.0 + 2.0 ** -8, 1.0), (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6),
+             (1.0 + 2.0 ** -7, 1.0 + 2.0 ** -7), (1.0 + 1.1 * 2.0 ** -8, 1.0 + 2.0 ** -7),
+             (-3.0 - 2.0 ** -7, -3.0), (0.0, 0.0), (2.0 ** -130, 2.0 ** -130)]
+    for x, want in cases:
+        assert r(np.array([x]))[0] == want, (x, r(np.array([x]))[0], want)
+    v = np.random.default_rng(3).normal(size=1000) * 100
+    q = r(v)
+    # representable: low 16 bits of the float32 pattern are zero, and within half a spacing
+    assert not (q.astype(np.float32).view(np.uint32) & 0xFFFF).any()
+    assert (np.abs(q - v) <= np.abs(v) * 2.0 ** -8 + 1e-300).all()
+
+
+def test_param_packing_round_trip(oracle_mod):
+    rng = np.random.default_rng(4)
+    vec = rng.normal(size=128 * 2 + 128 + 64 * 128 + 64)
+    p = oracle_mod.unpack_params(vec)
+    assert p["W1"].shape == (128, 2) and p["W2"].shape == (64, 128)
+    assert p["W1"][5, 1] == vec[11] and p["b1"][0] == vec[256] and p["W2"][1, 0] == vec[384 + 128]
+    np.testing.assert_array_equal(oracle_mod.pack_params(p), vec)
