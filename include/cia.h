@@ -19,7 +19,9 @@
  *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
  *    global memory of the device that was current when the plan was made.
  *  - State at the boundary is always FP64 in the ORIGINAL node numbering of
- *    the graph.  The compute precision inside is the plan's (cia_options).
+ *    the graph, d values per node (d = 1 for the Kuramoto models: theta_m;
+ *    d = 4 for Cucker--Smale: s_x, s_y, v_x, v_y, node-major).  The compute
+ *    precision inside is the plan's (cia_options).
  *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Device work is asynchronous on that stream; an asynchronous CUDA error
  *    surfaces as CIA_ERR_CUDA from a later call on the same plan.
@@ -51,7 +53,8 @@ typedef enum {
 
 typedef enum {
     CIA_MODEL_KURAMOTO = 0,     /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
-    CIA_MODEL_KURAMOTO_HO = 1   /* the same plus a triadic term on complete community hyperedges (App. A.7) */
+    CIA_MODEL_KURAMOTO_HO = 1,  /* the same plus a triadic term on complete community hyperedges (App. A.7) */
+    CIA_MODEL_CUCKER_SMALE = 2  /* 2-D flocking agents (App. A.6), state (s_x, s_y, v_x, v_y) per node */
 } cia_model;
 
 typedef enum {
@@ -85,7 +88,15 @@ typedef struct {
  *   (K2/N^2) sum_{j != k; j, k in c, both != m} sin(theta_j + theta_k - 2 theta_m);
  * nodes in no community get no triadic term.  The CIA evaluates it from the
  * community moments Z_1, Z_2 (eq. HOKuramoto_fastRHS with the tuples that
- * repeat an index removed); the direct method sums the pairs one by one. */
+ * repeat an index removed); the direct method sums the pairs one by one.
+ * CIA_MODEL_CUCKER_SMALE (App. A.6, eq. Cucker_Smale, n = 2): per node the
+ * state is x_m = (s_m, v_m), position and velocity in R^2, and
+ *   s_m' = v_m,   v_m' = (1/N) sum_l a_ml eta(||s_l - s_m||^2) (v_l - v_m),
+ *   eta(y) = K (sigma^2 + y)^-beta.
+ * Its CIA needs a separable basis of eta (step P2): a learned feature map set
+ * with cia_plan_set_basis (include/cia_basis.h).  The links of S (missing and
+ * inter-community) are summed with the exact eta.  FP32 only; p, d_sin,
+ * d_cos and K2 are ignored. */
 typedef struct {
     int model;                  /* cia_model */
     int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
@@ -93,12 +104,14 @@ typedef struct {
     double d_cos[CIA_MAX_HARMONICS];
     double K;                   /* coupling constant multiplying (1/N) sum */
     double K2;                  /* triadic coupling (CIA_MODEL_KURAMOTO_HO), multiplies (1/N^2) sum */
+    double sigma, beta;         /* Cucker--Smale weight eta(y) = K (sigma^2 + y)^-beta, sigma > 0 */
 } cia_coupling;
 
 typedef struct {
     int precision;              /* cia_precision */
     int build_direct;           /* nonzero: also keep the full CSR on the device (CIA_METHOD_DIRECT) */
-    int tile_nodes;             /* nodes per work tile, 0 = default (256); a multiple of 32, <= 1024 */
+    int tile_nodes;             /* nodes per work tile, 0 = default (256; 128 for Cucker--Smale);
+                                   a multiple of 32, <= 1024 (<= 128 for Cucker--Smale) */
     int group_size;             /* threads per row of the direct method's CSR sums: 0 = default,
                                    else 4, 8, 16 or 32 (the CIA sums use one thread per row) */
     int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (32768); a multiple of 16.
@@ -127,6 +140,8 @@ typedef struct {
     int staging;                /* 0 = TMA bulk staging in use, 1 = plain loads */
     int group_size_direct;      /* threads per row of the direct method */
     int64_t max_tile_index_bytes; /* largest sparse-index footprint of a tile */
+    int model;                  /* cia_model */
+    int state_dim;              /* d: FP64 values per node at the boundary */
 } cia_plan_info;
 
 /* ---- status -------------------------------------------------------------- */
@@ -147,7 +162,7 @@ const char *cia_last_error(void);
  *   Sec. 3.1): all its links are then treated as sparse extra links.
  *   Labels need not be contiguous in i; M = max label + 1 (empty labels allowed).
  * omega: host, g->n natural frequencies f_m = omega_m (NULL = all zero).
- *   With CIA_FP32 they are rounded to FP32.
+ *   With CIA_FP32 they are rounded to FP32.  Must be NULL for Cucker--Smale.
  * The plan computes the permutation kappa that sorts nodes by (label, id)
  * with unlabelled nodes last, the community offsets, and the two halves of S:
  *   missing links inside each block (the -1 entries of S without the
@@ -186,7 +201,11 @@ cia_status cia_plan_get_split(const cia_plan_t *plan, int64_t *miss_rowptr, int3
 /* One right-hand-side evaluation dxdt = H(x) with the CIA:
  * (E1) per-community observables Z_{c,k} = sum_{l in c} e^{i k x_l} and the
  * dense term from them (eq. FastHdense), (E2) the sparse sum over S, plus f.
- * x, dxdt: device, n doubles each, original node order; they may not alias.
+ * x, dxdt: device, n x d doubles each, original node order; they may not alias.
+ * Cucker--Smale: needs a basis (cia_plan_set_basis); the dense term is
+ *   sum_r phi_r(s_m) (H_cr - U_cr v_m) with U_c = (1/N) sum_{l in c} phi(s_l),
+ *   H_c = (1/N) sum_{l in c} phi(s_l) v_l (eqs. Cucker_Smale_orderParams and
+ *   Cucker_Smale_fast_RHS), positions relative to the community centroid.
  * With CIA_FP32 the state is rounded to FP32 and all sums run in FP32
  * (per-community observables with FP64 accumulation across tiles). */
 cia_status cia_rhs(cia_plan_t *plan, const double *x, double *dxdt, void *stream);
@@ -197,16 +216,20 @@ cia_status cia_rhs_direct(cia_plan_t *plan, const double *x, double *dxdt, void 
 
 /* Advance x by nsteps classical RK4 steps of size dt (the paper allows any
  * Runge-Kutta method, Sec. 3), evaluating every stage with `method`.
- * x: device, n doubles, original order, in/out; returned wrapped to
- *   [-pi, pi].  Time accumulation theta += dt sum_s b_s k_s is FP64 in both
+ * x: device, n x d doubles, original order, in/out; Kuramoto phases are
+ *   returned wrapped to [-pi, pi].  Time accumulation theta += dt sum_s b_s k_s is FP64 in both
  *   precisions; stage states are in the plan's precision.
  * r_out: device, nsteps doubles or NULL; r_out[j] = |(1/N) sum_l e^{i x_l}|
- *   after step j+1 (the Kuramoto order parameter, eq. KuramotoFirstOP).
- * nsteps = 0 only round-trips x through the wrap. */
+ *   after step j+1 (the Kuramoto order parameter, eq. KuramotoFirstOP);
+ *   must be NULL for Cucker--Smale.
+ * nsteps = 0 only round-trips x through the wrap.
+ * Cucker--Smale with method CIA and an error check set (cia_plan_set_check):
+ * if a check fails, the remaining steps use the direct method and the call
+ * returns CIA_ERR_FALLBACK after completing them (x is valid). */
 cia_status cia_integrate(cia_plan_t *plan, int method, double *x, double dt, int64_t nsteps,
                          double *r_out, void *stream);
 
-/* cia_integrate with HOST buffers: copies x (n doubles) to the device, runs,
+/* cia_integrate with HOST buffers: copies x (n x d doubles) to the device, runs,
  * copies x and, if r_out_host is not NULL, nsteps order parameters back, and
  * synchronises the stream.  Pinned host memory makes the copies asynchronous. */
 cia_status cia_integrate_host(cia_plan_t *plan, int method, double *x_host, double dt,
@@ -214,12 +237,13 @@ cia_status cia_integrate_host(cia_plan_t *plan, int method, double *x_host, doub
 
 /* ---- resident state: the pieces cia_integrate is made of ------------------ */
 
-/* Load x (device, n doubles, original order) into the plan's resident FP64
- * master state (permuted, wrapped to [-pi, pi]) and compute the observables
- * of that state.  Until the next load the plan owns the state. */
+/* Load x (device, n x d doubles, original order) into the plan's resident
+ * FP64 master state (permuted; Kuramoto phases wrapped to [-pi, pi]) and
+ * compute the observables of that state.  Until the next load the plan owns
+ * the state. */
 cia_status cia_state_load(cia_plan_t *plan, const double *x, void *stream);
 
-/* Copy the resident master state to x (device, n doubles, original order). */
+/* Copy the resident master state to x (device, n x d doubles, original order). */
 cia_status cia_state_store(cia_plan_t *plan, double *x, void *stream);
 
 /* Advance the resident state by nsteps RK4 steps of size dt (see

@@ -99,6 +99,68 @@ cia_status cia_basis_adam_step(cia_basis_t *basis, const float *grad, const cia_
 cia_status cia_basis_fit(cia_basis_t *basis, const float *pairs, int64_t count,
                          const cia_fit_options *opt, cia_fit_report *report, void *stream);
 
+/* ---- the basis inside a Cucker--Smale plan -------------------------------- */
+
+/* Use the basis' current parameters (copied, rounded to BF16 on use) for the
+ * plan's CIA.  Resets the plan's check state.  The copy is ordered after all
+ * work issued to the basis on the legacy default stream; synchronise other
+ * streams first. */
+cia_status cia_plan_set_basis(cia_plan_t *plan, const cia_basis_t *basis);
+
+/* Draw `count` training pairs (layout of cia_basis_pair_grad) from the plan's
+ * resident state: node i uniform over the nodes that belong to a community,
+ * partner l uniform over the other nodes of i's community, positions relative
+ * to that community's centroid, target t = eta(||s_i - s_l||^2) with the
+ * plan's K, sigma, beta.  The generator is SplitMix64 (Steele, Lea and Flood
+ * 2014) on the counter seed + 2q (+1).  pairs: device, count x 5 floats. */
+cia_status cia_plan_sample_pairs(cia_plan_t *plan, int64_t count, uint64_t seed, float *pairs,
+                                 void *stream);
+
+/* Sampled check of the learned basis during cia_advance / cia_integrate with
+ * the CIA (needs opt.build_direct): before step 0 and every `every` steps,
+ * for up to 512 fixed community nodes m (evenly spaced in the permuted order)
+ *   err = max_m |dense_m - (1/N) sum_{l in c(m), l != m} eta (v_l - v_m)|,
+ *   ref = max_m |(1/N) sum_{l in N(m)} eta (v_l - v_m)|      (max over both components),
+ * the first being exactly the CIA's deviation from the direct right-hand side
+ * (its sparse corrections are exact).  If err > bound * ref the remaining
+ * steps, and later calls, use the direct method (cia_plan_set_check or
+ * cia_plan_set_basis re-arms the CIA).  every = 0 turns the check off. */
+cia_status cia_plan_set_check(cia_plan_t *plan, int64_t every, double bound);
+
+typedef struct {
+    int64_t checks;             /* checks run since the last set_check / set_basis */
+    double last_error;          /* err / ref of the last check */
+    double max_error;           /* largest err / ref */
+    int fell_back;              /* nonzero once a check failed */
+    int64_t fallback_step;      /* step (within the call that failed) at which it failed, -1 if none */
+} cia_check_report;
+
+cia_status cia_plan_get_check(const cia_plan_t *plan, cia_check_report *report);
+
+typedef struct {
+    double dt;                  /* step of the direct RK4 trajectory */
+    int64_t steps;              /* its length in steps */
+    int64_t snapshots;          /* states where pairs are drawn: steps 0, steps/snapshots, ... */
+    int64_t pairs;              /* pairs in total, split evenly over the snapshots */
+    uint64_t seed;
+    cia_fit_options fit;
+} cia_learn_options;
+
+typedef struct {
+    int64_t pairs;              /* pairs drawn */
+    cia_fit_report fit;
+} cia_learn_report;
+
+/* Learn the basis from the dynamics themselves: load x0 (device, n x 4
+ * doubles, original order), integrate it with the DIRECT method (needs
+ * opt.build_direct) for opt->steps RK4 steps of opt->dt, drawing
+ * opt->pairs / opt->snapshots pairs (cia_plan_sample_pairs) at each snapshot,
+ * fit the basis to all of them (cia_basis_fit) and set it as the plan's basis.
+ * The plan's resident state is left at the end of the trajectory.
+ * Synchronises the stream; *report may be NULL. */
+cia_status cia_learn_fit(cia_plan_t *plan, cia_basis_t *basis, const double *x0,
+                         const cia_learn_options *opt, cia_learn_report *report, void *stream);
+
 /* Wait for the basis' work on `stream`; CIA_ERR_TIMEOUT (flag cleared) if a
  * bounded tensor-core wait of its kernels gave up since the last check. */
 cia_status cia_basis_sync(cia_basis_t *basis, void *stream);

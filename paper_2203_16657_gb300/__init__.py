@@ -44,11 +44,14 @@ class Plan:
     (-1 = no community), omega: natural frequencies (host float64).
     Coupling h(x) = sum_k d_sin[k] sin((k+1)x) + d_cos[k] cos((k+1)x), scaled by K/N;
     model="kuramoto_ho" adds the triadic term on community hyperedges, scaled by K2/N^2.
+    model="cucker_smale": state [n, 4] = (s_x, s_y, v_x, v_y) per node, weight
+    eta(y) = K (sigma^2 + y)^-beta; the CIA needs a basis (set_basis / learn_fit).
     """
 
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
-                 tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0):
+                 tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0, sigma=1.0,
+                 beta=0.0):
         lib = load()
         self._lib = lib
         self._keep = []
@@ -73,6 +76,8 @@ class Plan:
             cp.d_cos[k] = float(d_cos[k])
         cp.K = float(K)
         cp.K2 = float(K2)
+        cp.sigma = float(sigma)
+        cp.beta = float(beta)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
                            int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging])
         om = None
@@ -87,6 +92,8 @@ class Plan:
         self._h = handle
         self.n = n
         self.precision = precision
+        self.dim = 4 if model == "cucker_smale" else 1
+        self.size = n * self.dim
 
     # ------------------------------------------------------------ bookkeeping
     def info(self) -> dict:
@@ -119,48 +126,92 @@ class Plan:
         if out is None:
             out = torch.empty_like(x)
         fn = self._lib.cia_rhs if method == "cia" else self._lib.cia_rhs_direct
-        _abi.check(fn(self._h, _dev_ptr(x, "float64", self.n), _dev_ptr(out, "float64", self.n),
+        _abi.check(fn(self._h, _dev_ptr(x, "float64", self.size), _dev_ptr(out, "float64", self.size),
                       _stream_handle(stream)))
         return out
 
     def integrate(self, x, dt, steps, method="cia", r_out=None, stream=None):
         """Advance x (CUDA float64, original order) in place by `steps` RK4 steps."""
         rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
-        _abi.check(self._lib.cia_integrate(self._h, _abi.METHOD[method],
-                                           _dev_ptr(x, "float64", self.n), float(dt), int(steps),
-                                           rp, _stream_handle(stream)))
+        st = self._lib.cia_integrate(self._h, _abi.METHOD[method],
+                                     _dev_ptr(x, "float64", self.size), float(dt), int(steps),
+                                     rp, _stream_handle(stream))
+        self._status(st)
         return x
 
     def integrate_host(self, x: np.ndarray, dt, steps, method="cia", r_out=None, stream=None):
         """Host-buffer integration (copies inside the call); x is updated in place."""
-        if x.dtype != np.float64 or not x.flags.c_contiguous or len(x) != self.n:
-            raise ValueError("x must be a contiguous float64 array of n entries")
+        if x.dtype != np.float64 or not x.flags.c_contiguous or x.size != self.size:
+            raise ValueError("x must be a contiguous float64 array of n x d entries")
         rp = None
         if r_out is not None:
             if r_out.dtype != np.float64 or len(r_out) != steps:
                 raise ValueError("r_out must be float64 with `steps` entries")
             rp = r_out.ctypes.data
-        _abi.check(self._lib.cia_integrate_host(self._h, _abi.METHOD[method], x.ctypes.data,
-                                                float(dt), int(steps), rp,
-                                                _stream_handle(stream)))
+        self._status(self._lib.cia_integrate_host(self._h, _abi.METHOD[method], x.ctypes.data,
+                                                  float(dt), int(steps), rp,
+                                                  _stream_handle(stream)))
         return x
 
     def state_load(self, x, stream=None):
         """Make x (CUDA float64, original order) the resident state."""
-        _abi.check(self._lib.cia_state_load(self._h, _dev_ptr(x, "float64", self.n),
+        _abi.check(self._lib.cia_state_load(self._h, _dev_ptr(x, "float64", self.size),
                                             _stream_handle(stream)))
 
     def state_store(self, x, stream=None):
         """Copy the resident state into x (CUDA float64, original order)."""
-        _abi.check(self._lib.cia_state_store(self._h, _dev_ptr(x, "float64", self.n),
+        _abi.check(self._lib.cia_state_store(self._h, _dev_ptr(x, "float64", self.size),
                                              _stream_handle(stream)))
         return x
 
     def advance(self, dt, steps, method="cia", r_out=None, stream=None):
         """Advance the resident state by `steps` RK4 steps."""
         rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
-        _abi.check(self._lib.cia_advance(self._h, _abi.METHOD[method], float(dt), int(steps), rp,
-                                         _stream_handle(stream)))
+        self._status(self._lib.cia_advance(self._h, _abi.METHOD[method], float(dt), int(steps), rp,
+                                           _stream_handle(stream)))
+
+    def _status(self, st):
+        """CIA_ERR_FALLBACK is informational: the results are valid and the
+        check report says what happened; every other error raises."""
+        if st == 6:
+            self.last_fallback = load().cia_last_error().decode(errors="replace")
+            return
+        _abi.check(st)
+
+    # ------------------------------------------------------------ learned basis (Cucker--Smale)
+    def set_basis(self, basis: "Basis"):
+        _abi.check(self._lib.cia_plan_set_basis(self._h, basis._h))
+
+    def sample_pairs(self, count, seed=0, out=None, stream=None):
+        """Training pairs [count, 5] drawn from the resident state."""
+        import torch
+        if out is None:
+            out = torch.empty((int(count), 5), dtype=torch.float32, device="cuda")
+        _abi.check(self._lib.cia_plan_sample_pairs(self._h, int(count), int(seed),
+                                                   _dev_ptr(out, "float32", 5 * int(count)),
+                                                   _stream_handle(stream)))
+        return out
+
+    def set_check(self, every, bound):
+        _abi.check(self._lib.cia_plan_set_check(self._h, int(every), float(bound)))
+
+    def check_report(self) -> dict:
+        r = _abi.CheckReport()
+        _abi.check(self._lib.cia_plan_get_check(self._h, ctypes.byref(r)))
+        return {name: getattr(r, name) for name, _ in _abi.CheckReport._fields_}
+
+    def learn_fit(self, basis: "Basis", x0, *, dt, steps, snapshots, pairs, seed=0,
+                  batch=16384, epochs=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  stream=None) -> dict:
+        o = _abi.LearnOptions(float(dt), int(steps), int(snapshots), int(pairs), int(seed),
+                              _abi.FitOptions(int(batch), int(epochs),
+                                              _abi.AdamOptions(lr, beta1, beta2, eps)))
+        rep = _abi.LearnReport()
+        _abi.check(self._lib.cia_learn_fit(self._h, basis._h, _dev_ptr(x0, "float64", self.size),
+                                           ctypes.byref(o), ctypes.byref(rep),
+                                           _stream_handle(stream)))
+        return {"pairs": rep.pairs, "steps": rep.fit.steps, "first_loss": rep.fit.first_loss,
+                "last_epoch_loss": rep.fit.last_epoch_loss}
 
     def profile_begin(self, capacity: int):
         _abi.check(self._lib.cia_profile_begin(self._h, int(capacity)))

@@ -20,7 +20,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
-MODEL = {"kuramoto": 0, "kuramoto_ho": 1}
+MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2}
 
 
 class CiaError(RuntimeError):
@@ -38,7 +38,8 @@ class Coupling(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("p", ctypes.c_int),
                 ("d_sin", ctypes.c_double * CIA_MAX_HARMONICS),
                 ("d_cos", ctypes.c_double * CIA_MAX_HARMONICS),
-                ("K", ctypes.c_double), ("K2", ctypes.c_double)]
+                ("K", ctypes.c_double), ("K2", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -55,7 +56,8 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("group_size", ctypes.c_int),
                 ("tile_nodes", ctypes.c_int), ("missing_index_bytes", ctypes.c_int),
                 ("staging", ctypes.c_int), ("group_size_direct", ctypes.c_int),
-                ("max_tile_index_bytes", ctypes.c_int64)]
+                ("max_tile_index_bytes", ctypes.c_int64), ("model", ctypes.c_int),
+                ("state_dim", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -80,6 +82,21 @@ class FitOptions(ctypes.Structure):
 class FitReport(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("first_loss", ctypes.c_double),
                 ("last_epoch_loss", ctypes.c_double)]
+
+
+class CheckReport(ctypes.Structure):
+    _fields_ = [("checks", ctypes.c_int64), ("last_error", ctypes.c_double),
+                ("max_error", ctypes.c_double), ("fell_back", ctypes.c_int),
+                ("fallback_step", ctypes.c_int64)]
+
+
+class LearnOptions(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("steps", ctypes.c_int64), ("snapshots", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("seed", ctypes.c_uint64), ("fit", FitOptions)]
+
+
+class LearnReport(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("fit", FitReport)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -116,6 +133,12 @@ SIGNATURES = {
     "cia_basis_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(FitOptions),
                                      ctypes.POINTER(FitReport), _P]),
     "cia_basis_sync": (ctypes.c_int, [_P, _P]),
+    "cia_plan_set_basis": (ctypes.c_int, [_P, _P]),
+    "cia_plan_sample_pairs": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
+    "cia_plan_set_check": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    "cia_plan_get_check": (ctypes.c_int, [_P, ctypes.POINTER(CheckReport)]),
+    "cia_learn_fit": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(LearnOptions),
+                                     ctypes.POINTER(LearnReport), _P]),
 }
 
 _lib = None

@@ -623,3 +623,118 @@ extern "C" cia_status cia_basis_sync(cia_basis_t *basis, void *stream) {
     }
     return CIA_OK;
 }
+
+// ---- the basis inside a Cucker--Smale plan -----------------------------------
+
+namespace {
+
+cia_status check_cs_plan(const cia_plan *pl) {
+    if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->model != CIA_MODEL_CUCKER_SMALE) return fail(CIA_ERR_INVALID_ARG, "not a Cucker-Smale plan");
+    int dev = -1;
+    CIA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(CIA_ERR_INVALID_ARG, "plan belongs to another device");
+    return CIA_OK;
+}
+
+void reset_check(cia_plan *pl) {
+    pl->checks = 0;
+    pl->check_last = pl->check_max = 0.0;
+    pl->fell_back = false;
+    pl->fallback_step = -1;
+}
+
+}  // namespace
+
+extern "C" cia_status cia_plan_set_basis(cia_plan_t *plan, const cia_basis_t *basis) {
+    clear_error();
+    cia_status st = check_cs_plan(plan);
+    if (st != CIA_OK) return st;
+    if ((st = check_basis(basis)) != CIA_OK) return st;
+    CIA_CUDA_TRY(cudaMemcpy(plan->d.cs_params, basis->params, kParams * sizeof(float), cudaMemcpyDeviceToDevice));
+    plan->cs_has_basis = true;
+    plan->cs_feat_valid = false;
+    reset_check(plan);
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_sample_pairs(cia_plan_t *plan, int64_t count, uint64_t seed, float *pairs,
+                                            void *stream) {
+    clear_error();
+    cia_status st = check_cs_plan(plan);
+    if (st != CIA_OK) return st;
+    if (count < 0) return fail(CIA_ERR_INVALID_ARG, "count < 0");
+    if (count == 0) return CIA_OK;
+    if (!pairs) return fail(CIA_ERR_INVALID_ARG, "pairs is NULL");
+    if (plan->M < 1 || plan->off[plan->M] < 1) return fail(CIA_ERR_INVALID_ARG, "the plan has no community nodes");
+    CIA_CUDA_TRY(cs_launch_sample(plan, plan->state_slot, count, seed, pairs, (cudaStream_t)stream));
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_set_check(cia_plan_t *plan, int64_t every, double bound) {
+    clear_error();
+    cia_status st = check_cs_plan(plan);
+    if (st != CIA_OK) return st;
+    if (every < 0) return fail(CIA_ERR_INVALID_ARG, "every < 0");
+    if (every > 0 && !(bound > 0.0 && std::isfinite(bound))) return fail(CIA_ERR_INVALID_ARG, "bound must be positive");
+    if (every > 0 && !plan->has_direct)
+        return fail(CIA_ERR_INVALID_ARG, "the check needs the direct method (build_direct)");
+    if (every > 0 && plan->cs_check_count < 1) return fail(CIA_ERR_INVALID_ARG, "the plan has no community nodes");
+    plan->check_every = every;
+    plan->check_bound = bound;
+    reset_check(plan);
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_get_check(const cia_plan_t *plan, cia_check_report *report) {
+    clear_error();
+    if (!plan || !report) return fail(CIA_ERR_INVALID_ARG, "plan or report is NULL");
+    report->checks = plan->checks;
+    report->last_error = plan->check_last;
+    report->max_error = plan->check_max;
+    report->fell_back = plan->fell_back ? 1 : 0;
+    report->fallback_step = plan->fallback_step;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_learn_fit(cia_plan_t *plan, cia_basis_t *basis, const double *x0,
+                                    const cia_learn_options *opt, cia_learn_report *report, void *stream) {
+    clear_error();
+    cia_status st = check_cs_plan(plan);
+    if (st != CIA_OK) return st;
+    if ((st = check_basis(basis)) != CIA_OK) return st;
+    if (!x0 || !opt) return fail(CIA_ERR_INVALID_ARG, "x0 or options are NULL");
+    if (!plan->has_direct) return fail(CIA_ERR_INVALID_ARG, "learning from trajectories needs build_direct");
+    if (opt->steps < 0 || opt->snapshots < 1 || opt->pairs < opt->snapshots || !std::isfinite(opt->dt))
+        return fail(CIA_ERR_INVALID_ARG, "need steps >= 0, snapshots >= 1, pairs >= snapshots and a finite dt");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t per = opt->pairs / opt->snapshots;
+    const int64_t total = per * opt->snapshots;
+    float *pairs = nullptr;
+    CIA_CUDA_TRY(cudaMalloc(&pairs, (size_t)total * 5 * sizeof(float)));
+    struct Free {
+        float *p;
+        ~Free() { cudaFree(p); }
+    } guard{pairs};
+    if ((st = cia_state_load(plan, x0, stream)) != CIA_OK) return st;
+    int64_t done = 0;
+    for (int64_t k = 0; k < opt->snapshots; ++k) {
+        st = cia_plan_sample_pairs(plan, per, opt->seed + (uint64_t)k * (1ull << 40), pairs + (size_t)k * per * 5,
+                                   stream);
+        if (st != CIA_OK) return st;
+        const int64_t next = (k + 1) * opt->steps / opt->snapshots;
+        if (next > done) {
+            if ((st = cia_advance(plan, CIA_METHOD_DIRECT, opt->dt, next - done, nullptr, stream)) != CIA_OK) return st;
+            done = next;
+        }
+    }
+    cia_fit_report fr{};
+    if ((st = cia_basis_fit(basis, pairs, total, &opt->fit, &fr, stream)) != CIA_OK) return st;
+    if ((st = cia_plan_set_basis(plan, basis)) != CIA_OK) return st;
+    if (report) {
+        report->pairs = total;
+        report->fit = fr;
+    }
+    CIA_CUDA_TRY(cudaStreamSynchronize(s));
+    return CIA_OK;
+}

@@ -81,6 +81,17 @@ struct DeviceBuffers {
     int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up
     double *r_tmp = nullptr;            // [r_cap] staging for order parameters
     int64_t r_cap = 0;
+    // Cucker--Smale (4 state values per node)
+    float4 *cs_y[2] = {nullptr, nullptr};     // [n] FP32 stage states (s_x, s_y, v_x, v_y)
+    double *cs_master = nullptr;              // [n][4] FP64 master state
+    float4 *cs_acc = nullptr;                 // [n] sum_s b_s k_s
+    void *cs_feat = nullptr;                  // [n][64] BF16 features of the current stage state
+    double *cs_part[2] = {nullptr, nullptr};  // [T][192] tile sums of phi, phi v_x, phi v_y
+    float *cs_params = nullptr;               // basis parameters (FP32 master copy)
+    int32_t *cs_check_nodes = nullptr;        // [check_count] sampled community nodes
+    int32_t *cs_check_comm = nullptr;         // their communities
+    double *cs_check_out = nullptr;           // [check_count][2] error, reference
+    float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
 };
 
 }  // namespace cia
@@ -121,6 +132,19 @@ struct cia_plan {
     int64_t prof_cap = 0, prof_used = 0, prof_other = 0;
     std::vector<cudaEvent_t> prof_ev;   // 2 per recorded launch
     int state_slot = 0;                 // phasor/partial slot holding the resident state
+    int n_sms = 0;
+    // Cucker--Smale
+    int state_dim = 1;                  // FP64 values per node at the boundary
+    double cs_sigma = 1.0, cs_beta = 0.0;
+    bool cs_has_basis = false;          // a basis was set (cia_plan_set_basis)
+    bool cs_feat_valid = false;         // features/partials match the resident state
+    int64_t cs_check_count = 0;
+    int64_t check_every = 0;            // steps between learned-basis checks (0 = off)
+    double check_bound = 0.0;
+    int64_t checks = 0;
+    double check_last = 0.0, check_max = 0.0;
+    bool fell_back = false;
+    int64_t fallback_step = -1;
 };
 
 namespace cia {
@@ -140,5 +164,15 @@ cudaError_t launch_order_parameter(cia_plan *pl, int ph_slot, double *r_out, cud
 cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
 size_t stage_smem_bytes(const cia_plan *pl, int method);
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
+
+// Cucker--Smale launchers (cucker_smale.cu).
+cudaError_t cs_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
+cudaError_t cs_launch_features(cia_plan *pl, int slot, cudaStream_t s);
+cudaError_t cs_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
+cudaError_t cs_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
+cudaError_t cs_launch_store(cia_plan *pl, double *x, cudaStream_t s);
+cudaError_t cs_launch_check(cia_plan *pl, int slot, cudaStream_t s);
+cudaError_t cs_launch_sample(cia_plan *pl, int slot, int64_t count, uint64_t seed, float *pairs, cudaStream_t s);
+size_t cs_stage_smem_bytes(const cia_plan *pl);
 
 }  // namespace cia

@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "cia_basis.h"
 #include "cia_internal.h"
 
 namespace cia {
@@ -296,8 +297,27 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
     if (pl->staging != 0 && pl->staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
-    if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO)
+    if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
+        cp->model != CIA_MODEL_CUCKER_SMALE)
         return fail(CIA_ERR_UNSUPPORTED, "unknown model");
+    if (cp->model == CIA_MODEL_CUCKER_SMALE) {
+        if (pl->precision != CIA_FP32)
+            return fail(CIA_ERR_UNSUPPORTED, "the Cucker-Smale model runs in FP32 (precision CIA_FP32)");
+        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the Cucker-Smale model");
+        if (!std::isfinite(cp->K) || !std::isfinite(cp->sigma) || !std::isfinite(cp->beta))
+            return fail(CIA_ERR_NUMERIC, "K, sigma or beta is not finite");
+        if (!(cp->sigma > 0.0)) return fail(CIA_ERR_INVALID_ARG, "sigma must be positive");
+        if (!(opt && opt->tile_nodes)) pl->tile_nodes = 128;
+        if (pl->tile_nodes > 128)
+            return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be <= 128 for the Cucker-Smale model");
+        pl->model = cp->model;
+        pl->state_dim = 4;
+        pl->p = 1;
+        pl->K = cp->K;
+        pl->cs_sigma = cp->sigma;
+        pl->cs_beta = cp->beta;
+        pl->staging = 1;   // the TMA-pipelined stage kernel is the Kuramoto one
+    } else {
     if (cp->p < 1 || cp->p > CIA_MAX_HARMONICS)
         return fail(CIA_ERR_INVALID_ARG, "p must be in [1, CIA_MAX_HARMONICS]");
     pl->model = cp->model;
@@ -316,6 +336,7 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         pl->d_cos[k] = cp->d_cos[k];
     }
     for (int k = cp->p; k < CIA_MAX_HARMONICS; ++k) pl->d_sin[k] = pl->d_cos[k] = 0.0;
+    }
     if (omega)
         for (int64_t i = 0; i < n; ++i)
             if (!std::isfinite(omega[i]))
@@ -565,6 +586,39 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         d.omega = po;
     }
     cia_status s2;
+    CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, pl->device));
+    if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
+    if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
+    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
+    if (pl->model == CIA_MODEL_CUCKER_SMALE) {
+        for (int b = 0; b < 2; ++b) {
+            if ((s2 = alloc_bytes(pl, (void **)&d.cs_y[b], (size_t)(n + 1) * sizeof(float4))) != CIA_OK) return s2;
+            if ((s2 = upload<double>(pl, &d.cs_part[b], nullptr, (size_t)T * 3 * CIA_BASIS_RANK)) != CIA_OK)
+                return s2;
+        }
+        if ((s2 = upload<double>(pl, &d.cs_master, nullptr, (size_t)n * 4)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, (void **)&d.cs_acc, (size_t)n * sizeof(float4))) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.cs_feat, (size_t)n * CIA_BASIS_RANK * 2)) != CIA_OK) return s2;
+        if ((s2 = upload<float>(pl, &d.cs_params, nullptr, CIA_BASIS_PARAMS)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, (void **)&d.cs_cen, (size_t)std::max<int64_t>(M, 1) * sizeof(float2))) != CIA_OK)
+            return s2;
+        // nodes of the learned-basis check: evenly spaced over the community nodes
+        const int64_t nc = pl->off[M];
+        pl->cs_check_count = std::min<int64_t>(512, nc);
+        std::vector<int32_t> cn(pl->cs_check_count), cc(pl->cs_check_count);
+        for (int64_t k = 0; k < pl->cs_check_count; ++k) {
+            cn[k] = (int32_t)((2 * k + 1) * nc / (2 * pl->cs_check_count));
+            cc[k] = comm_of[cn[k]];
+        }
+        UP(d.cs_check_nodes, cn.data(), cn.size());
+        UP(d.cs_check_comm, cc.data(), cc.size());
+        if ((s2 = upload<double>(pl, &d.cs_check_out, nullptr, (size_t)std::max<int64_t>(1, pl->cs_check_count) * 2)) !=
+            CIA_OK)
+            return s2;
+        UP(d.tile_desc, tdesc.data(), tdesc.size());
+        CIA_CUDA_TRY(cudaDeviceSynchronize());
+        return CIA_OK;
+    }
     if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
     if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
     for (int b = 0; b < 2; ++b) {
@@ -575,9 +629,6 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     if ((s2 = alloc_bytes(pl, &d.wdt_half, n * rb)) != CIA_OK) return s2;
     if ((s2 = alloc_bytes(pl, &d.wdt_full, n * rb)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.wdt_full64, nullptr, n)) != CIA_OK) return s2;
-    if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, n)) != CIA_OK) return s2;
-    if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, n)) != CIA_OK) return s2;
-    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
     if (pl->triadic && pl->has_direct && (s2 = alloc_bytes(pl, &d.tri, n * rb)) != CIA_OK) return s2;
     // The persistent TMA pipeline needs at most 256 nodes per tile (one
     // consumer thread per node) and, in shared memory, the CTA's tile
@@ -701,6 +752,8 @@ extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *inf
     info->staging = pl->staging;
     info->group_size_direct = pl->group_size_direct;
     info->max_tile_index_bytes = pl->max_tile_idx_bytes;
+    info->model = pl->model;
+    info->state_dim = pl->state_dim;
     return CIA_OK;
 }
 
