@@ -118,6 +118,9 @@ typedef struct {
                                    A tile is cut at tile_nodes rows or at this many index bytes. */
     int staging;                /* 0 = auto: TMA bulk copies of each tile's indices and community
                                    phasors into shared memory when they fit; 1 = plain loads */
+    int use_graphs;             /* 0 = auto: cia_advance replays one captured CUDA graph per RK4
+                                   step when it advances >= 2 steps (not while profiling);
+                                   1 = plain launches only */
 } cia_options;
 
 typedef struct cia_plan cia_plan_t;
@@ -142,6 +145,7 @@ typedef struct {
     int64_t max_tile_index_bytes; /* largest sparse-index footprint of a tile */
     int model;                  /* cia_model */
     int state_dim;              /* d: FP64 values per node at the boundary */
+    int64_t instances;          /* independent networks (1 unless cia_plan_create_batch) */
 } cia_plan_info;
 
 /* ---- status -------------------------------------------------------------- */
@@ -174,6 +178,39 @@ const char *cia_last_error(void);
 cia_status cia_plan_create(const cia_graph *g, const int32_t *community, const double *omega,
                            const cia_coupling *coupling, const cia_options *opt,
                            cia_plan_t **out);
+
+/* An ensemble of B independent networks in one plan, so that every RK4
+ * stage of all of them is one launch.  Instance i has its own graph
+ * graphs[i], labels communities[i] and frequencies omegas[i] (omegas or
+ * omegas[i] may be NULL = zero), and its own normalisation K / N_i.  The
+ * state of the ensemble concatenates the instances in order (instance i
+ * occupies [sum_{j<i} N_j, sum_{j<=i} N_j)); cia_integrate / cia_advance then
+ * fill r_out with nsteps x B order parameters, r_out[j * B + i] for instance
+ * i after step j + 1.  Kuramoto model (CIA_MODEL_KURAMOTO) only. */
+cia_status cia_plan_create_batch(int64_t B, const cia_graph *graphs, const int32_t *const *communities,
+                                 const double *const *omegas, const cia_coupling *coupling,
+                                 const cia_options *opt, cia_plan_t **out);
+
+/* Cut the plan's communities into tiles again with other tile parameters
+ * (the same meaning and limits as in cia_options; 0 = default); the split of
+ * S is reused.  The resident state's observables are recomputed on the next
+ * cia_state_load, so call it again before cia_advance. */
+cia_status cia_plan_retile(cia_plan_t *plan, int tile_nodes, int tile_index_bytes, int staging);
+
+typedef struct {
+    int candidates;             /* tilings timed */
+    int tile_nodes, tile_index_bytes, staging;   /* the fastest, now the plan's tiling */
+    double best_ms_per_step;    /* its device time per RK4 step */
+    double worst_ms_per_step;   /* the slowest candidate's */
+} cia_tune_report;
+
+/* Autotuner: time `steps` RK4 steps of the CIA (after two warm-up steps) for
+ * each candidate tiling -- tile_index_bytes in {16384, 32768, 49152} with TMA
+ * staging and, with plain loads, tile_nodes in {128, 256} -- starting from the
+ * state x (device, n x d doubles, original order), and keep the fastest.
+ * Leaves x's state resident (cia_state_load).  Synchronises the stream. */
+cia_status cia_plan_autotune(cia_plan_t *plan, const double *x, double dt, int64_t steps,
+                             cia_tune_report *report, void *stream);
 
 /* Release everything the plan owns (NULL is a no-op). */
 cia_status cia_plan_destroy(cia_plan_t *plan);
@@ -221,7 +258,8 @@ cia_status cia_rhs_direct(cia_plan_t *plan, const double *x, double *dxdt, void 
  *   precisions; stage states are in the plan's precision.
  * r_out: device, nsteps doubles or NULL; r_out[j] = |(1/N) sum_l e^{i x_l}|
  *   after step j+1 (the Kuramoto order parameter, eq. KuramotoFirstOP);
- *   must be NULL for Cucker--Smale.
+ *   nsteps x B values for an ensemble (cia_plan_create_batch); must be NULL
+ *   for Cucker--Smale.
  * nsteps = 0 only round-trips x through the wrap.
  * Cucker--Smale with method CIA and an error check set (cia_plan_set_check):
  * if a check fails, the remaining steps use the direct method and the call

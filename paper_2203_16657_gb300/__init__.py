@@ -51,17 +51,75 @@ class Plan:
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
                  tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0, sigma=1.0,
-                 beta=0.0):
+                 beta=0.0, use_graphs=True, _batch=None):
         lib = load()
         self._lib = lib
         self._keep = []
-        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
-        col = np.ascontiguousarray(col, dtype=np.int32)
-        labels = np.ascontiguousarray(labels, dtype=np.int32)
-        n = len(rowptr) - 1
-        if len(labels) != n:
-            raise ValueError("labels must have n entries")
-        g = _abi.Graph(n, rowptr.ctypes.data, col.ctypes.data)
+        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta)
+        opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
+                           int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging],
+                           0 if use_graphs else 1)
+        handle = ctypes.c_void_p()
+        if _batch is not None:
+            graphs, labs, oms = _batch
+            B = len(graphs)
+            garr = (_abi.Graph * B)()
+            larr = (ctypes.c_void_p * B)()
+            oarr = (ctypes.c_void_p * B)()
+            keep = []
+            n = 0
+            for i, ((rp, cl), lb, om) in enumerate(zip(graphs, labs, oms)):
+                rp = np.ascontiguousarray(rp, dtype=np.int64)
+                cl = np.ascontiguousarray(cl, dtype=np.int32)
+                lb = np.ascontiguousarray(lb, dtype=np.int32)
+                if len(lb) != len(rp) - 1:
+                    raise ValueError("instance %d: labels must have n entries" % i)
+                garr[i] = _abi.Graph(len(rp) - 1, rp.ctypes.data, cl.ctypes.data)
+                larr[i] = lb.ctypes.data
+                keep += [rp, cl, lb]
+                if om is not None:
+                    om = np.ascontiguousarray(om, dtype=np.float64)
+                    if len(om) != len(rp) - 1:
+                        raise ValueError("instance %d: omega must have n entries" % i)
+                    oarr[i] = om.ctypes.data
+                    keep.append(om)
+                n += len(rp) - 1
+            _abi.check(lib.cia_plan_create_batch(B, garr, larr, oarr, ctypes.byref(cp),
+                                                 ctypes.byref(opt), ctypes.byref(handle)))
+        else:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            labels = np.ascontiguousarray(labels, dtype=np.int32)
+            n = len(rowptr) - 1
+            if len(labels) != n:
+                raise ValueError("labels must have n entries")
+            g = _abi.Graph(n, rowptr.ctypes.data, col.ctypes.data)
+            om = None
+            if omega is not None:
+                om = np.ascontiguousarray(omega, dtype=np.float64)
+                if len(om) != n:
+                    raise ValueError("omega must have n entries")
+            _abi.check(lib.cia_plan_create(ctypes.byref(g), labels.ctypes.data,
+                                           om.ctypes.data if om is not None else None,
+                                           ctypes.byref(cp), ctypes.byref(opt), ctypes.byref(handle)))
+        self._h = handle
+        self.n = n
+        self.precision = precision
+        self.dim = 4 if model == "cucker_smale" else 1
+        self.size = n * self.dim
+        self.instances = self.info()["instances"]
+
+    @classmethod
+    def batch(cls, graphs, labels, omegas=None, **kw):
+        """An ensemble of independent networks: graphs = [(rowptr, col), ...],
+        labels and omegas per instance; states concatenate the instances and
+        order parameters come as [steps, B] (include/cia.h, cia_plan_create_batch)."""
+        if omegas is None:
+            omegas = [None] * len(graphs)
+        return cls(None, None, None, _batch=(list(graphs), list(labels), list(omegas)), **kw)
+
+    @staticmethod
+    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta):
         d_sin = list(d_sin)
         d_cos = list(d_cos)
         p = len(d_sin)
@@ -78,22 +136,7 @@ class Plan:
         cp.K2 = float(K2)
         cp.sigma = float(sigma)
         cp.beta = float(beta)
-        opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
-                           int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging])
-        om = None
-        if omega is not None:
-            om = np.ascontiguousarray(omega, dtype=np.float64)
-            if len(om) != n:
-                raise ValueError("omega must have n entries")
-        handle = ctypes.c_void_p()
-        _abi.check(lib.cia_plan_create(ctypes.byref(g), labels.ctypes.data,
-                                       om.ctypes.data if om is not None else None,
-                                       ctypes.byref(cp), ctypes.byref(opt), ctypes.byref(handle)))
-        self._h = handle
-        self.n = n
-        self.precision = precision
-        self.dim = 4 if model == "cucker_smale" else 1
-        self.size = n * self.dim
+        return cp
 
     # ------------------------------------------------------------ bookkeeping
     def info(self) -> dict:
@@ -132,7 +175,7 @@ class Plan:
 
     def integrate(self, x, dt, steps, method="cia", r_out=None, stream=None):
         """Advance x (CUDA float64, original order) in place by `steps` RK4 steps."""
-        rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
+        rp = _dev_ptr(r_out, "float64", int(steps) * self.instances) if r_out is not None else None
         st = self._lib.cia_integrate(self._h, _abi.METHOD[method],
                                      _dev_ptr(x, "float64", self.size), float(dt), int(steps),
                                      rp, _stream_handle(stream))
@@ -145,8 +188,8 @@ class Plan:
             raise ValueError("x must be a contiguous float64 array of n x d entries")
         rp = None
         if r_out is not None:
-            if r_out.dtype != np.float64 or len(r_out) != steps:
-                raise ValueError("r_out must be float64 with `steps` entries")
+            if r_out.dtype != np.float64 or r_out.size != steps * self.instances:
+                raise ValueError("r_out must be float64 with steps x instances entries")
             rp = r_out.ctypes.data
         self._status(self._lib.cia_integrate_host(self._h, _abi.METHOD[method], x.ctypes.data,
                                                   float(dt), int(steps), rp,
@@ -166,9 +209,20 @@ class Plan:
 
     def advance(self, dt, steps, method="cia", r_out=None, stream=None):
         """Advance the resident state by `steps` RK4 steps."""
-        rp = _dev_ptr(r_out, "float64", int(steps)) if r_out is not None else None
+        rp = _dev_ptr(r_out, "float64", int(steps) * self.instances) if r_out is not None else None
         self._status(self._lib.cia_advance(self._h, _abi.METHOD[method], float(dt), int(steps), rp,
                                            _stream_handle(stream)))
+
+    def retile(self, tile_nodes=0, tile_index_bytes=0, staging="auto"):
+        _abi.check(self._lib.cia_plan_retile(self._h, int(tile_nodes), int(tile_index_bytes),
+                                             {"auto": 0, "plain": 1}[staging]))
+
+    def autotune(self, x, dt, steps=10, stream=None) -> dict:
+        """Time the candidate tilings from state x and keep the fastest."""
+        r = _abi.TuneReport()
+        _abi.check(self._lib.cia_plan_autotune(self._h, _dev_ptr(x, "float64", self.size), float(dt),
+                                               int(steps), ctypes.byref(r), _stream_handle(stream)))
+        return {name: getattr(r, name) for name, _ in _abi.TuneReport._fields_}
 
     def _status(self, st):
         """CIA_ERR_FALLBACK is informational: the results are valid and the

@@ -45,7 +45,8 @@ class Coupling(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("build_direct", ctypes.c_int),
                 ("tile_nodes", ctypes.c_int), ("group_size", ctypes.c_int),
-                ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -57,7 +58,13 @@ class PlanInfo(ctypes.Structure):
                 ("tile_nodes", ctypes.c_int), ("missing_index_bytes", ctypes.c_int),
                 ("staging", ctypes.c_int), ("group_size_direct", ctypes.c_int),
                 ("max_tile_index_bytes", ctypes.c_int64), ("model", ctypes.c_int),
-                ("state_dim", ctypes.c_int)]
+                ("state_dim", ctypes.c_int), ("instances", ctypes.c_int64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int), ("tile_nodes", ctypes.c_int),
+                ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int),
+                ("best_ms_per_step", ctypes.c_double), ("worst_ms_per_step", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -107,6 +114,11 @@ SIGNATURES = {
     "cia_plan_create": (ctypes.c_int, [ctypes.POINTER(Graph), _P, _P, ctypes.POINTER(Coupling),
                                        ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "cia_plan_destroy": (ctypes.c_int, [_P]),
+    "cia_plan_create_batch": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, ctypes.POINTER(Coupling),
+                                             ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "cia_plan_retile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cia_plan_autotune": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.POINTER(TuneReport), _P]),
     "cia_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "cia_plan_get_permutation": (ctypes.c_int, [_P, _P, _P]),
     "cia_plan_get_split": (ctypes.c_int, [_P, _P, _P, _P, _P]),

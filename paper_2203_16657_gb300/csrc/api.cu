@@ -10,6 +10,17 @@
 
 using namespace cia;
 
+namespace cia {
+
+void invalidate_graphs(cia_plan *pl) {
+    if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
+    pl->graph_exec = nullptr;
+    pl->graph_method = pl->graph_slot = -1;
+    pl->graph_r_out = nullptr;
+}
+
+}  // namespace cia
+
 namespace {
 
 cia_status fail(cia_status s, const std::string &msg) {
@@ -184,6 +195,43 @@ cia_status cs_advance(cia_plan *pl, int method, double dt, int64_t nsteps, doubl
     return CIA_OK;
 }
 
+// Capture (or reuse) the CUDA graph of one RK4 step: four stage launches
+// starting from `slot`, then the order parameters when r_out is given.
+cia_status ensure_step_graph(cia_plan *pl, int m, int slot, double dt, double *r_out) {
+    if (pl->graph_exec && pl->graph_method == m && pl->graph_slot == slot && pl->graph_dt == dt &&
+        pl->graph_r == (r_out != nullptr) && pl->graph_r_out == r_out)
+        return CIA_OK;
+    invalidate_graphs(pl);
+    if (!pl->capture_stream) CIA_CUDA_TRY(cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = pl->capture_stream;
+    CIA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    int sl = slot;
+    for (int stage = 1; stage <= 4 && err == cudaSuccess; ++stage) {
+        err = launch_rk4_stage(pl, m, stage, sl, dt, cs);
+        sl ^= 1;
+    }
+    if (err == cudaSuccess && r_out) err = launch_order_parameters(pl, sl, r_out, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(cs, &graph);
+    if (err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(err, "kernel launch during graph capture");
+    }
+    if (end != cudaSuccess) return cuda_fail(end, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (inst != cudaSuccess) return cuda_fail(inst, "cudaGraphInstantiate");
+    pl->graph_exec = exec;
+    pl->graph_method = m;
+    pl->graph_slot = slot;
+    pl->graph_dt = dt;
+    pl->graph_r = r_out != nullptr;
+    pl->graph_r_out = r_out;
+    return CIA_OK;
+}
+
 void destroy_events(cia_plan *pl) {
     for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
     pl->prof_ev.clear();
@@ -205,6 +253,7 @@ extern "C" cia_status cia_state_load(cia_plan_t *pl, const double *x, void *stre
         CIA_CUDA_TRY(launch_phasors_from_x(pl, x, true, 0, (cudaStream_t)stream));
     }
     pl->state_slot = 0;
+    pl->needs_load = false;
     pl->prof_other++;
     return CIA_OK;
 }
@@ -225,20 +274,32 @@ extern "C" cia_status cia_advance(cia_plan_t *pl, int method, double dt, int64_t
     if (st != CIA_OK) return st;
     if (!std::isfinite(dt)) return fail(CIA_ERR_NUMERIC, "dt is not finite");
     if (nsteps < 0) return fail(CIA_ERR_INVALID_ARG, "nsteps < 0");
+    if (pl->needs_load) return fail(CIA_ERR_INVALID_ARG, "the tiling changed: load a state first (cia_state_load)");
     cudaStream_t s = (cudaStream_t)stream;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) return cs_advance(pl, method, dt, nsteps, r_out, s);
     const int m = method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA;
     st = ensure_omega_constants(pl, dt, s);
     if (st != CIA_OK) return st;
+    if (r_out) CIA_CUDA_TRY(cudaMemsetAsync(pl->d.r_counter, 0, sizeof(int64_t), s));
+    const bool profiling = pl->prof_on && pl->prof_used < pl->prof_cap;
+    const bool graphs = pl->use_graphs == 0 && nsteps >= 2 && !profiling;
     int slot = pl->state_slot;
     for (int64_t j = 0; j < nsteps; ++j) {
+        if (graphs && j >= 1) {
+            // steps 1.. replay one captured step (step 0 ran plain launches,
+            // which also configured every kernel); 4 stages return the slot
+            if ((st = ensure_step_graph(pl, m, slot, dt, r_out)) != CIA_OK) return st;
+            CIA_CUDA_TRY(cudaGraphLaunch(pl->graph_exec, s));
+            pl->prof_other += 4 + (r_out ? 1 : 0);
+            continue;
+        }
         for (int stage = 1; stage <= 4; ++stage) {
             st = stage_launch(pl, m, stage, slot, dt, s);
             if (st != CIA_OK) return st;
             slot ^= 1;
         }
         if (r_out) {
-            CIA_CUDA_TRY(launch_order_parameter(pl, slot, r_out + j, s));
+            CIA_CUDA_TRY(launch_order_parameters(pl, slot, r_out, s));
             pl->prof_other++;
         }
     }
@@ -340,6 +401,79 @@ extern "C" cia_status cia_sync(cia_plan_t *pl, void *stream) {
     if (flag) {
         CIA_CUDA_TRY(cudaMemset(pl->d.err_flag, 0, sizeof(int)));
         return fail(CIA_ERR_TIMEOUT, "a device-side wait gave up; results since the last cia_sync are invalid");
+    }
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double dt, int64_t steps,
+                                        cia_tune_report *report, void *stream) {
+    clear_error();
+    cia_status st = check_plan(pl, CIA_METHOD_CIA);
+    if (st != CIA_OK && st != CIA_ERR_UNSUPPORTED) return st;
+    if (!x) return fail(CIA_ERR_INVALID_ARG, "x is NULL");
+    if (steps < 1 || !std::isfinite(dt)) return fail(CIA_ERR_INVALID_ARG, "need steps >= 1 and a finite dt");
+    struct Cand { int tn, tib, staging; };
+    std::vector<Cand> cands;
+    if (pl->model == CIA_MODEL_CUCKER_SMALE) {
+        for (int tn : {64, 128})
+            for (int tib : {16384, 32768}) cands.push_back({tn, tib, 1});
+    } else {
+        for (int tib : {16384, 32768, 49152}) cands.push_back({256, tib, 0});
+        for (int tn : {128, 256}) cands.push_back({tn, 32768, 1});
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CIA_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{e0, e1};
+    double best = INFINITY, worst = 0.0;
+    int bi = -1, tried = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const Cand &c = cands[i];
+        if ((st = cia_plan_retile(pl, c.tn, c.tib, c.staging)) != CIA_OK) return st;
+        if (c.staging == 0 && pl->staging != 0) continue;   // the TMA pipeline did not fit: same as plain
+        if ((st = cia_state_load(pl, x, stream)) != CIA_OK) return st;
+        if ((st = check_plan(pl, CIA_METHOD_CIA)) != CIA_OK) continue;   // does not fit this GPU
+        if ((st = cia_advance(pl, CIA_METHOD_CIA, dt, 2, nullptr, stream)) != CIA_OK && st != CIA_ERR_FALLBACK)
+            return st;
+        CIA_CUDA_TRY(cudaEventRecord(e0, s));
+        if ((st = cia_advance(pl, CIA_METHOD_CIA, dt, steps, nullptr, stream)) != CIA_OK && st != CIA_ERR_FALLBACK)
+            return st;
+        CIA_CUDA_TRY(cudaEventRecord(e1, s));
+        CIA_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CIA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if ((st = cia_sync(pl, stream)) != CIA_OK) return st;
+        const double per = (double)ms / (double)steps;
+        ++tried;
+        worst = std::max(worst, per);
+        if (per < best) {
+            best = per;
+            bi = (int)i;
+        }
+    }
+    if (bi < 0) return fail(CIA_ERR_UNSUPPORTED, "no candidate tiling fits this GPU");
+    const Cand &c = cands[bi];
+    if ((st = cia_plan_retile(pl, c.tn, c.tib, c.staging)) != CIA_OK) return st;
+    if ((st = cia_state_load(pl, x, stream)) != CIA_OK) return st;
+    CIA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (report) {
+        report->candidates = tried;
+        report->tile_nodes = c.tn;
+        report->tile_index_bytes = c.tib;
+        report->staging = pl->staging;
+        report->best_ms_per_step = best;
+        report->worst_ms_per_step = worst;
     }
     return CIA_OK;
 }

@@ -92,6 +92,20 @@ struct DeviceBuffers {
     int32_t *cs_check_comm = nullptr;         // their communities
     double *cs_check_out = nullptr;           // [check_count][2] error, reference
     float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
+    // ensembles of independent networks
+    void *tile_kn = nullptr;                  // [T] K / N_i of the tile's instance, compute precision
+    int32_t *inst_tiles = nullptr;            // [B][4] community tiles [0,1), free tiles [2,3) of instance i
+    int64_t *inst_off = nullptr;              // [B+1] node offsets of the instances
+    int64_t *r_counter = nullptr;             // step index of the next order-parameter row
+};
+
+// The split of S kept on the host after planning (re-tiling reuses it).
+struct HostSplit {
+    std::vector<int32_t> comm_of;              // [n] community of permuted node m, -1 if none
+    std::vector<int64_t> miss_cnt, miss_off;   // per row: missing links, offsets into miss_local
+    std::vector<int32_t> miss_local;           // community-local indices, ascending per row
+    std::vector<int64_t> inter_cnt, inter_off; // per row: inter links, offsets into inter_col
+    std::vector<int32_t> inter_col;            // permuted ids, ascending per row
 };
 
 }  // namespace cia
@@ -133,6 +147,23 @@ struct cia_plan {
     std::vector<cudaEvent_t> prof_ev;   // 2 per recorded launch
     int state_slot = 0;                 // phasor/partial slot holding the resident state
     int n_sms = 0;
+    cia::HostSplit hs;
+    std::vector<void *> tile_allocs;    // device buffers of the current tiling
+    int64_t tile_bytes = 0;
+    int staging_req = 0;                // staging the caller asked for (the tiling may downgrade it)
+    int use_graphs = 0;                 // 0: one CUDA graph per RK4 step when advancing >= 2 steps
+    // ensembles of independent networks (cia_plan_create_batch)
+    int64_t B = 1;
+    std::vector<int64_t> inst_off;      // [B+1] node offsets (original ids)
+    std::vector<int64_t> inst_comm_off; // [B+1] community offsets
+    // CUDA graph of one RK4 step (cached by method, dt, slot and order-parameter output)
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_method = -1, graph_slot = -1;
+    bool graph_r = false;
+    double graph_dt = 0.0;
+    double *graph_r_out = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    bool needs_load = false;            // the tiling changed since the last cia_state_load
     // Cucker--Smale
     int state_dim = 1;                  // FP64 values per node at the boundary
     double cs_sigma = 1.0, cs_beta = 0.0;
@@ -160,10 +191,15 @@ cudaError_t launch_rhs(cia_plan *pl, int method, int ph_slot, double *dxdt, cuda
 cudaError_t launch_omega_constants(cia_plan *pl, double dt, cudaStream_t s);
 cudaError_t launch_rk4_stage(cia_plan *pl, int method, int stage, int ph_in_slot, double dt,
                              cudaStream_t s);
-cudaError_t launch_order_parameter(cia_plan *pl, int ph_slot, double *r_out, cudaStream_t s);
 cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
 size_t stage_smem_bytes(const cia_plan *pl, int method);
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
+
+// Drop the cached CUDA graph of an RK4 step (api.cu).
+void invalidate_graphs(cia_plan *pl);
+// Order parameters of every instance of the state in slot `slot`:
+// r_base[counter * B + i], then ++counter (kuramoto.cu).
+cudaError_t launch_order_parameters(cia_plan *pl, int slot, double *r_base, cudaStream_t s);
 
 // Cucker--Smale launchers (cucker_smale.cu).
 cudaError_t cs_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);

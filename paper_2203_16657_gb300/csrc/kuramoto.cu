@@ -96,6 +96,7 @@ struct StageParams {
     int tile_nodes;
     T d_sin[CIA_MAX_HARMONICS], d_cos[CIA_MAX_HARMONICS];
     T k_over_n;                // K / N
+    const T *tile_kn;          // ensembles: K / N_i per tile (NULL: k_over_n everywhere)
     T k2_over_n2;              // K2 / N^2 (higher-order model; 0 otherwise)
     const T *tri;              // direct method, higher-order model: triadic term per node
     const int64_t *off;
@@ -197,7 +198,7 @@ __device__ __forceinline__ void finalize_tile(const StageParams<T> &a, int t, in
             const T im = zi * u.x - zr * u.y;
             coup += a.d_sin[k] * im + a.d_cos[k] * re;
         }
-        coup *= a.k_over_n;
+        coup *= a.tile_kn ? a.tile_kn[t] : a.k_over_n;
         if (P >= 2 && dense && a.k2_over_n2 != T(0))
             coup += a.k2_over_n2 * triadic_from_moments<T>(zc[0].x, zc[0].y, zc[P >= 2 ? 1 : 0].x, zc[P >= 2 ? 1 : 0].y,
                                                            uk[0].x, uk[0].y, uk[P >= 2 ? 1 : 0].x, uk[P >= 2 ? 1 : 0].y);
@@ -772,7 +773,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                 const T im = zi * uu.x - zr * uu.y;
                 coup += a.d_sin[kk] * im + a.d_cos[kk] * re;
             }
-            coup *= a.k_over_n;
+            coup *= a.tile_kn ? a.tile_kn[i] : a.k_over_n;
             if (P >= 2 && dense && a.k2_over_n2 != T(0)) {
                 const C z1 = zrun[(size_t)h.run * P], z2 = zrun[(size_t)h.run * P + (P >= 2 ? 1 : 0)];
                 coup += a.k2_over_n2 * triadic_from_moments<T>(z1.x, z1.y, z2.x, z2.y, uk[0].x, uk[0].y,
@@ -932,9 +933,41 @@ __global__ void omega_constants_kernel(int64_t n, const T *omega, double dt, T *
     }
 }
 
-// r = |sum over all tiles of the first-harmonic tile sums| / N.
+// Order parameter of every instance, r_i = |sum over the instance's tiles of
+// the first-harmonic tile sums| / N_i (eq. KuramotoFirstOP), written to
+// r_base[c * B + i] with c = *counter, which is then incremented: the same
+// launch, captured once in a CUDA graph, fills consecutive rows.  One block;
+// warp w handles instances w, w + 32, ...
 template <int P>
-__global__ void order_parameter_kernel(int64_t n, int64_t tiles, const double *part, double *r_out) {
+__global__ void __launch_bounds__(1024) order_parameters_kernel(int64_t B, const int32_t *inst_tiles,
+                                                                const int64_t *inst_off, const double *part,
+                                                                double *r_base, int64_t *counter) {
+    __shared__ int64_t row;
+    if (threadIdx.x == 0) row = *counter;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t i = warp; i < B; i += nw) {
+        double re = 0.0, im = 0.0;
+        for (int rng = 0; rng < 2; ++rng)
+            for (int t = inst_tiles[4 * i + 2 * rng] + lane; t < inst_tiles[4 * i + 2 * rng + 1]; t += 32) {
+                re += part[(int64_t)t * P * 2];
+                im += part[(int64_t)t * P * 2 + 1];
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) r_base[row * B + i] = sqrt(re * re + im * im) / (double)(inst_off[i + 1] - inst_off[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = row + 1;
+}
+
+// r = |sum over all tiles of the first-harmonic tile sums| / N, written to
+// r_base[*counter], then ++*counter.
+template <int P>
+__global__ void order_parameter_kernel(int64_t n, int64_t tiles, const double *part, double *r_base,
+                                       int64_t *counter) {
     __shared__ double sre[kThreads], sim[kThreads];
     double re = 0.0, im = 0.0;
     for (int64_t t = threadIdx.x; t < tiles; t += kThreads) {
@@ -951,7 +984,11 @@ __global__ void order_parameter_kernel(int64_t n, int64_t tiles, const double *p
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *r_out = sqrt(sre[0] * sre[0] + sim[0] * sim[0]) / (double)n;
+    if (threadIdx.x == 0) {
+        const int64_t row = *counter;
+        r_base[row] = sqrt(sre[0] * sre[0] + sim[0] * sim[0]) / (double)n;
+        *counter = row + 1;
+    }
 }
 
 __global__ void scatter_master_kernel(int64_t n, const int32_t *perm, const double *theta, double *x) {
@@ -1016,6 +1053,7 @@ StageParams<T> base_params(cia_plan *pl, int method) {
         a.d_cos[k] = (T)pl->d_cos[k];
     }
     a.k_over_n = (T)(pl->K / (double)pl->n);
+    a.tile_kn = (const T *)pl->d.tile_kn;
     a.k2_over_n2 = (T)(pl->K2 / ((double)pl->n * (double)pl->n));
     a.tri = (method == Method::DIRECT && pl->triadic) ? (const T *)pl->d.tri : nullptr;
     a.off = pl->d.off;
@@ -1207,13 +1245,25 @@ cudaError_t launch_omega_constants(cia_plan *pl, double dt, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_order_parameter(cia_plan *pl, int slot, double *r_out, cudaStream_t s) {
+cudaError_t launch_order_parameters(cia_plan *pl, int slot, double *r_base, cudaStream_t s) {
+    const double *part = pl->d.part[slot];
+    int64_t *ctr = pl->d.r_counter;
+    if (pl->B > 1) {
+        const int64_t *io = pl->d.inst_off;
+        const int32_t *it = pl->d.inst_tiles;
+        switch (pl->p) {
+            case 1: order_parameters_kernel<1><<<1, 1024, 0, s>>>(pl->B, it, io, part, r_base, ctr); break;
+            case 2: order_parameters_kernel<2><<<1, 1024, 0, s>>>(pl->B, it, io, part, r_base, ctr); break;
+            case 3: order_parameters_kernel<3><<<1, 1024, 0, s>>>(pl->B, it, io, part, r_base, ctr); break;
+            default: order_parameters_kernel<4><<<1, 1024, 0, s>>>(pl->B, it, io, part, r_base, ctr); break;
+        }
+        return cudaGetLastError();
+    }
     switch (pl->p) {
-        case 1: order_parameter_kernel<1><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
-        case 2: order_parameter_kernel<2><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
-        case 3: order_parameter_kernel<3><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
-        case 4: order_parameter_kernel<4><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, pl->d.part[slot], r_out); break;
-        default: return cudaErrorInvalidValue;
+        case 1: order_parameter_kernel<1><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, part, r_base, ctr); break;
+        case 2: order_parameter_kernel<2><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, part, r_base, ctr); break;
+        case 3: order_parameter_kernel<3><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, part, r_base, ctr); break;
+        default: order_parameter_kernel<4><<<1, kThreads, 0, s>>>(pl->n, pl->n_tiles, part, r_base, ctr); break;
     }
     return cudaGetLastError();
 }

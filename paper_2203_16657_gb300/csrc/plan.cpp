@@ -95,13 +95,16 @@ static cia_status validate_graph(const cia_graph *g) {
     return CIA_OK;
 }
 
+// Device copy of src (count elements; zero-filled when src is NULL), owned by
+// the plan; `tile` marks buffers that belong to the current tiling.
 template <typename T>
-static cia_status upload(cia_plan *pl, T **dst, const T *src, size_t count) {
+static cia_status upload(cia_plan *pl, T **dst, const T *src, size_t count, bool tile = false) {
     size_t bytes = std::max<size_t>(count * sizeof(T), 256);
     void *p = nullptr;
     CIA_CUDA_TRY(cudaMalloc(&p, bytes));
-    pl->allocations.push_back(p);
+    (tile ? pl->tile_allocs : pl->allocations).push_back(p);
     pl->device_bytes += (int64_t)bytes;
+    if (tile) pl->tile_bytes += (int64_t)bytes;
     if (src && count) CIA_CUDA_TRY(cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice));
     else CIA_CUDA_TRY(cudaMemset(p, 0, bytes));
     *dst = (T *)p;
@@ -112,9 +115,20 @@ static cia_status alloc_bytes(cia_plan *pl, void **dst, size_t bytes) {
     return upload<unsigned char>(pl, (unsigned char **)dst, nullptr, bytes);
 }
 
+// Ensemble instance of an original node id (0 for a single network).
+static int64_t instance_of_node(const cia_plan *pl, int64_t id) {
+    if (pl->B <= 1) return 0;
+    return (int64_t)(std::upper_bound(pl->inst_off.begin(), pl->inst_off.end(), id) - pl->inst_off.begin()) - 1;
+}
+
 static void free_all(cia_plan *pl) {
+    invalidate_graphs(pl);
+    if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
+    pl->capture_stream = nullptr;
     for (void *p : pl->allocations) cudaFree(p);
     pl->allocations.clear();
+    for (void *p : pl->tile_allocs) cudaFree(p);
+    pl->tile_allocs.clear();
     for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
     pl->prof_ev.clear();
     if (pl->d.r_tmp) cudaFree(pl->d.r_tmp);
@@ -281,8 +295,11 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inte
     }
 }
 
-static cia_status build_plan(const cia_graph *g, const int32_t *community, const double *omega,
-                             const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
+// Phase 1 of planning: options, model, validation, kappa and the split of S
+// into the host lists kept by the plan (pl->hs), the direct method's CSR and
+// every device buffer that does not depend on the tiling.
+static cia_status build_split(const cia_graph *g, const int32_t *community, const double *omega,
+                              const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
     const int64_t n = g->n;
     // ---- options and model
     pl->precision = opt ? opt->precision : CIA_FP64;
@@ -297,6 +314,8 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
     if (pl->staging != 0 && pl->staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
+    pl->use_graphs = opt ? opt->use_graphs : 0;
+    if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
         cp->model != CIA_MODEL_CUCKER_SMALE)
         return fail(CIA_ERR_UNSUPPORTED, "unknown model");
@@ -372,12 +391,17 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     pl->max_comm = 0;
     for (int64_t c = 0; c < M; ++c) pl->max_comm = std::max(pl->max_comm, pl->off[c + 1] - pl->off[c]);
     pl->miss_idx_bytes = pl->max_comm <= 65535 ? 2 : 4;
-    std::vector<int32_t> comm_of(n, -1);
+    auto &hs = pl->hs;
+    hs.comm_of.assign(n, -1);
+    auto &comm_of = hs.comm_of;
     for (int64_t c = 0; c < M; ++c)
         for (int64_t m = pl->off[c]; m < pl->off[c + 1]; ++m) comm_of[m] = (int32_t)c;
 
     // ---- pass 1: per-row counts of missing and inter links
-    std::vector<int64_t> miss_cnt(n, 0), inter_cnt(n, 0);
+    hs.miss_cnt.assign(n, 0);
+    hs.inter_cnt.assign(n, 0);
+    auto &miss_cnt = hs.miss_cnt;
+    auto &inter_cnt = hs.inter_cnt;
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t m = 0; m < n; ++m) {
         int32_t i = pl->perm[m];
@@ -395,7 +419,11 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
     }
     auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
     auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
-    std::vector<int64_t> miss_off(n + 1, 0), inter_off(n + 1, 0), full_rp;
+    hs.miss_off.assign(n + 1, 0);
+    hs.inter_off.assign(n + 1, 0);
+    auto &miss_off = hs.miss_off;
+    auto &inter_off = hs.inter_off;
+    std::vector<int64_t> full_rp;
     for (int64_t m = 0; m < n; ++m) {
         miss_off[m + 1] = miss_off[m] + miss_cnt[m];
         inter_off[m + 1] = inter_off[m] + inter_cnt[m];
@@ -412,7 +440,10 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
 
     // ---- pass 2: the lists themselves (missing as community-local indices),
     // ascending within each row
-    std::vector<int32_t> miss_local(miss_off[n]), inter_col(inter_off[n]);
+    hs.miss_local.assign(miss_off[n], 0);
+    hs.inter_col.assign(inter_off[n], 0);
+    auto &miss_local = hs.miss_local;
+    auto &inter_col = hs.inter_col;
     std::vector<int32_t> full_col(pl->has_direct ? full_rp[n] : 0);
 #pragma omp parallel
     {
@@ -454,6 +485,114 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         }
     }
 
+    // ---- default threads per row of the direct method (16-byte vectors;
+    // about two vectors per thread)
+    const int gs = opt ? opt->group_size : 0;
+    if (gs != 0 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
+        return fail(CIA_ERR_INVALID_ARG, "group_size must be 0, 4, 8, 16 or 32");
+    pl->group_size = 32;
+    if (pl->has_direct) {
+        double mean_vec_direct = (double)(full_rp[n] / 4) / (double)std::max<int64_t>(1, n);
+        int gd = 4;
+        while (gd < 32 && 2.0 * gd < mean_vec_direct) gd *= 2;
+        pl->group_size_direct = gs ? gs : gd;
+    }
+
+    // ---- upload
+    CIA_CUDA_TRY(cudaGetDevice(&pl->device));
+    auto &d = pl->d;
+#define UP(dst, src, cnt)                                  \
+    do {                                                   \
+        cia_status _s = upload(pl, &(dst), (src), (cnt));  \
+        if (_s != CIA_OK) return _s;                       \
+    } while (0)
+    UP(d.perm, pl->perm.data(), (size_t)n);
+    UP(d.off, pl->off.data(), (size_t)M + 1);
+    if (pl->has_direct) {
+        UP(d.full_rowptr, full_rp.data(), full_rp.size());
+        UP(d.full_col, full_col.data(), full_col.size());
+    }
+    const size_t rb = pl->precision == CIA_FP64 ? sizeof(double) : sizeof(float);
+    {
+        std::vector<unsigned char> om(n * rb, 0);
+        for (int64_t m = 0; m < n; ++m) {
+            double w = omega ? omega[pl->perm[m]] : 0.0;
+            if (rb == sizeof(double)) std::memcpy(&om[m * rb], &w, rb);
+            else {
+                float wf = (float)w;
+                std::memcpy(&om[m * rb], &wf, rb);
+            }
+        }
+        unsigned char *po = nullptr;
+        UP(po, om.data(), om.size());
+        d.omega = po;
+    }
+    cia_status s2;
+    CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, pl->device));
+    if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
+    if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
+    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
+    if ((s2 = upload<int64_t>(pl, &d.r_counter, nullptr, 1)) != CIA_OK) return s2;
+    if (pl->B > 1) UP(d.inst_off, pl->inst_off.data(), pl->inst_off.size());
+    if (pl->model == CIA_MODEL_CUCKER_SMALE) {
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = alloc_bytes(pl, (void **)&d.cs_y[b], (size_t)(n + 1) * sizeof(float4))) != CIA_OK) return s2;
+        if ((s2 = upload<double>(pl, &d.cs_master, nullptr, (size_t)n * 4)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, (void **)&d.cs_acc, (size_t)n * sizeof(float4))) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.cs_feat, (size_t)n * CIA_BASIS_RANK * 2)) != CIA_OK) return s2;
+        if ((s2 = upload<float>(pl, &d.cs_params, nullptr, CIA_BASIS_PARAMS)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, (void **)&d.cs_cen, (size_t)std::max<int64_t>(M, 1) * sizeof(float2))) != CIA_OK)
+            return s2;
+        // nodes of the learned-basis check: evenly spaced over the community nodes
+        const int64_t nc = pl->off[M];
+        pl->cs_check_count = std::min<int64_t>(512, nc);
+        std::vector<int32_t> cn(pl->cs_check_count), cc(pl->cs_check_count);
+        for (int64_t k = 0; k < pl->cs_check_count; ++k) {
+            cn[k] = (int32_t)((2 * k + 1) * nc / (2 * pl->cs_check_count));
+            cc[k] = comm_of[cn[k]];
+        }
+        UP(d.cs_check_nodes, cn.data(), cn.size());
+        UP(d.cs_check_comm, cc.data(), cc.size());
+        if ((s2 = upload<double>(pl, &d.cs_check_out, nullptr, (size_t)std::max<int64_t>(1, pl->cs_check_count) * 2)) !=
+            CIA_OK)
+            return s2;
+    }
+    if (pl->model != CIA_MODEL_CUCKER_SMALE) {
+        if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = alloc_bytes(pl, &d.ph[b], (size_t)pl->p * pl->ph_stride * 2 * rb)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.wdt_half, n * rb)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.wdt_full, n * rb)) != CIA_OK) return s2;
+        if ((s2 = upload<double>(pl, &d.wdt_full64, nullptr, n)) != CIA_OK) return s2;
+        if (pl->triadic && pl->has_direct && (s2 = alloc_bytes(pl, &d.tri, n * rb)) != CIA_OK) return s2;
+    }
+#undef UP
+    return CIA_OK;
+}
+
+// Phase 2 of planning: cut the communities into work tiles, build the
+// sliced-ELL blobs and every device buffer whose size depends on the tiling.
+// Runs again (after freeing the previous tiling) when the tiling changes.
+static cia_status build_tiles(cia_plan *pl) {
+    const int64_t n = pl->n, M = pl->M;
+    auto &hs = pl->hs;
+    const auto &miss_cnt = hs.miss_cnt;
+    const auto &miss_off = hs.miss_off;
+    const auto &miss_local = hs.miss_local;
+    const auto &inter_cnt = hs.inter_cnt;
+    const auto &inter_off = hs.inter_off;
+    const auto &inter_col = hs.inter_col;
+    for (void *p : pl->tile_allocs) cudaFree(p);
+    pl->device_bytes -= pl->tile_bytes;
+    pl->tile_allocs.clear();
+    pl->tile_bytes = 0;
+    pl->staging = pl->staging_req;
+    pl->n_ctas = 0;
+    pl->max_cta_tiles = pl->max_cta_runs = 0;
+    invalidate_graphs(pl);
+    auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
+    auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
     // ---- tiles: runs of consecutive rows of one community, cut at tile_nodes
     // rows or when the rows' sparse indices (padded to 16-byte vectors) would
     // exceed tile_index_bytes; a single longer row forms a tile of its own
@@ -483,7 +622,17 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         cut((int32_t)c, pl->off[c], pl->off[c + 1]);
     }
     comm_tile_begin[M] = (int32_t)tile_comm.size();
-    cut(-1, pl->off[M], n);
+    // nodes without a community: never a tile across two instances of a batch
+    {
+        int64_t s = pl->off[M];
+        while (s < n) {
+            const int64_t inst = instance_of_node(pl, pl->perm[s]);
+            int64_t e = s + 1;
+            while (e < n && instance_of_node(pl, pl->perm[e]) == inst) ++e;
+            cut(-1, s, e);
+            s = e;
+        }
+    }
     const int64_t T = (int64_t)tile_comm.size();
     pl->n_tiles = T;
 
@@ -538,98 +687,63 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
         pl->blob_bytes = blob_off[T];
     }
 
-    // ---- default threads per row of the direct method (16-byte vectors;
-    // about two vectors per thread)
-    const int gs = opt ? opt->group_size : 0;
-    if (gs != 0 && gs != 4 && gs != 8 && gs != 16 && gs != 32)
-        return fail(CIA_ERR_INVALID_ARG, "group_size must be 0, 4, 8, 16 or 32");
-    pl->group_size = 32;
-    if (pl->has_direct) {
-        double mean_vec_direct = (double)(full_rp[n] / 4) / (double)std::max<int64_t>(1, n);
-        int gd = 4;
-        while (gd < 32 && 2.0 * gd < mean_vec_direct) gd *= 2;
-        pl->group_size_direct = gs ? gs : gd;
-    }
-
     // ---- upload
-    CIA_CUDA_TRY(cudaGetDevice(&pl->device));
     auto &d = pl->d;
-#define UP(dst, src, cnt)                                  \
-    do {                                                   \
-        cia_status _s = upload(pl, &(dst), (src), (cnt));  \
-        if (_s != CIA_OK) return _s;                       \
+#define UPT(dst, src, cnt)                                       \
+    do {                                                         \
+        cia_status _s = upload(pl, &(dst), (src), (cnt), true);  \
+        if (_s != CIA_OK) return _s;                             \
     } while (0)
-    UP(d.perm, pl->perm.data(), (size_t)n);
-    UP(d.off, pl->off.data(), (size_t)M + 1);
-    UP(d.tile_comm, tile_comm.data(), tile_comm.size());
-    UP(d.tile_first, tile_first.data(), tile_first.size());
-    UP(d.tile_count, tile_count.data(), tile_count.size());
-    UP(d.comm_tile_begin, comm_tile_begin.data(), comm_tile_begin.size());
-    UP(d.blob, blob.data(), blob.size());
-    if (pl->has_direct) {
-        UP(d.full_rowptr, full_rp.data(), full_rp.size());
-        UP(d.full_col, full_col.data(), full_col.size());
+    UPT(d.tile_comm, tile_comm.data(), tile_comm.size());
+    UPT(d.tile_first, tile_first.data(), tile_first.size());
+    UPT(d.tile_count, tile_count.data(), tile_count.size());
+    UPT(d.comm_tile_begin, comm_tile_begin.data(), comm_tile_begin.size());
+    UPT(d.blob, blob.data(), blob.size());
+    cia_status s2;
+    if (pl->model == CIA_MODEL_CUCKER_SMALE) {
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = upload<double>(pl, &d.cs_part[b], nullptr, (size_t)T * 3 * CIA_BASIS_RANK, true)) != CIA_OK)
+                return s2;
+        pl->cs_feat_valid = false;
+    } else {
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = upload<double>(pl, &d.part[b], nullptr, (size_t)T * pl->p * 2, true)) != CIA_OK) return s2;
     }
-    const size_t rb = pl->precision == CIA_FP64 ? sizeof(double) : sizeof(float);
-    {
-        std::vector<unsigned char> om(n * rb, 0);
-        for (int64_t m = 0; m < n; ++m) {
-            double w = omega ? omega[pl->perm[m]] : 0.0;
-            if (rb == sizeof(double)) std::memcpy(&om[m * rb], &w, rb);
+    // ensembles: K / N_i per tile and each instance's tile ranges
+    if (pl->B > 1) {
+        const size_t rb = pl->precision == CIA_FP64 ? sizeof(double) : sizeof(float);
+        std::vector<unsigned char> kn(T * rb);
+        std::vector<int32_t> itab(4 * pl->B, 0);
+        for (int64_t i = 0; i < pl->B; ++i) {
+            itab[4 * i + 0] = comm_tile_begin[pl->inst_comm_off[i]];
+            itab[4 * i + 1] = comm_tile_begin[pl->inst_comm_off[i + 1]];
+            itab[4 * i + 2] = itab[4 * i + 3] = (int32_t)T;
+        }
+        for (int64_t t = 0; t < T; ++t) {
+            const int64_t inst = instance_of_node(pl, pl->perm[tile_first[t]]);
+            const double v = pl->K / (double)(pl->inst_off[inst + 1] - pl->inst_off[inst]);
+            if (rb == sizeof(double)) std::memcpy(&kn[t * rb], &v, rb);
             else {
-                float wf = (float)w;
-                std::memcpy(&om[m * rb], &wf, rb);
+                const float f = (float)v;
+                std::memcpy(&kn[t * rb], &f, rb);
+            }
+            if (tile_comm[t] < 0) {
+                if (itab[4 * inst + 2] == (int32_t)T) itab[4 * inst + 2] = (int32_t)t;
+                itab[4 * inst + 3] = (int32_t)t + 1;
             }
         }
-        unsigned char *po = nullptr;
-        UP(po, om.data(), om.size());
-        d.omega = po;
+        for (int64_t i = 0; i < pl->B; ++i)
+            if (itab[4 * i + 2] == (int32_t)T) itab[4 * i + 2] = itab[4 * i + 3] = 0;
+        unsigned char *pk = nullptr;
+        UPT(pk, kn.data(), kn.size());
+        d.tile_kn = pk;
+        UPT(d.inst_tiles, itab.data(), itab.size());
     }
-    cia_status s2;
-    CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, pl->device));
-    if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
-    if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
-    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
-        for (int b = 0; b < 2; ++b) {
-            if ((s2 = alloc_bytes(pl, (void **)&d.cs_y[b], (size_t)(n + 1) * sizeof(float4))) != CIA_OK) return s2;
-            if ((s2 = upload<double>(pl, &d.cs_part[b], nullptr, (size_t)T * 3 * CIA_BASIS_RANK)) != CIA_OK)
-                return s2;
-        }
-        if ((s2 = upload<double>(pl, &d.cs_master, nullptr, (size_t)n * 4)) != CIA_OK) return s2;
-        if ((s2 = alloc_bytes(pl, (void **)&d.cs_acc, (size_t)n * sizeof(float4))) != CIA_OK) return s2;
-        if ((s2 = alloc_bytes(pl, &d.cs_feat, (size_t)n * CIA_BASIS_RANK * 2)) != CIA_OK) return s2;
-        if ((s2 = upload<float>(pl, &d.cs_params, nullptr, CIA_BASIS_PARAMS)) != CIA_OK) return s2;
-        if ((s2 = alloc_bytes(pl, (void **)&d.cs_cen, (size_t)std::max<int64_t>(M, 1) * sizeof(float2))) != CIA_OK)
-            return s2;
-        // nodes of the learned-basis check: evenly spaced over the community nodes
-        const int64_t nc = pl->off[M];
-        pl->cs_check_count = std::min<int64_t>(512, nc);
-        std::vector<int32_t> cn(pl->cs_check_count), cc(pl->cs_check_count);
-        for (int64_t k = 0; k < pl->cs_check_count; ++k) {
-            cn[k] = (int32_t)((2 * k + 1) * nc / (2 * pl->cs_check_count));
-            cc[k] = comm_of[cn[k]];
-        }
-        UP(d.cs_check_nodes, cn.data(), cn.size());
-        UP(d.cs_check_comm, cc.data(), cc.size());
-        if ((s2 = upload<double>(pl, &d.cs_check_out, nullptr, (size_t)std::max<int64_t>(1, pl->cs_check_count) * 2)) !=
-            CIA_OK)
-            return s2;
-        UP(d.tile_desc, tdesc.data(), tdesc.size());
+        UPT(d.tile_desc, tdesc.data(), tdesc.size());
         CIA_CUDA_TRY(cudaDeviceSynchronize());
         return CIA_OK;
     }
-    if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
-    if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
-    for (int b = 0; b < 2; ++b) {
-        if ((s2 = alloc_bytes(pl, &d.ph[b], (size_t)pl->p * pl->ph_stride * 2 * rb)) != CIA_OK) return s2;
-        if ((s2 = upload<double>(pl, &d.part[b], nullptr, (size_t)pl->n_tiles * pl->p * 2)) != CIA_OK)
-            return s2;
-    }
-    if ((s2 = alloc_bytes(pl, &d.wdt_half, n * rb)) != CIA_OK) return s2;
-    if ((s2 = alloc_bytes(pl, &d.wdt_full, n * rb)) != CIA_OK) return s2;
-    if ((s2 = upload<double>(pl, &d.wdt_full64, nullptr, n)) != CIA_OK) return s2;
-    if (pl->triadic && pl->has_direct && (s2 = alloc_bytes(pl, &d.tri, n * rb)) != CIA_OK) return s2;
     // The persistent TMA pipeline needs at most 256 nodes per tile (one
     // consumer thread per node) and, in shared memory, the CTA's tile
     // descriptors and observables plus a ring of at least two tile buffers
@@ -677,8 +791,8 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
                 tdesc[u].pbuf = tile_comm[u] >= 0 ? (r & 1) : 0;
             }
         }
-        UP(d.cta_tile_begin, ctb.data(), ctb.size());
-        UP(d.cta_runs, runs.data(), runs.size());
+        UPT(d.cta_tile_begin, ctb.data(), ctb.size());
+        UPT(d.cta_runs, runs.data(), runs.size());
     }
     if (pl->staging == 0) {
         int optin = 0;
@@ -690,10 +804,18 @@ static cia_status build_plan(const cia_graph *g, const int32_t *community, const
             if (pipeline_smem_bytes(pl, st) <= (size_t)optin - 1024) pl->ring_stages = st;
         if (pl->ring_stages == 0) pl->staging = 1;
     }
-    UP(d.tile_desc, tdesc.data(), tdesc.size());
-#undef UP
+    UPT(d.tile_desc, tdesc.data(), tdesc.size());
+#undef UPT
     CIA_CUDA_TRY(cudaDeviceSynchronize());
     return CIA_OK;
+}
+
+static cia_status build_plan(const cia_graph *g, const int32_t *community, const double *omega,
+                             const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
+    cia_status st = build_split(g, community, omega, cp, opt, pl);
+    if (st != CIA_OK) return st;
+    pl->staging_req = pl->staging;
+    return build_tiles(pl);
 }
 
 extern "C" cia_status cia_plan_create(const cia_graph *g, const int32_t *community,
@@ -725,6 +847,103 @@ extern "C" cia_status cia_plan_create(const cia_graph *g, const int32_t *communi
     return CIA_OK;
 }
 
+extern "C" cia_status cia_plan_create_batch(int64_t B, const cia_graph *graphs, const int32_t *const *communities,
+                                            const double *const *omegas, const cia_coupling *coupling,
+                                            const cia_options *opt, cia_plan_t **out) {
+    clear_error();
+    if (!out) return fail(CIA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (B < 1 || !graphs || !communities || !coupling)
+        return fail(CIA_ERR_INVALID_ARG, "need B >= 1 and non-NULL graphs, communities and coupling");
+    if (coupling->model != CIA_MODEL_KURAMOTO)
+        return fail(CIA_ERR_UNSUPPORTED, "ensembles support the Kuramoto model only");
+    cia_plan *pl = new (std::nothrow) cia_plan();
+    if (!pl) return fail(CIA_ERR_OOM, "host allocation of the plan failed");
+    cia_status st = CIA_OK;
+    try {
+        // the disjoint union: node ids and community labels offset per instance
+        pl->B = B;
+        pl->inst_off.assign(B + 1, 0);
+        pl->inst_comm_off.assign(B + 1, 0);
+        int64_t nnz = 0;
+        for (int64_t i = 0; i < B && st == CIA_OK; ++i) {
+            const cia_graph &g = graphs[i];
+            if (g.n < 1 || !g.rowptr || (!g.col && g.rowptr[g.n] > 0) || !communities[i])
+                st = fail(CIA_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": empty graph or NULL array");
+            else {
+                int32_t mx = -1;
+                for (int64_t v = 0; v < g.n; ++v) mx = std::max(mx, communities[i][v]);
+                pl->inst_off[i + 1] = pl->inst_off[i] + g.n;
+                pl->inst_comm_off[i + 1] = pl->inst_comm_off[i] + (int64_t)mx + 1;
+                nnz += g.rowptr[g.n];
+            }
+        }
+        if (st == CIA_OK && (pl->inst_off[B] > (int64_t)INT32_MAX - 1 || pl->inst_comm_off[B] > (int64_t)INT32_MAX))
+            st = fail(CIA_ERR_INVALID_ARG, "the ensemble has too many nodes or communities");
+        if (st == CIA_OK) {
+            const int64_t n = pl->inst_off[B];
+            std::vector<int64_t> rowptr(n + 1, 0);
+            std::vector<int32_t> col(nnz), lab(n);
+            std::vector<double> om(n, 0.0);
+            int64_t w = 0;
+            for (int64_t i = 0; i < B; ++i) {
+                const cia_graph &g = graphs[i];
+                const int64_t o = pl->inst_off[i];
+                for (int64_t v = 0; v < g.n; ++v) {
+                    for (int64_t e = g.rowptr[v]; e < g.rowptr[v + 1]; ++e) {
+                        const int32_t c = g.col[e];
+                        // out-of-range columns stay out of range of the instance (checked below)
+                        col[w++] = (c < 0 || c >= g.n) ? -1 : (int32_t)(c + o);
+                    }
+                    rowptr[o + v + 1] = w;
+                    const int32_t l = communities[i][v];
+                    lab[o + v] = l < 0 ? l : (int32_t)(l + pl->inst_comm_off[i]);
+                    if (omegas && omegas[i]) om[o + v] = omegas[i][v];
+                }
+            }
+            cia_graph u{n, rowptr.data(), col.data()};
+            st = build_plan(&u, lab.data(), om.data(), coupling, opt, pl);
+        }
+    } catch (const std::bad_alloc &) {
+        st = fail(CIA_ERR_OOM, "host allocation failed while planning");
+    } catch (const std::exception &e) {
+        st = fail(CIA_ERR_INVALID_ARG, std::string("planning failed: ") + e.what());
+    }
+    if (st != CIA_OK) {
+        free_all(pl);
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_index_bytes, int staging) {
+    clear_error();
+    if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
+    const int tn = tile_nodes ? tile_nodes : (pl->model == CIA_MODEL_CUCKER_SMALE ? 128 : 256);
+    if (tn < 32 || tn > 1024 || tn % 32 || (pl->model == CIA_MODEL_CUCKER_SMALE && tn > 128))
+        return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024] (<= 128 for Cucker-Smale)");
+    const int tib = tile_index_bytes ? tile_index_bytes : 32768;
+    if (tib < 256 || tib % 16) return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
+    if (staging != 0 && staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
+    int dev = -1;
+    CIA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != pl->device) return fail(CIA_ERR_INVALID_ARG, "plan belongs to another device");
+    CIA_CUDA_TRY(cudaDeviceSynchronize());
+    pl->tile_nodes = tn;
+    pl->tile_index_bytes = tib;
+    pl->staging_req = pl->model == CIA_MODEL_CUCKER_SMALE ? 1 : staging;
+    cia_status st;
+    try {
+        st = build_tiles(pl);
+    } catch (const std::bad_alloc &) {
+        st = fail(CIA_ERR_OOM, "host allocation failed while re-tiling");
+    }
+    pl->needs_load = true;
+    return st;
+}
+
 extern "C" cia_status cia_plan_destroy(cia_plan_t *plan) {
     clear_error();
     if (!plan) return CIA_OK;
@@ -754,6 +973,7 @@ extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *inf
     info->max_tile_index_bytes = pl->max_tile_idx_bytes;
     info->model = pl->model;
     info->state_dim = pl->state_dim;
+    info->instances = pl->B;
     return CIA_OK;
 }
 

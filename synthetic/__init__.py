@@ -4,12 +4,13 @@ Nothing here computes any part of the community integration method.
 """
 from .graphs import (Graph, complete_graph_communities, equal_sizes, lognormal_sizes,
                      random_labels_graph, rng_for, sbm_graph)
-from .workloads import (CuckerSmaleWorkload, KuramotoWorkload, as_fp32_values, cached,
-                        cucker_smale, kuramoto_ho, kuramoto_lognormal, kuramoto_sbm_small)
+from .workloads import (CuckerSmaleWorkload, EnsembleWorkload, KuramotoWorkload, as_fp32_values,
+                        cached, cucker_smale, kuramoto_ensemble, kuramoto_ho, kuramoto_lognormal,
+                        kuramoto_sbm_small)
 
 __all__ = [
     "Graph", "complete_graph_communities", "equal_sizes", "lognormal_sizes",
     "random_labels_graph", "rng_for", "sbm_graph", "CuckerSmaleWorkload",
     "KuramotoWorkload", "as_fp32_values", "cached", "cucker_smale", "kuramoto_ho",
-    "kuramoto_lognormal", "kuramoto_sbm_small",
+    "kuramoto_lognormal", "kuramoto_sbm_small", "EnsembleWorkload", "kuramoto_ensemble",
 ]

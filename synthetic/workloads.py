@@ -16,6 +16,11 @@ Workloads (sizes, distributions and integrator settings):
   pairwise K1=1 plus triadic K2=2, omega ~ N(0,1), dt=0.005, 1000 steps.
 * ``cucker_smale``: N=131072, 128 communities of 1024, p_in=0.9, inter degree
   6, s ~ U[0,10]^2, v ~ N(0,1)^2, dt=0.01, 1000 steps.
+* ``kuramoto_ensemble``: independent Kuramoto networks, per instance
+  N_i ~ U{256..16384}, M_i ~ U{2..32} communities of equal size (+-1),
+  p_in ~ U[0.7, 1.0], integer inter degree ~ U{2..10}, omega ~ N(0,1),
+  theta0 ~ U[0, 2pi), K=4, RK4 dt=0.01, 500 steps, FP32 (4096 instances at
+  full size; tests and the measurement take the first few).
 
 ``scale`` shrinks the node count and community sizes for tests; the structure
 (p_in, degree, distributions) is unchanged.
@@ -119,6 +124,38 @@ def cucker_smale(scale: float = 1.0, steps: int = 1000) -> CuckerSmaleWorkload:
     s0 = as_fp32_values(rng.uniform(0.0, 10.0, size=(g.n, 2)))
     v0 = as_fp32_values(rng.normal(0.0, 1.0, size=(g.n, 2)))
     return CuckerSmaleWorkload("cucker_smale", g, s0, v0, 1.0, 1.0, 0.4, 0.01, steps, "fp32")
+
+
+@dataclasses.dataclass
+class EnsembleWorkload:
+    """Independent Kuramoto networks evaluated together (one plan, one launch per stage)."""
+
+    name: str
+    instances: list             # KuramotoWorkload per instance
+    K: float
+    dt: float
+    steps: int
+    precision: str
+
+
+def kuramoto_ensemble(instances: int = 4096, n_range=(256, 16384), steps: int = 500) -> EnsembleWorkload:
+    """The first `instances` networks of the seeded ensemble (instance i has
+    the same graph whatever `instances` is); n_range bounds N_i for tests."""
+    seed = SEED_BASE + 4
+    out = []
+    for i in range(instances):
+        rng = rng_for(seed + 7919 * (i + 1))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        m = int(rng.integers(2, 33))
+        m = min(m, n // 2)
+        p_in = float(rng.uniform(0.7, 1.0))
+        deg = int(rng.integers(2, 11))
+        g = sbm_graph(equal_sizes(n, m), p_in, inter_degree=float(deg), seed=seed + 7919 * (i + 1) + 1)
+        omega = as_fp32_values(rng.normal(0.0, 1.0, size=g.n))
+        theta0 = as_fp32_values(_phases(rng, g.n))
+        out.append(KuramotoWorkload("kuramoto_ensemble[%d]" % i, g, theta0, omega, 4.0,
+                                    np.array([1.0]), np.array([0.0]), 0.01, steps, "fp32"))
+    return EnsembleWorkload("kuramoto_ensemble", out, 4.0, 0.01, steps, "fp32")
 
 
 @functools.lru_cache(maxsize=4)

@@ -80,3 +80,47 @@ def test_bad_options_rejected(lib):
     with pytest.raises(lib.CiaError) as e:
         _plan(lib, [0, 1, 2], [1, 0], [0, -3])
     assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+
+
+def test_batch_validation_on_host(lib):
+    good = (np.array([0, 1, 2]), np.array([1, 0]))
+    bad = (np.array([0, 1, 1]), np.array([1]))          # asymmetric
+    with pytest.raises(lib.CiaError) as e:
+        lib.Plan.batch([good, bad], [[0, 0], [0, 0]])
+    assert e.value.status_name == "CIA_ERR_INVALID_GRAPH"
+    with pytest.raises(lib.CiaError) as e:
+        lib.Plan.batch([], [])
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+    with pytest.raises(lib.CiaError) as e:
+        lib.Plan.batch([good], [[0, 0]], model="kuramoto_ho")
+    assert e.value.status_name == "CIA_ERR_UNSUPPORTED"
+    with pytest.raises(lib.CiaError) as e:
+        lib.Plan.batch([good, (np.array([0, 1, 2]), np.array([5, 0]))], [[0, 0], [0, 0]])
+    assert e.value.status_name == "CIA_ERR_INVALID_GRAPH"
+
+
+def test_cucker_smale_options_on_host(lib):
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], model="cucker_smale", precision="fp64")
+    assert e.value.status_name == "CIA_ERR_UNSUPPORTED"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], np.zeros(2), model="cucker_smale", precision="fp32")
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], model="cucker_smale", precision="fp32", sigma=0.0)
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], model="cucker_smale", precision="fp32", tile_nodes=256)
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+    with pytest.raises(lib.CiaError) as e:
+        _plan(lib, [0, 1, 2], [1, 0], [0, 0], model="cucker_smale", precision="fp32",
+              beta=float("nan"))
+    assert e.value.status_name == "CIA_ERR_NUMERIC"
+
+
+def test_basis_rejects_bad_parameters_on_host(lib):
+    with pytest.raises(lib.CiaError) as e:
+        lib.Basis(np.full(lib.Basis.PARAMS, np.inf, dtype=np.float32))
+    assert e.value.status_name == "CIA_ERR_NUMERIC"
+    with pytest.raises(ValueError):
+        lib.Basis(np.zeros(10, dtype=np.float32))

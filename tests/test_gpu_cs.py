@@ -302,3 +302,27 @@ def test_learn_fit_gains_over_untrained(P, oracle_mod):
     plan.integrate(x.clone(), w.dt, 1)
     after = plan.check_report()["last_error"]
     assert after < 0.2 * before, (before, after)
+
+
+def test_full_size_direct_and_constant_cia(P, oracle_mod):
+    """The N = 131072 workload in the bench's launch configuration: the direct
+    RHS against the FP64 oracle, and the CIA with a constant feature map (exact
+    for a constant weight) against the oracle's direct sum."""
+    import torch
+    import synthetic as S
+    w = S.cached("cucker_smale", 1.0)
+    g = w.graph
+    x = _x0(w)
+    xd = torch.from_numpy(x.ravel()).cuda()
+    plan = _plan(P, w)
+    out = plan.rhs(xd, method="direct").cpu().numpy().reshape(-1, 4)
+    ref = oracle_mod.cs_direct(g.rowptr, g.col, x, w.K, w.sigma, w.beta)
+    assert _rel_v(out, ref) <= 1e-5
+    vec = oracle_mod.pack_params(_params(28, const=True)).astype(np.float32)
+    b2 = oracle_mod.bf16_round(vec)[-R:]
+    K = float((b2 * b2).sum())
+    plan2 = _plan(P, w, K=K, beta=0.0, build_direct=False)
+    plan2.set_basis(P.Basis(vec))
+    out2 = plan2.rhs(xd).cpu().numpy().reshape(-1, 4)
+    ref2 = oracle_mod.cs_direct(g.rowptr, g.col, x, K, w.sigma, 0.0)
+    assert _rel_v(out2, ref2) <= 1e-5
