@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-method timing")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle RK4 steps in the CPU sample")
+    ap.add_argument("--no-cs", action="store_true",
+                    help="skip the Cucker-Smale (learned basis) secondary workload")
+    ap.add_argument("--cs-pairs", type=int, default=10_000_000, help="training pairs of the CS basis")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble secondary workload")
+    ap.add_argument("--ens-instances", type=int, default=32,
+                    help="instances of the seeded 4096-network ensemble to run")
+    ap.add_argument("--only", choices=["cs", "ensemble"], default=None,
+                    help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
 
 
@@ -221,6 +229,152 @@ def reference_arm(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ Cucker--Smale (secondary line)
+
+CS_WORKLOAD = ("cucker_smale: N=131072, 128 communities of 1024, p_in=0.9, inter degree 6, "
+               "s~U[0,10]^2, v~N(0,1)^2, eta=(1+r^2)^-0.4, learned rank-64 basis (2-128-64 MLP, "
+               "BF16 tcgen05, FP32 accumulate) trained on pairs from direct trajectories, RK4 "
+               "dt=0.01, FP32 state + FP64 time accumulation")
+
+
+def cs_stage_bytes(info: dict) -> float:
+    """Algorithmic bytes of one CIA stage of the Cucker--Smale model (the stage
+    launch plus the feature launch), averaged over the four RK4 stages.
+
+    Per node: stage state read (16 B, gathers reuse it), next state written
+    (16 B) and read again by the feature launch (16 B), FP64 master read
+    (32 B; written in the final stage: +8 B on average), accumulator read in
+    3 of 4 stages and written (12 + 16 B), BF16 features read and written
+    (2 x 128 B).  Per missing link a 16-bit index, per inter link a 32-bit
+    index.
+    """
+    per_node = 16 + 16 + 16 + 32 + 8 + 12 + 16 + 256
+    return info["n"] * per_node + info["nnz_missing"] * 2 + info["nnz_inter"] * 4
+
+
+def cs_basis_init(seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, 0.4, (128, 2))
+    b1 = rng.uniform(-2.0, 2.0, 128)
+    W2 = rng.normal(0.0, 0.3 / np.sqrt(128), (64, 128))
+    b2 = np.full(64, 0.05)
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2]).astype(np.float32)
+
+
+def cs_leg(args, torch, cia, flush) -> dict:
+    """Learned-basis CIA vs the direct method on the Cucker--Smale workload:
+    basis training from direct trajectories (timed), RHS errors against the
+    FP64 oracle at the initial state, RK4 step throughput of both methods."""
+    import oracle
+    import synthetic as S
+    oracle.set_num_threads(host_cores())
+    w = S.cucker_smale(args.scale)
+    g = w.graph
+    plan = cia.Plan(g.rowptr, g.col, g.labels, None, K=w.K, sigma=w.sigma, beta=w.beta,
+                    precision="fp32", model="cucker_smale", build_direct=True)
+    info = plan.info()
+    x0np = np.concatenate([w.s0, w.v0], axis=1)
+    x0 = torch.from_numpy(x0np.ravel().copy()).cuda()
+    basis = cia.Basis(cs_basis_init(2203166574))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fit = plan.learn_fit(basis, x0, dt=w.dt, steps=100, snapshots=10, pairs=args.cs_pairs,
+                         seed=2203166575, batch=16384, epochs=2, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # accuracy at the initial state against the FP64 oracle (velocity part)
+    ref = oracle.cs_direct(g.rowptr, g.col, x0np, w.K, w.sigma, w.beta)
+    errs = {}
+    for m in ("cia", "direct"):
+        got = plan.rhs(x0, method=m).cpu().numpy().reshape(-1, 4)
+        errs[m] = float(np.abs(got[:, 2:] - ref[:, 2:]).max() / np.abs(ref[:, 2:]).max())
+    plan.set_check(every=1, bound=1e9)
+    plan.integrate(x0.clone(), w.dt, 1)
+    check = plan.check_report()["last_error"]
+    plan.set_check(every=0, bound=0.0)
+    steps = max(3, args.steps // 2)
+    ms, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
+    dms, dprof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "direct", flush, True)
+    total, dtotal = float(sum(ms)), float(sum(dms))
+    stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    sb = cs_stage_bytes(info)
+    return {
+        "workload": CS_WORKLOAD, "n": g.n, "nnz_graph": info["nnz_graph"],
+        "nnz_missing": info["nnz_missing"], "nnz_inter": info["nnz_inter"], "steps": steps,
+        "cia": {"value": g.n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
+                "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9},
+        "direct": {"value": g.n * steps / (dtotal / 1e3), "unit": UNIT, "ms_per_step": dtotal / steps},
+        "speedup_cia_over_direct": dtotal / max(total, 1e-12),
+        "error_vs_fp64_oracle": {"cia_rhs_velocity_rel": errs["cia"],
+                                 "direct_rhs_velocity_rel": errs["direct"],
+                                 "sampled_check_err_over_ref": check},
+        "basis_training": {"pairs": fit["pairs"], "optimizer_steps": fit["steps"],
+                           "first_loss": fit["first_loss"], "last_epoch_loss": fit["last_epoch_loss"],
+                           "seconds_incl_trajectory": train_s},
+    }
+
+
+# ------------------------------------------------------------------ batched ensemble (secondary line)
+
+ENS_WORKLOAD = ("kuramoto_ensemble: the first {B} of 4096 seeded independent Kuramoto networks, "
+                "N_i~U{{256..16384}}, M_i~U{{2..32}} equal communities, p_in~U[0.7,1], inter degree "
+                "U{{2..10}}, omega~N(0,1), K=4, RK4 dt=0.01, FP32 + FP64 time accumulation; one "
+                "launch per RK4 stage for all instances, r(t) per instance")
+
+
+def ensemble_leg(args, torch, cia, flush) -> dict:
+    """All instances in one plan: autotuned tiling, per-step device time with
+    the L2 flushed between steps, the same steps replayed from one CUDA graph
+    per step (L2 warm), and the RHS error of every instance against the FP64
+    oracle."""
+    import oracle
+    import synthetic as S
+    oracle.set_num_threads(host_cores())
+    e = S.kuramoto_ensemble(args.ens_instances)
+    inst = e.instances
+    B = len(inst)
+    plan = cia.Plan.batch([(w.graph.rowptr, w.graph.col) for w in inst], [w.graph.labels for w in inst],
+                          [w.omega for w in inst], K=e.K, precision="fp32")
+    x0np = np.concatenate([w.theta0 for w in inst])
+    x0 = torch.from_numpy(x0np.copy()).cuda()
+    tune = plan.autotune(x0, e.dt, steps=5)
+    info = plan.info()
+    n = info["n"]
+    out = plan.rhs(x0).cpu().numpy()
+    err, o = 0.0, 0
+    for w in inst:
+        m = w.graph.n
+        ref = oracle.kuramoto_direct(w.graph.rowptr, w.graph.col, w.theta0, w.omega, e.K)
+        err = max(err, coupling_rel_err(out[o:o + m], ref, w.omega))
+        o += m
+    steps = max(3, args.steps // 2)
+    ms, prof = timed_steps(torch, plan, x0, e.dt, steps, args.warmup, "cia", flush, True)
+    total = float(sum(ms))
+    # graph replay: all steps in one advance call, order parameters per instance
+    r = torch.zeros(steps * B, dtype=torch.float64, device="cuda")
+    plan.state_load(x0)
+    plan.advance(e.dt, args.warmup, r_out=torch.zeros(args.warmup * B, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.advance(e.dt, steps, r_out=r)
+    b.record()
+    torch.cuda.synchronize()
+    gms = a.elapsed_time(b)
+    stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    sb = stage_bytes(info, "fp32")
+    return {
+        "workload": ENS_WORKLOAD.format(B=B), "instances": B, "n": n, "nnz_graph": info["nnz_graph"],
+        "nnz_missing": info["nnz_missing"], "nnz_inter": info["nnz_inter"], "steps": steps,
+        "value": n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
+        "l2": "flushed between timed steps",
+        "graph_replay": {"value": n * steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / steps,
+                         "l2": "warm (steps replayed back to back)", "with_order_parameters": True},
+        "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
+        "autotune": tune, "rhs_coupling_rel_err_vs_fp64_oracle_max_over_instances": err,
+    }
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, profile: bool):
@@ -264,6 +418,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2203_16657_gb300 as cia
+    if args.only:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        leg = cs_leg if args.only == "cs" else ensemble_leg
+        print(json.dumps({"leg": args.only, **leg(args, torch, cia, flush)}), flush=True)
+        return 0
     w = S.kuramoto_lognormal(scale=args.scale)
     g = w.graph
     plan = cia.Plan(g.rowptr, g.col, g.labels, w.omega, K=w.K, precision="fp32",
@@ -319,6 +478,13 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    cs = None
+    if not args.no_cs and world == 1:
+        cs = cs_leg(args, torch, cia, flush)
+    ens = None
+    if not args.no_ensemble and world == 1:
+        ens = ensemble_leg(args, torch, cia, flush)
+
     pk = peaks()
     stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
     sb = stage_bytes(info, "fp32")
@@ -361,6 +527,10 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if cs is not None:
+        line["cucker_smale"] = cs
+    if ens is not None:
+        line["ensemble"] = ens
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

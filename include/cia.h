@@ -114,10 +114,14 @@ typedef struct {
                                    a multiple of 32, <= 1024 (<= 128 for Cucker--Smale) */
     int group_size;             /* threads per row of the direct method's CSR sums: 0 = default,
                                    else 4, 8, 16 or 32 (the CIA sums use one thread per row) */
-    int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (32768); a multiple of 16.
+    int tile_index_bytes;       /* sparse-index bytes per tile, 0 = default (65536); a multiple of 16.
                                    A tile is cut at tile_nodes rows or at this many index bytes. */
-    int staging;                /* 0 = auto: TMA bulk copies of each tile's indices and community
-                                   phasors into shared memory when they fit; 1 = plain loads */
+    int staging;                /* CIA stage kernel: 0 = auto (2 when it fits); 1 = plain loads,
+                                   one CTA per tile; 2 = one CTA per tile with the community's
+                                   phasors copied (TMA) into shared memory; 3 = persistent
+                                   warp-specialised CTAs with TMA copies of each tile's indices
+                                   and community phasors.  2 and 3 fall back to 1 when their
+                                   buffers do not fit. */
     int use_graphs;             /* 0 = auto: cia_advance replays one captured CUDA graph per RK4
                                    step when it advances >= 2 steps (not while profiling);
                                    1 = plain launches only */
@@ -140,7 +144,7 @@ typedef struct {
     int group_size;
     int tile_nodes;
     int missing_index_bytes;    /* 2 (16-bit community-local index) or 4 */
-    int staging;                /* 0 = TMA bulk staging in use, 1 = plain loads */
+    int staging;                /* the kernel in use: 1, 2 or 3 as in cia_options */
     int group_size_direct;      /* threads per row of the direct method */
     int64_t max_tile_index_bytes; /* largest sparse-index footprint of a tile */
     int model;                  /* cia_model */
@@ -205,9 +209,12 @@ typedef struct {
 } cia_tune_report;
 
 /* Autotuner: time `steps` RK4 steps of the CIA (after two warm-up steps) for
- * each candidate tiling -- tile_index_bytes in {16384, 32768, 49152} with TMA
- * staging and, with plain loads, tile_nodes in {128, 256} -- starting from the
- * state x (device, n x d doubles, original order), and keep the fastest.
+ * each candidate tiling -- the window kernel (staging 2) with 256-row tiles
+ * and tile_index_bytes 32768, 65536 or 98304 or with 128-row tiles and 32768,
+ * the pipelined (3) and the plain (1) kernel with 256-row tiles and 32768;
+ * for Cucker--Smale, 64- or 128-row tiles with 16384 or 32768 -- starting
+ * from the state x (device, n x d doubles, original order), and keep the
+ * fastest.
  * Leaves x's state resident (cia_state_load).  Synchronises the stream. */
 cia_status cia_plan_autotune(cia_plan_t *plan, const double *x, double dt, int64_t steps,
                              cia_tune_report *report, void *stream);

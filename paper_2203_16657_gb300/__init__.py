@@ -57,7 +57,7 @@ class Plan:
         self._keep = []
         cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
-                           int(group_size), int(tile_index_bytes), {"auto": 0, "plain": 1}[staging],
+                           int(group_size), int(tile_index_bytes), _abi.STAGING[staging],
                            0 if use_graphs else 1)
         handle = ctypes.c_void_p()
         if _batch is not None:
@@ -215,7 +215,7 @@ class Plan:
 
     def retile(self, tile_nodes=0, tile_index_bytes=0, staging="auto"):
         _abi.check(self._lib.cia_plan_retile(self._h, int(tile_nodes), int(tile_index_bytes),
-                                             {"auto": 0, "plain": 1}[staging]))
+                                             _abi.STAGING[staging]))
 
     def autotune(self, x, dt, steps=10, stream=None) -> dict:
         """Time the candidate tilings from state x and keep the fastest."""

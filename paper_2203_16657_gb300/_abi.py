@@ -20,6 +20,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
+STAGING = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}
 MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2}
 
 

@@ -64,9 +64,9 @@ cia_status check_plan(cia_plan *pl, int method) {
                                                  " nodes) does not fit the shared-memory community tile");
         return CIA_OK;
     }
-    const size_t need = (method == CIA_METHOD_CIA && pl->staging == 0)
-                            ? pipeline_smem_bytes(pl, pl->ring_stages)
-                            : stage_smem_bytes(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA);
+    const size_t need = (method == CIA_METHOD_CIA && pl->staging == 3)   ? pipeline_smem_bytes(pl, pl->ring_stages)
+                        : (method == CIA_METHOD_CIA && pl->staging == 2) ? window_smem_bytes(pl)
+                        : stage_smem_bytes(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA);
     if (method == CIA_METHOD_DIRECT && pl->triadic &&
         (size_t)(pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->max_comm > (size_t)optin - 1024)
         return fail(CIA_ERR_UNSUPPORTED, "the direct triadic term stages a whole community in shared memory; "
@@ -418,8 +418,10 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
         for (int tn : {64, 128})
             for (int tib : {16384, 32768}) cands.push_back({tn, tib, 1});
     } else {
-        for (int tib : {16384, 32768, 49152}) cands.push_back({256, tib, 0});
-        for (int tn : {128, 256}) cands.push_back({tn, 32768, 1});
+        for (int tib : {32768, 65536, 98304}) cands.push_back({256, tib, 2});
+        cands.push_back({128, 32768, 2});
+        cands.push_back({256, 32768, 3});
+        cands.push_back({256, 32768, 1});
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -441,7 +443,7 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
     for (size_t i = 0; i < cands.size(); ++i) {
         const Cand &c = cands[i];
         if ((st = cia_plan_retile(pl, c.tn, c.tib, c.staging)) != CIA_OK) return st;
-        if (c.staging == 0 && pl->staging != 0) continue;   // the TMA pipeline did not fit: same as plain
+        if (c.staging != pl->staging) continue;   // the kernel does not fit: another candidate covers its fallback
         if ((st = cia_state_load(pl, x, stream)) != CIA_OK) return st;
         if ((st = check_plan(pl, CIA_METHOD_CIA)) != CIA_OK) continue;   // does not fit this GPU
         if ((st = cia_advance(pl, CIA_METHOD_CIA, dt, 2, nullptr, stream)) != CIA_OK && st != CIA_ERR_FALLBACK)

@@ -58,6 +58,7 @@ struct DeviceBuffers {
     // A missing list longer than 64 entries is split into chunks whose
     // partial sums are added per row in chunk order.
     cia::TileDesc *tile_desc = nullptr; // [T]
+    int32_t *tile_order = nullptr;      // [T] launch order of the per-tile kernels (costliest first)
     unsigned char *blob = nullptr;      // [sum of blob bytes]
     int32_t *cta_tile_begin = nullptr;  // [n_ctas+1] tile range of each persistent CTA
     int32_t *cta_runs = nullptr;        // [n_ctas] community runs (maximal same-community tile runs) per CTA
@@ -134,7 +135,8 @@ struct cia_plan {
     int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0, max_cta_runs = 0;
     int n_ctas = 0;                     // persistent grid of the pipelined CIA kernel (one per SM)
     int ring_stages = 0;                // tile buffers of its TMA ring
-    int staging = 0;                    // 0 = persistent TMA pipeline, 1 = plain loads
+    int staging = 2;                    // kernel: 1 = plain loads, 2 = per-tile CTAs with the community
+                                        // window in shared memory, 3 = persistent TMA pipeline
     double dt_cached = 0.0;             // dt the wdt_* buffers were computed for
     bool wdt_valid = false;
     std::vector<int32_t> perm;          // host copy of kappa
@@ -194,6 +196,7 @@ cudaError_t launch_rk4_stage(cia_plan *pl, int method, int stage, int ph_in_slot
 cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
 size_t stage_smem_bytes(const cia_plan *pl, int method);
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
+size_t window_smem_bytes(const cia_plan *pl);
 
 // Drop the cached CUDA graph of an RK4 step (api.cu).
 void invalidate_graphs(cia_plan *pl);

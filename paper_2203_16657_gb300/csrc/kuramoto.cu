@@ -32,6 +32,12 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+#ifndef CIA_WINDOW_MIN_BLOCKS
+#define CIA_WINDOW_MIN_BLOCKS 4    // resident CTAs per SM the window kernel's registers are sized for
+#endif
+#ifndef CIA_WINDOW_VECTORS
+#define CIA_WINDOW_VECTORS 2       // missing-index vectors of a chunk loaded before any is used (<= 8)
+#endif
 constexpr int kMaxChunks = 512;    // missing-list chunks per tile (partial sums in shared memory)
 
 template <typename T> struct Vec2;
@@ -39,6 +45,14 @@ template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
 __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+// Component-wise sum of two complex numbers: one packed FP32 add (two
+// IEEE round-to-nearest additions in one instruction) or two FP64 adds.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<uint64_t *>(&a)), "l"(*reinterpret_cast<uint64_t *>(&b)));
+    return *reinterpret_cast<float2 *>(&r);
+}
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
 __device__ __forceinline__ void sincos_t(float y, float *s, float *c) { sincosf(y, s, c); }
 __device__ __forceinline__ void sincos_t(double y, double *s, double *c) { sincos(y, s, c); }
@@ -103,6 +117,7 @@ struct StageParams {
     const int32_t *tile_comm, *tile_first, *tile_count, *comm_tile_begin;
     // CIA: sliced-ELL sparse remainder, one blob per tile
     const TileDesc *tile_desc;
+    const int32_t *tile_order;  // launch order of the per-tile kernels (NULL: tile = block)
     const unsigned char *blob;
     // direct: padded full CSR
     const int64_t *sp_rowptr;
@@ -274,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) cia_stage_kernel(const StageParams<T
     __shared__ C zc[P];
     __shared__ double red[kWarps][2 * P];
 
-    const int t = blockIdx.x;
+    const int t = a.tile_order ? a.tile_order[blockIdx.x] : (int)blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const int64_t stride = a.ph_stride;
     const bool dense = d.comm >= 0;
@@ -358,6 +373,225 @@ __global__ void __launch_bounds__(kThreads) cia_stage_kernel(const StageParams<T
     __syncthreads();
     finalize_tile<T, P, MODE>(a, t, d.first, d.count, dense, zc, sWi, red,
                               [&](int k, int64_t m) { return __ldg(a.ph_in + k * stride + m); });
+}
+
+// CIA stage with the community window in shared memory, one CTA per tile.
+// Thread 0 copies the phasors of the tile's community (lo - shift ..
+// lo + lambda, rounded to 16 bytes) into shared memory with one bulk (TMA)
+// copy per harmonic; meanwhile warp 0 reduces the community observable and
+// every thread loads its node's inputs.  The entry after the community is set
+// to zero, so the padding index lambda of the missing lists reads a zero
+// phasor without a test.  Phase A (warp per slice, lane per row) then reads
+// the missing links from shared memory and the inter-community links from
+// global memory; Phase B is one thread per node.  Many CTAs share an SM, so
+// the hardware interleaves tiles at different phases.
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_kernel(const StageParams<T> a) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ C zc[P];
+    __shared__ double red[kWarps][2 * P];
+    __shared__ uint64_t wbar;
+
+    const int t = a.tile_order ? a.tile_order[blockIdx.x] : (int)blockIdx.x;
+    const TileDesc d = a.tile_desc[t];
+    const int64_t stride = a.ph_stride;
+    const bool dense = d.comm >= 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // bring the tile's index blob into L2 while the window, the observable
+    // and the node inputs are fetched: Phase A then reads it at L2 latency
+    if (threadIdx.x == 32) bulk_prefetch_l2(a.blob + d.blob_off, d.blob_bytes);
+    C *win = reinterpret_cast<C *>(smem_raw);                       // [P][ph_region]
+    C *sWm = win + (size_t)P * a.ph_region;                         // [P][kMaxChunks]
+    C *sWi = sWm + P * kMaxChunks;                                  // [P][tile_nodes]
+    const C *cw = win + d.shift;                                    // cw[k * ph_region + l], l in [0, lambda]
+    if (dense && threadIdx.x == 0) {
+        mbar_init(&wbar, 1);
+        const uint32_t bytes = (uint32_t)(((size_t)(d.shift + d.lam) * sizeof(C) + 15) & ~(size_t)15);
+        mbar_arrive_expect_tx(&wbar, bytes * P);
+        for (int k = 0; k < P; ++k)
+            bulk_g2s(win + (size_t)k * a.ph_region, a.ph_in + k * stride + (d.lo - d.shift), bytes, &wbar);
+    }
+    if (dense) community_observable<T, P>(a, d.comm, zc);
+    // node inputs of Phase B, loaded while the copy is in flight
+    const int r = threadIdx.x;
+    const int64_t m = d.first + r;
+    const bool live = r < d.count;
+    double theta_m = 0.0, wdt64_m = 0.0;
+    T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
+    int32_t perm_m = 0;
+    if (live) {
+        if (MODE == kRhs) {
+            omega_m = a.omega[m];
+            perm_m = a.perm[m];
+        } else {
+            theta_m = a.theta[m];
+            if (!a.first_stage) acc_m = a.acc[m];
+            if (MODE == kStage) wdt_m = a.wdt_next[m];
+            else wdt64_m = a.wdt64[m];
+        }
+    }
+    const unsigned char *b = a.blob + d.blob_off;
+    const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
+    const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
+    const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
+    const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
+    const uint32_t vt = live ? __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r) : 0u;
+    __syncthreads();   // the barrier's initialisation is visible to every waiter
+    bool ok = true;
+    if (dense) {
+        ok = mbar_wait_bounded(&wbar, 0, kWaitLimitNs);
+        if (!ok && threadIdx.x == 0) atomicExch(a.err_flag, 1);
+    }
+    if (__syncthreads_or(!ok)) {
+        // the copy may still land: wait for it once more before the CTA's
+        // shared memory is released
+        if (dense) mbar_wait_bounded(&wbar, 0, kWaitLimitNs);
+        return;
+    }
+    if (dense && threadIdx.x < P) win[(size_t)threadIdx.x * a.ph_region + d.shift + d.lam] = mk2(T(0), T(0));
+    __syncthreads();
+
+    for (int s = warp; s < d.nsl; s += kWarps) {
+        const uint4 sd = __ldg(sdesc + s);
+        const uint32_t rows = __ldg(srows + s * 32 + lane);
+        const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+        C macc[P], iacc[P];   // sum over the missing links (subtracted at the end), over the inter links
+#pragma unroll
+        for (int k = 0; k < P; ++k) macc[k] = iacc[k] = mk2(T(0), T(0));
+        const int4 *iv = ivec + sd.z + lane;
+        const uint4 *mv = mvec + sd.x + lane;
+        // every load of the slice's first index vectors is issued before any
+        // of them is used: inter-community vectors, then the first missing
+        // vectors; the inter gathers (global memory, longest latency) follow,
+        // and the missing links (shared memory) are summed while they fly
+        constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;
+        constexpr uint32_t kMv = (P == 1 && sizeof(T) == 4) ? CIA_WINDOW_VECTORS : 1;   // vectors loaded ahead
+        int4 qi[kPre];
+        uint4 qm[kMv];
+#pragma unroll
+        for (uint32_t j = 0; j < kPre; ++j)
+            if (j < sd.w) qi[j] = __ldg(iv + 32 * j);
+#pragma unroll
+        for (uint32_t j = 0; j < kMv; ++j)
+            if (j < sd.y) qm[j] = __ldg(mv + 32 * j);
+        C pre[kPre][4][P];
+        for (uint32_t j0 = 0; j0 < sd.w || j0 == 0; j0 += kPre) {
+            if (j0 > 0) {
+#pragma unroll
+                for (uint32_t j = 0; j < kPre; ++j)
+                    if (j0 + j < sd.w) qi[j] = __ldg(iv + 32 * (j0 + j));
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kPre; ++j) {
+                if (j0 + j < sd.w) {
+                    const int l4[4] = {qi[j].x, qi[j].y, qi[j].z, qi[j].w};
+#pragma unroll
+                    for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                        for (int k = 0; k < P; ++k) pre[j][hh][k] = __ldg(a.ph_in + k * stride + l4[hh]);
+                }
+            }
+            if (j0 == 0) {
+                for (uint32_t m0 = 0; m0 < sd.y; m0 += kMv) {
+                    if (m0 > 0) {
+#pragma unroll
+                        for (uint32_t j = 0; j < kMv; ++j)
+                            if (m0 + j < sd.y) qm[j] = __ldg(mv + 32 * (m0 + j));
+                    }
+#pragma unroll
+                    for (uint32_t j = 0; j < kMv; ++j) {
+                        if (m0 + j < sd.y) {
+                            const uint32_t w4[4] = {qm[j].x, qm[j].y, qm[j].z, qm[j].w};
+#pragma unroll
+                            for (int hh = 0; hh < 4; ++hh) {
+                                const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
+#pragma unroll
+                                for (int k = 0; k < P; ++k)
+                                    macc[k] = add2(macc[k], add2(cw[k * a.ph_region + l0], cw[k * a.ph_region + l1]));
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kPre; ++j) {
+                if (j0 + j < sd.w) {
+#pragma unroll
+                    for (int k = 0; k < P; ++k)
+                        iacc[k] = add2(iacc[k], add2(add2(pre[j][0][k], pre[j][1][k]), add2(pre[j][2][k], pre[j][3][k])));
+                }
+            }
+        }
+        if (mrow != 0xffffu) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) sWm[k * kMaxChunks + mrow] = mk2(-macc[k].x, -macc[k].y);
+        }
+        if (irow != 0xffffu) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) sWi[k * a.tile_nodes + irow] = iacc[k];
+        }
+    }
+    __syncthreads();
+    // Phase B, thread per node
+    T sre[P], sim[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
+    if (live) {
+        T coup = T(0);
+        C uk[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const C u = dense ? cw[k * a.ph_region + (int)(m - d.lo)] : __ldg(a.ph_in + k * stride + m);
+            uk[k] = u;
+            C w = sWi[k * a.tile_nodes + r];
+            for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
+                const C v = sWm[k * kMaxChunks + c];
+                w.x += v.x;
+                w.y += v.y;
+            }
+            T zr = w.x, zi = w.y;
+            if (dense) {
+                // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
+                zr += zc[k].x - u.x;
+                zi += zc[k].y - u.y;
+            }
+            const T re = zr * u.x + zi * u.y;
+            const T im = zi * u.x - zr * u.y;
+            coup += a.d_sin[k] * im + a.d_cos[k] * re;
+        }
+        coup *= a.tile_kn ? a.tile_kn[t] : a.k_over_n;
+        if (P >= 2 && dense && a.k2_over_n2 != T(0))
+            coup += a.k2_over_n2 * triadic_from_moments<T>(zc[0].x, zc[0].y, zc[P >= 2 ? 1 : 0].x,
+                                                           zc[P >= 2 ? 1 : 0].y, uk[0].x, uk[0].y,
+                                                           uk[P >= 2 ? 1 : 0].x, uk[P >= 2 ? 1 : 0].y);
+        if (a.tri) coup += a.tri[m];
+        if (MODE == kRhs) {
+            a.rhs_out[perm_m] = (double)omega_m + (double)coup;
+        } else {
+            const T accv = acc_m + a.b_s * coup;
+            T y;
+            if (MODE == kStage) {
+                a.acc[m] = accv;
+                y = (T)theta_m + wdt_m + a.c_next_dt * coup;
+            } else {
+                // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
+                const double th = wrap_pi(theta_m + wdt64_m + a.dt * (double)accv);
+                a.theta[m] = th;
+                y = (T)th;
+            }
+            C u[P];
+            phasors<T, P>(y, u);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                a.ph_out[k * stride + m] = u[k];
+                sre[k] = u[k].x;
+                sim[k] = u[k].y;
+            }
+        }
+    }
+    if (MODE == kRhs) return;
+    block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
 }
 
 // ---- persistent, warp-specialised CIA stage (the main path) ----------------
@@ -1054,6 +1288,7 @@ StageParams<T> base_params(cia_plan *pl, int method) {
     }
     a.k_over_n = (T)(pl->K / (double)pl->n);
     a.tile_kn = (const T *)pl->d.tile_kn;
+    a.tile_order = pl->d.tile_order;
     a.k2_over_n2 = (T)(pl->K2 / ((double)pl->n * (double)pl->n));
     a.tri = (method == Method::DIRECT && pl->triadic) ? (const T *)pl->d.tri : nullptr;
     a.off = pl->d.off;
@@ -1096,7 +1331,7 @@ cudaError_t launch_kernel(K kernel, size_t &configured, int64_t blocks, size_t s
 
 template <typename T, int P, int MODE>
 cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream_t s) {
-    if (pl->staging == 0) {
+    if (pl->staging == 3) {
         auto kernel = cia_pipeline_kernel<T, P, MODE>;
         static size_t cfg = 0;
         const size_t smem = pipeline_smem_bytes(pl, pl->ring_stages);
@@ -1107,6 +1342,10 @@ cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream
         }
         void *args[] = {const_cast<StageParams<T> *>(&a)};
         return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_ctas), dim3(kPipeThreads), args, smem, s);
+    }
+    if (pl->staging == 2) {
+        static size_t cfgw = 0;
+        return launch_kernel(cia_window_kernel<T, P, MODE>, cfgw, pl->n_tiles, window_smem_bytes(pl), &a, s);
     }
     static size_t cfg = 0;
     return launch_kernel(cia_stage_kernel<T, P, MODE>, cfg, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
@@ -1204,6 +1443,13 @@ cudaError_t stage_t(cia_plan *pl, int method, int stage, int slot, double dt, cu
 size_t stage_smem_bytes(const cia_plan *pl, int method) {
     const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
     return method == Method::DIRECT ? cb * (size_t)pl->tile_nodes : cb * (size_t)(kMaxChunks + pl->tile_nodes);
+}
+
+// Dynamic shared memory of the window kernel: the community phasor window
+// of every harmonic, chunk sums and inter sums.
+size_t window_smem_bytes(const cia_plan *pl) {
+    const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
+    return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes);
 }
 
 // Dynamic shared memory of the pipelined CIA kernel: a ring of tile buffers

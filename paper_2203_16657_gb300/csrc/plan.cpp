@@ -309,11 +309,11 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     pl->tile_nodes = (opt && opt->tile_nodes) ? opt->tile_nodes : 256;
     if (pl->tile_nodes < 32 || pl->tile_nodes > 1024 || pl->tile_nodes % 32)
         return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024]");
-    pl->tile_index_bytes = (opt && opt->tile_index_bytes) ? opt->tile_index_bytes : 32768;
+    pl->tile_index_bytes = (opt && opt->tile_index_bytes) ? opt->tile_index_bytes : 65536;
     if (pl->tile_index_bytes < 256 || pl->tile_index_bytes % 16)
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
-    if (pl->staging != 0 && pl->staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
+    if (pl->staging < 0 || pl->staging > 3) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2 or 3");
     pl->use_graphs = opt ? opt->use_graphs : 0;
     if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
@@ -748,9 +748,18 @@ static cia_status build_tiles(cia_plan *pl) {
     // consumer thread per node) and, in shared memory, the CTA's tile
     // descriptors and observables plus a ring of at least two tile buffers
     // and two community phasor windows; otherwise the kernels use plain loads.
+    // kernel choice: 0 (auto) takes the window kernel; the window and the
+    // pipelined kernel need 16-bit community-local indices, at most 256 rows
+    // per tile and shared memory for their buffers, else plain loads
     pl->ring_stages = 0;
-    if (pl->staging == 0 && (pl->miss_idx_bytes != 2 || pl->tile_nodes > 256)) pl->staging = 1;
-    if (pl->staging == 0) {
+    if (pl->staging == 0) pl->staging = 2;
+    if (pl->staging != 1 && (pl->miss_idx_bytes != 2 || pl->tile_nodes > 256)) pl->staging = 1;
+    if (pl->staging == 2) {
+        int optin = 0;
+        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+        if (window_smem_bytes(pl) > (size_t)optin - 1024) pl->staging = 1;
+    }
+    if (pl->staging == 3) {
         // contiguous tile ranges, one per SM, balanced by the bytes each tile
         // moves (index vectors, per-node state, community phasor windows)
         int sms = 0;
@@ -794,7 +803,7 @@ static cia_status build_tiles(cia_plan *pl) {
         UPT(d.cta_tile_begin, ctb.data(), ctb.size());
         UPT(d.cta_runs, runs.data(), runs.size());
     }
-    if (pl->staging == 0) {
+    if (pl->staging == 3) {
         int optin = 0;
         CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
         // a multiple of the two consumer groups, so that each ring buffer is
@@ -803,6 +812,17 @@ static cia_status build_tiles(cia_plan *pl) {
         for (int st = 4; st >= 2 && pl->ring_stages == 0; st -= 2)
             if (pipeline_smem_bytes(pl, st) <= (size_t)optin - 1024) pl->ring_stages = st;
         if (pl->ring_stages == 0) pl->staging = 1;
+    }
+    {
+        // launch order of the one-CTA-per-tile kernels: the costliest tiles
+        // first, so that the last CTAs to start are short (greedy longest-
+        // processing-time scheduling by the hardware's CTA dispatcher)
+        std::vector<int32_t> order(T);
+        for (int64_t t = 0; t < T; ++t) order[t] = (int32_t)t;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return tile_bytes[x] + 48 * (int64_t)tile_count[x] > tile_bytes[y] + 48 * (int64_t)tile_count[y];
+        });
+        UPT(d.tile_order, order.data(), order.size());
     }
     UPT(d.tile_desc, tdesc.data(), tdesc.size());
 #undef UPT
@@ -924,9 +944,9 @@ extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_i
     const int tn = tile_nodes ? tile_nodes : (pl->model == CIA_MODEL_CUCKER_SMALE ? 128 : 256);
     if (tn < 32 || tn > 1024 || tn % 32 || (pl->model == CIA_MODEL_CUCKER_SMALE && tn > 128))
         return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024] (<= 128 for Cucker-Smale)");
-    const int tib = tile_index_bytes ? tile_index_bytes : 32768;
+    const int tib = tile_index_bytes ? tile_index_bytes : 65536;
     if (tib < 256 || tib % 16) return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
-    if (staging != 0 && staging != 1) return fail(CIA_ERR_INVALID_ARG, "staging must be 0 or 1");
+    if (staging < 0 || staging > 3) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2 or 3");
     int dev = -1;
     CIA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != pl->device) return fail(CIA_ERR_INVALID_ARG, "plan belongs to another device");

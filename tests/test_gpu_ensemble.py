@@ -148,8 +148,8 @@ def test_ensemble_of_one_equals_single_plan(P):
     assert torch.equal(xa, xb)
 
 
-@pytest.mark.parametrize("tile_nodes,tib,staging", [(64, 4096, "plain"), (256, 16384, "auto"),
-                                                   (128, 49152, "auto")])
+@pytest.mark.parametrize("tile_nodes,tib,staging", [(64, 4096, "plain"), (256, 16384, "pipeline"),
+                                                   (128, 49152, "auto"), (256, 8192, "window")])
 def test_retile_keeps_results(P, oracle_mod, tile_nodes, tib, staging):
     import torch
     e = _small(4)

@@ -87,22 +87,23 @@ def test_rhs_fp64_small_sbm(cia, oracle_mod, torch_mod, method):
     assert coupling_rel_err(got, ref, w.omega) < FP64_TOL
 
 
+@pytest.mark.parametrize("staging", ["pipeline", "window"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_rhs_harmonics(cia, oracle_mod, torch_mod, p, precision):
+def test_rhs_harmonics(cia, oracle_mod, torch_mod, p, precision, staging):
     rng = np.random.default_rng(p)
     g = S.sbm_graph([40, 70, 33, 64], 0.8, inter_degree=5.0, seed=50 + p, n_free=9)
     d_sin, d_cos = rng.normal(size=p), rng.normal(size=p)
     th = S.as_fp32_values(rng.uniform(-np.pi, np.pi, g.n))
     om = S.as_fp32_values(rng.normal(size=g.n))
-    plan = make_plan(cia, g, om, 2.0, d_sin, d_cos, precision, tile_nodes=32)
+    plan = make_plan(cia, g, om, 2.0, d_sin, d_cos, precision, tile_nodes=32, staging=staging)
     ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 2.0, d_sin, d_cos)
     tol = FP64_TOL if precision == "fp64" else FP32_TOL
     for method in ("cia", "direct"):
         assert coupling_rel_err(gpu_rhs(torch_mod, plan, th, method), ref, om) < tol, method
 
 
-@pytest.mark.parametrize("staging", ["auto", "plain"])
+@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline"])
 @pytest.mark.parametrize("group_size", [4, 8, 16, 32])
 @pytest.mark.parametrize("tile_nodes,tile_index_bytes", [(32, 0), (96, 0), (1024, 0), (256, 256),
                                                          (1024, 4096)])
@@ -116,8 +117,9 @@ def test_rhs_launch_shapes(cia, oracle_mod, torch_mod, group_size, tile_nodes, t
     om = rng.normal(size=g.n)
     plan = make_plan(cia, g, om, 3.0, tile_nodes=tile_nodes, group_size=group_size,
                      tile_index_bytes=tile_index_bytes, staging=staging)
-    # the pipelined TMA kernel takes tiles of at most 256 rows
-    assert plan.info()["staging"] == (0 if staging == "auto" and tile_nodes <= 256 else 1)
+    # the pipelined TMA kernel and the window kernel take tiles of at most 256 rows
+    want = {"auto": 2, "plain": 1, "window": 2, "pipeline": 3}[staging]
+    assert plan.info()["staging"] == (want if tile_nodes <= 256 else 1)
     ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 3.0)
     for method in ("cia", "direct"):
         assert coupling_rel_err(gpu_rhs(torch_mod, plan, th, method), ref, om) < FP64_TOL
@@ -154,7 +156,7 @@ def test_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
             assert coupling_rel_err(got, ref, om) < FP64_TOL
 
 
-@pytest.mark.parametrize("staging", ["auto", "plain"])
+@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline"])
 def test_rhs_fp32_lognormal_reduced(cia, oracle_mod, torch_mod, staging):
     w = S.kuramoto_lognormal(scale=1 / 16)
     g = w.graph
