@@ -319,6 +319,13 @@ cia_status cia_profile_end(cia_plan_t *plan, cia_profile *out);
  * then invalid. */
 cia_status cia_sync(cia_plan_t *plan, void *stream);
 
+/* Failure-detection self-test: launch, on `stream`, a kernel that waits on an
+ * mbarrier nothing arrives on, with a bound of limit_ns nanoseconds (1e3 ..
+ * 1e9).  The wait gives up, sets the plan's error flag and the kernel
+ * returns; the next cia_sync reports CIA_ERR_TIMEOUT and clears the flag.
+ * The CUDA context and the plan stay usable. */
+cia_status cia_selftest_bounded_wait(cia_plan_t *plan, int64_t limit_ns, void *stream);
+
 /* ---- right-hand side without device allocation --------------------------- */
 
 /* The FP64 Kuramoto CIA right-hand side of cia_rhs, for callers that may not

@@ -8,9 +8,13 @@
  * (eq. Cucker_Smale_etaExpansion).  This library replaces the Fourier modes
  * by a learned rank-R feature map,
  *     eta(||s_l - s_m||^2) ~ phi(s_l) . phi(s_m),
- *     phi(x) = W2 silu(W1 x + b1) + b2,     x in R^2, phi(x) in R^R,
- * a two-layer perceptron 2 -> 128 -> 64 evaluated with BF16 weights and
- * activations on the tensor cores (FP32 accumulation).  The same features
+ *     phi(x) = W2 sin(W1 x + b1) + b2,     x in R^2, phi(x) in R^R,
+ * a two-layer perceptron 2 -> 128 -> 64 whose second layer runs on the
+ * tensor cores with BF16 weights and activations (FP32 accumulation); the
+ * first layer (K = 2) runs on the FP32 cores.  With the sine activation the
+ * hidden units are plane waves sin(<w_j, x> + b_j): the paper's Fourier
+ * modes are one setting of the parameters (cia_basis_params_fourier), which
+ * training then improves.  The same features
  * feed the community moments U_c, H_c (eq. Cucker_Smale_orderParams) and the
  * dense evaluation (eq. Cucker_Smale_fast_RHS), so the approximate pair
  * weight is symmetric and the CIA conserves momentum like the exact model.
@@ -18,7 +22,7 @@
  * centroid), which leaves every pair difference unchanged.
  *
  * A basis object holds the FP32 master parameters and the Adam moments on
- * the device.  Every evaluation rounds the parameters to BF16 first.
+ * the device.  Every evaluation rounds W2 to BF16 first.
  * Training minimises the mean squared pair loss
  *     L = (1/B) sum_b (phi(a_b) . phi(c_b) - t_b)^2
  * over pairs (a_b, c_b) of positions with target t_b = eta(||a_b - c_b||^2).
@@ -54,7 +58,9 @@ typedef struct {
 typedef struct {
     int64_t batch;              /* pairs per optimiser step, a multiple of 64 (e.g. 16384) */
     int64_t epochs;             /* passes over the pair array */
-    cia_adam_options adam;
+    cia_adam_options adam;      /* adam.lr is the step size of the first step */
+    double lr_final;            /* step size of the last step, geometric decay in between
+                                   (0 = constant adam.lr) */
 } cia_fit_options;
 
 typedef struct {
@@ -62,6 +68,18 @@ typedef struct {
     double first_loss;          /* loss of the first batch (before its update) */
     double last_epoch_loss;     /* mean batch loss over the last epoch */
 } cia_fit_report;
+
+/* Parameters (host, CIA_BASIS_PARAMS floats) that make phi the rank-64
+ * Fourier basis of the weight eta(y) = K (sigma^2 + y)^-beta on the box
+ * [-L, L]^2 of differences (App. A.6): the coefficients c_alpha of the
+ * periodic extension (rectangle rule on a 256 x 256 grid) of the 32 strongest
+ * mode pairs +-alpha, each as two hidden units sin(pi <alpha, x> / L + pi/2)
+ * and sin(pi <alpha, x> / L) weighted sqrt(2 c_alpha) (alpha = 0: the bias
+ * sqrt(c_0)), so that phi(x) . phi(y) is the truncated series of
+ * eta(||x - y||^2).  The remaining hidden units get seeded small random
+ * frequencies and zero output weights.  Host-only, no device work. */
+cia_status cia_basis_params_fourier(double K, double sigma, double beta, double L, uint64_t seed,
+                                    float *params);
 
 /* Create a basis on the current device from host parameters (packed as
  * above, CIA_BASIS_PARAMS floats); Adam moments start at zero. */

@@ -333,6 +333,7 @@ def angle_diff(a, b) -> np.ndarray:
 
 from .mlp import (mlp_forward, mlp_backward, pair_loss, pair_loss_grad,  # noqa: E402
                   silu, silu_grad, cs_kernel_weight, bf16_round, unpack_params, pack_params)
+from .fourier import fourier_coefficients, fourier_basis, fourier_features, radial  # noqa: E402
 
 __all__ = [
     "build", "num_threads", "set_num_threads", "Split", "split", "rebuild_b",
@@ -340,5 +341,6 @@ __all__ = [
     "cs_direct", "cs_cia", "rk4_step", "euler_step", "wrap_phase", "order_parameter",
     "integrate", "angle_diff", "mlp_forward", "mlp_backward", "pair_loss",
     "pair_loss_grad", "silu", "silu_grad", "cs_kernel_weight", "bf16_round",
-    "unpack_params", "pack_params",
+    "unpack_params", "pack_params", "fourier_coefficients", "fourier_basis", "fourier_features",
+    "radial",
 ]

@@ -9,7 +9,9 @@ phi(s_l) . phi(s_m), which plays the role of the Fourier expansion of step P2
 separates the l and m parts (Sec. 3.3).  The feature map is a two-layer
 perceptron
 
-    phi(x) = W2 silu(W1 x + b1) + b2,     W1: [H, 2], W2: [R, H]
+    phi(x) = W2 sin(W1 x + b1) + b2,     W1: [H, 2], W2: [R, H]
+
+(act="silu" gives the SiLU variant z / (1 + e^-z) instead of sin.)
 
 evaluated on positions x relative to a shift common to the community.  It is
 fitted by least squares on pairs:
@@ -64,7 +66,10 @@ def cs_kernel_weight(d2, K=1.0, sigma=1.0, beta=0.4):
     return K * np.power(sigma * sigma + np.asarray(d2, dtype=np.float64), -beta)
 
 
-def mlp_forward(params: dict, x: np.ndarray, hidden_round=None):
+ACTS = {"sin": (np.sin, np.cos)}
+
+
+def mlp_forward(params: dict, x: np.ndarray, hidden_round=None, act: str = "sin"):
     """phi(x) for x of shape [B, 2]; returns (phi [B, R], cache).
 
     hidden_round, if given, is applied to the hidden activations before the
@@ -72,11 +77,11 @@ def mlp_forward(params: dict, x: np.ndarray, hidden_round=None):
     """
     x = np.asarray(x, dtype=np.float64)
     z1 = x @ params["W1"].T + params["b1"]
-    a1 = silu(z1)
+    a1 = silu(z1) if act == "silu" else ACTS[act][0](z1)
     if hidden_round is not None:
         a1 = hidden_round(a1)
     out = a1 @ params["W2"].T + params["b2"]
-    return out, {"x": x, "z1": z1, "a1": a1}
+    return out, {"x": x, "z1": z1, "a1": a1, "act": act}
 
 
 def mlp_backward(params: dict, cache: dict, dout: np.ndarray) -> dict:
@@ -85,26 +90,26 @@ def mlp_backward(params: dict, cache: dict, dout: np.ndarray) -> dict:
     dW2 = dout.T @ a1
     db2 = dout.sum(axis=0)
     da1 = dout @ params["W2"]
-    dz1 = da1 * silu_grad(z1)
+    dz1 = da1 * (silu_grad(z1) if cache["act"] == "silu" else ACTS[cache["act"]][1](z1))
     dW1 = dz1.T @ x
     db1 = dz1.sum(axis=0)
     return {"W1": dW1, "b1": db1, "W2": dW2, "b2": db2}
 
 
 def pair_loss(params: dict, a: np.ndarray, c: np.ndarray, target: np.ndarray,
-              hidden_round=None) -> float:
+              hidden_round=None, act: str = "sin") -> float:
     """(1/B) sum_b (target_b - phi(a_b) . phi(c_b))^2."""
-    fa, _ = mlp_forward(params, a, hidden_round)
-    fc, _ = mlp_forward(params, c, hidden_round)
+    fa, _ = mlp_forward(params, a, hidden_round, act)
+    fc, _ = mlp_forward(params, c, hidden_round, act)
     e = (fa * fc).sum(axis=1) - target
     return float((e * e).mean())
 
 
 def pair_loss_grad(params: dict, a: np.ndarray, c: np.ndarray, target: np.ndarray,
-                   hidden_round=None):
+                   hidden_round=None, act: str = "sin"):
     """Loss and its gradient (both inputs share the weights: tied features)."""
-    fa, ca = mlp_forward(params, a, hidden_round)
-    fc, cc = mlp_forward(params, c, hidden_round)
+    fa, ca = mlp_forward(params, a, hidden_round, act)
+    fc, cc = mlp_forward(params, c, hidden_round, act)
     B = len(target)
     e = (fa * fc).sum(axis=1) - target
     loss = float((e * e).mean())

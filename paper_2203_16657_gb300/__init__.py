@@ -256,10 +256,11 @@ class Plan:
 
     def learn_fit(self, basis: "Basis", x0, *, dt, steps, snapshots, pairs, seed=0,
                   batch=16384, epochs=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                  stream=None) -> dict:
+                  lr_final=0.0, stream=None) -> dict:
         o = _abi.LearnOptions(float(dt), int(steps), int(snapshots), int(pairs), int(seed),
                               _abi.FitOptions(int(batch), int(epochs),
-                                              _abi.AdamOptions(lr, beta1, beta2, eps)))
+                                              _abi.AdamOptions(lr, beta1, beta2, eps),
+                                              float(lr_final)))
         rep = _abi.LearnReport()
         _abi.check(self._lib.cia_learn_fit(self._h, basis._h, _dev_ptr(x0, "float64", self.size),
                                            ctypes.byref(o), ctypes.byref(rep),
@@ -278,6 +279,10 @@ class Plan:
 
     def sync(self, stream=None):
         _abi.check(self._lib.cia_sync(self._h, _stream_handle(stream)))
+
+    def selftest_bounded_wait(self, limit_ns=1_000_000, stream=None):
+        """Launch a kernel whose bounded wait must give up (failure detection)."""
+        _abi.check(self._lib.cia_selftest_bounded_wait(self._h, int(limit_ns), _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -318,6 +323,14 @@ class Basis:
         _abi.check(lib.cia_basis_create(params.ctypes.data, ctypes.byref(handle)))
         self._h = handle
 
+    @classmethod
+    def params_fourier(cls, K, sigma, beta, L, seed=0) -> np.ndarray:
+        """Parameters that make phi the rank-64 Fourier basis of the weight on [-L, L]^2."""
+        out = np.empty(cls.PARAMS, dtype=np.float32)
+        _abi.check(load().cia_basis_params_fourier(float(K), float(sigma), float(beta), float(L),
+                                                   int(seed), out.ctypes.data))
+        return out
+
     def params(self) -> np.ndarray:
         out = np.empty(self.PARAMS, dtype=np.float32)
         _abi.check(self._lib.cia_basis_get_params(self._h, out.ctypes.data))
@@ -354,9 +367,10 @@ class Basis:
                                                  ctypes.byref(o), _stream_handle(stream)))
 
     def fit(self, pairs, batch=16384, epochs=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-            stream=None) -> dict:
+            lr_final=0.0, stream=None) -> dict:
         B = pairs.shape[0]
-        o = _abi.FitOptions(int(batch), int(epochs), _abi.AdamOptions(lr, beta1, beta2, eps))
+        o = _abi.FitOptions(int(batch), int(epochs), _abi.AdamOptions(lr, beta1, beta2, eps),
+                            float(lr_final))
         rep = _abi.FitReport()
         _abi.check(self._lib.cia_basis_fit(self._h, _dev_ptr(pairs, "float32", 5 * B), B,
                                            ctypes.byref(o), ctypes.byref(rep),

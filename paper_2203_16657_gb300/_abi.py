@@ -84,7 +84,8 @@ class AdamOptions(ctypes.Structure):
 
 
 class FitOptions(ctypes.Structure):
-    _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int64), ("adam", AdamOptions)]
+    _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int64), ("adam", AdamOptions),
+                ("lr_final", ctypes.c_double)]
 
 
 class FitReport(ctypes.Structure):
@@ -129,6 +130,7 @@ SIGNATURES = {
     "cia_integrate_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int64,
                                           _P, _P]),
     "cia_sync": (ctypes.c_int, [_P, _P]),
+    "cia_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
     "cia_state_load": (ctypes.c_int, [_P, _P, _P]),
     "cia_state_store": (ctypes.c_int, [_P, _P, _P]),
     "cia_advance": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _P, _P]),
@@ -138,6 +140,8 @@ SIGNATURES = {
                                                _P, _P, ctypes.POINTER(Coupling), _P, _P]),
     # include/cia_basis.h
     "cia_basis_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "cia_basis_params_fourier": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_uint64, _P]),
     "cia_basis_destroy": (ctypes.c_int, [_P]),
     "cia_basis_get_params": (ctypes.c_int, [_P, _P]),
     "cia_basis_features": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "cia_internal.h"
+#include "sync.cuh"
 
 using namespace cia;
 
@@ -477,5 +478,30 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
         report->best_ms_per_step = best;
         report->worst_ms_per_step = worst;
     }
+    return CIA_OK;
+}
+
+namespace {
+
+// An mbarrier that nothing arrives on: the bounded wait gives up after
+// limit_ns and reports it through the plan's error flag, exactly as a stage
+// kernel whose producer never delivers.
+__global__ void selftest_wait_kernel(int *err_flag, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) cia::mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !cia::mbar_wait_bounded(&bar, 0, limit_ns)) atomicExch(err_flag, 1);
+}
+
+}  // namespace
+
+extern "C" cia_status cia_selftest_bounded_wait(cia_plan_t *pl, int64_t limit_ns, void *stream) {
+    clear_error();
+    cia_status st = check_device(pl);
+    if (st != CIA_OK) return st;
+    if (limit_ns < 1000 || limit_ns > 1000000000)
+        return fail(CIA_ERR_INVALID_ARG, "limit_ns must be in [1e3, 1e9]");
+    selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(pl->d.err_flag, (uint64_t)limit_ns);
+    CIA_CUDA_TRY(cudaGetLastError());
     return CIA_OK;
 }

@@ -12,7 +12,7 @@
 //   dA1   = dPhi W2                 (MMA: 128 x 128 x 64)
 //   dW2^T += A1^T dPhi              (MMA: 128 x 64 x 128, accumulated in tensor
 //                                    memory over all tiles of the CTA)
-//   dZ1   = dA1 * silu'(Z1)         (FP32 cores)
+//   dZ1   = dA1 * cos(Z1)           (FP32 cores; the activation is sin)
 //   dW1, db1, db2: column sums over the tile rows (FP32 cores)
 // Each CTA writes its partial gradient; a second kernel adds the partials in
 // CTA order (deterministic).
@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <string>
 #include <vector>
 
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) basis_pair_grad_kernel(const floa
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int j = j0 + e;
-                a[e] = valid ? mlp::bf16r(mlp::silu(fmaf(w.W1[j].x, x0, fmaf(w.W1[j].y, x1, w.b1[j])))) : 0.f;
+                a[e] = valid ? mlp::bf16r(mlp::act(fmaf(w.W1[j].x, x0, fmaf(w.W1[j].y, x1, w.b1[j])))) : 0.f;
                 st_bf16(A1T, umma::kmajor_offset(j, r, kTileRows), a[e]);
             }
             *reinterpret_cast<uint4 *>(A1 + umma::kmajor_offset(r, j0, kHidden)) =
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) basis_pair_grad_kernel(const floa
         }
         phase ^= 1u;
         umma::fence_after_sync();
-        // (e) dZ1 = dA1 * silu'(Z1) into the scratch, row r, units [64h, 64h + 64)
+        // (e) dZ1 = dA1 * sin'(Z1) into the scratch, row r, units [64h, 64h + 64)
         for (int c = 0; c < 4; ++c) {
             float v[16];
             umma::tmem_ld16(tmem + lane_base + (uint32_t)(64 + 64 * h + 16 * c), v);
@@ -316,8 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) basis_pair_grad_kernel(const floa
             for (int e = 0; e < 16; ++e) {
                 const int j = 64 * h + 16 * c + e;
                 const float z = fmaf(w.W1[j].x, x0, fmaf(w.W1[j].y, x1, w.b1[j]));
-                const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
-                S[r * kHidden + j] = v[e] * sg * fmaf(z, 1.0f - sg, 1.0f);
+                S[r * kHidden + j] = v[e] * mlp::act_grad(z);
             }
         }
         umma::fence_before_sync();
@@ -475,6 +475,89 @@ void free_basis(cia_basis *b) {
 
 using namespace cia;
 
+namespace {
+
+// SplitMix64 (Steele, Lea and Flood 2014): seeded doubles in [0, 1).
+struct SplitMix {
+    uint64_t s;
+    double uniform() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+};
+
+}  // namespace
+
+extern "C" cia_status cia_basis_params_fourier(double K, double sigma, double beta, double L, uint64_t seed,
+                                               float *params) {
+    clear_error();
+    if (!params) return fail(CIA_ERR_INVALID_ARG, "params is NULL");
+    if (!std::isfinite(K) || !std::isfinite(sigma) || !std::isfinite(beta) || !(L > 0.0) || !std::isfinite(L))
+        return fail(CIA_ERR_INVALID_ARG, "need finite K, sigma, beta and L > 0");
+    // coefficients of the periodic extension of g(d) = eta(|d|^2) on
+    // [-L, L)^2, rectangle rule on a G x G grid, for |alpha_i| <= A:
+    //   c_alpha = G^-2 sum_{j,k} g(x_j, y_k) e^{-i pi (alpha_1 x_j + alpha_2 y_k) / L}
+    // evaluated as two one-dimensional sums (first over y, then over x)
+    const int G = 256, A = 12, W = 2 * A + 1;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> x(G), g((size_t)G * G);
+    for (int j = 0; j < G; ++j) x[j] = -L + 2.0 * L * j / G;
+    const double s2 = sigma * sigma;
+    for (int j = 0; j < G; ++j)
+        for (int k = 0; k < G; ++k) g[(size_t)j * G + k] = K * std::pow(s2 + x[j] * x[j] + x[k] * x[k], -beta);
+    std::vector<std::complex<double>> e((size_t)W * G);   // e^{-i pi a x_k / L}
+    for (int a = -A; a <= A; ++a)
+        for (int k = 0; k < G; ++k) e[(size_t)(a + A) * G + k] = std::polar(1.0, -pi * a * x[k] / L);
+    std::vector<std::complex<double>> h((size_t)G * W);   // h[j][a2] = sum_k g[j][k] e^{-i pi a2 y_k / L}
+    for (int j = 0; j < G; ++j)
+        for (int a2 = 0; a2 < W; ++a2) {
+            std::complex<double> acc = 0.0;
+            for (int k = 0; k < G; ++k) acc += g[(size_t)j * G + k] * e[(size_t)a2 * G + k];
+            h[(size_t)j * W + a2] = acc;
+        }
+    struct Mode { int a1, a2; double c; };
+    std::vector<Mode> modes;
+    for (int a1 = 0; a1 <= A; ++a1)
+        for (int a2 = -A; a2 <= A; ++a2) {
+            if (a1 == 0 && a2 < 0) continue;   // one representative per +-alpha
+            std::complex<double> acc = 0.0;
+            for (int j = 0; j < G; ++j) acc += h[(size_t)j * W + (a2 + A)] * e[(size_t)(a1 + A) * G + j];
+            const double c = acc.real() / ((double)G * G);
+            if (c > 0.0) modes.push_back({a1, a2, c});
+        }
+    std::stable_sort(modes.begin(), modes.end(), [](const Mode &p, const Mode &q) { return p.c > q.c; });
+    std::fill(params, params + kParams, 0.0f);
+    SplitMix rng{seed};
+    int hid = 0, feat = 0;
+    for (const Mode &m : modes) {
+        const bool zero = m.a1 == 0 && m.a2 == 0;
+        if (feat + (zero ? 1 : 2) > kRank) continue;
+        if (zero) {
+            params[mlp::kOffB2 + feat++] = (float)std::sqrt(m.c);
+            continue;
+        }
+        const double w1 = pi * m.a1 / L, w2 = pi * m.a2 / L, amp = std::sqrt(2.0 * m.c);
+        for (int ph = 0; ph < 2; ++ph) {   // cos = sin(. + pi/2), then sin
+            params[mlp::kOffW1 + 2 * hid] = (float)w1;
+            params[mlp::kOffW1 + 2 * hid + 1] = (float)w2;
+            params[mlp::kOffB1 + hid] = (float)(ph == 0 ? pi / 2 : 0.0);
+            params[mlp::kOffW2 + feat * kHidden + hid] = (float)amp;
+            ++hid;
+            ++feat;
+        }
+    }
+    for (; hid < kHidden; ++hid) {
+        // spare plane waves: small random frequencies, no output weight yet
+        params[mlp::kOffW1 + 2 * hid] = (float)(0.5 * (2.0 * rng.uniform() - 1.0));
+        params[mlp::kOffW1 + 2 * hid + 1] = (float)(0.5 * (2.0 * rng.uniform() - 1.0));
+        params[mlp::kOffB1 + hid] = (float)(pi * (2.0 * rng.uniform() - 1.0));
+    }
+    return CIA_OK;
+}
+
 extern "C" cia_status cia_basis_create(const float *params, cia_basis_t **out) {
     clear_error();
     if (!params || !out) return fail(CIA_ERR_INVALID_ARG, "params or out is NULL");
@@ -572,9 +655,13 @@ extern "C" cia_status cia_basis_fit(cia_basis_t *basis, const float *pairs, int6
     if (opt->epochs < 0) return fail(CIA_ERR_INVALID_ARG, "epochs < 0");
     st = check_adam(&opt->adam);
     if (st != CIA_OK) return st;
+    if (opt->lr_final < 0.0 || !std::isfinite(opt->lr_final)) return fail(CIA_ERR_INVALID_ARG, "lr_final < 0");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t steps = 0;
     double epoch_loss = 0.0, first = 0.0;
+    const int64_t per_epoch = (count + opt->batch - 1) / opt->batch;
+    const int64_t total_steps = per_epoch * opt->epochs;
+    cia_adam_options ad = opt->adam;
     for (int64_t ep = 0; ep < opt->epochs; ++ep) {
         CIA_CUDA_TRY(cudaMemsetAsync(basis->fit_loss + 1, 0, sizeof(double), s));
         int64_t batches = 0;
@@ -582,7 +669,9 @@ extern "C" cia_status cia_basis_fit(cia_basis_t *basis, const float *pairs, int6
             const int64_t nb = std::min<int64_t>(opt->batch, count - b0);
             st = launch_pair_grad(basis, pairs + b0 * 5, nb, basis->grad, nullptr, basis->fit_loss, steps == 0, s);
             if (st != CIA_OK) return st;
-            st = adam(basis, basis->grad, &opt->adam, s);
+            if (opt->lr_final > 0.0 && total_steps > 1)
+                ad.lr = opt->adam.lr * std::pow(opt->lr_final / opt->adam.lr, (double)steps / (double)(total_steps - 1));
+            st = adam(basis, basis->grad, &ad, s);
             if (st != CIA_OK) return st;
             ++steps;
             ++batches;

@@ -49,6 +49,7 @@ constexpr int kTileMax = 128;          // rows of a tile = MMA M
 constexpr int kMaxChunks = 512;        // missing-list chunks per tile (plan limit)
 constexpr int kPart = 3 * CIA_BASIS_RANK;   // U, H_x, H_y per tile
 constexpr int kRank = CIA_BASIS_RANK;
+constexpr int kFs = kRank + 1;               // padded row stride of the shared feature tile
 
 enum CsMode { kRhs = 0, kStage = 1, kFinal = 2, kLoad = 3 };
 
@@ -63,6 +64,7 @@ struct CsParams {
     double inv_n64;
     float K, sigma2, neg_beta; // eta(y) = K (sigma2 + y)^neg_beta
     const TileDesc *tile_desc;
+    const int32_t *tile_order;
     const unsigned char *blob;
     const int32_t *comm_tile_begin;
     const int64_t *full_rowptr;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
     float2 *sWi = sWm + kMaxChunks;                                    // inter sums per row
     uint16_t *chunk_row = reinterpret_cast<uint16_t *>(sWi + kTileMax);
     __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(region);      // phase C: layer-2 operand
-    float *F = reinterpret_cast<float *>(region);                      // phase C: features [128][64]
+    float *F = reinterpret_cast<float *>(region);                      // phase C: features [128][kFs]
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, r = t & 127, h = t >> 7;
     uint32_t tmem = 0;
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    for (int k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
+        const int tile = a.tile_order ? a.tile_order[k] : k;   // costliest tiles first
         const TileDesc d = a.tile_desc[tile];
         const bool comm = d.comm >= 0;
         if (kFeatures && !comm) continue;   // nodes without a community have no dense term
@@ -320,8 +323,8 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
             for (int e = 0; e < 16; ++e) {
                 __nv_bfloat162 v = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
                 pk[e] = *reinterpret_cast<uint32_t *>(&v);
-                F[r * kRank + 32 * h + 2 * e] = bf16_lo(pk[e]);
-                F[r * kRank + 32 * h + 2 * e + 1] = bf16_hi(pk[e]);
+                F[r * kFs + 32 * h + 2 * e] = bf16_lo(pk[e]);
+                F[r * kFs + 32 * h + 2 * e + 1] = bf16_hi(pk[e]);
             }
             if (valid) {
                 uint4 *dst = reinterpret_cast<uint4 *>(a.feat + (d.first + r) * kRank + 32 * h);
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
                 float su = 0.f, hx = 0.f, hy = 0.f;
                 const int i1 = min(32 * q4 + 32, count);
                 for (int i = 32 * q4; i < i1; ++i) {
-                    const float v = F[i * kRank + fr];
+                    const float v = F[i * kFs + fr];
                     su += v;
                     hx = fmaf(v, yrow[i].z, hx);
                     hy = fmaf(v, yrow[i].w, hy);
@@ -564,6 +567,7 @@ CsParams base_params(const cia_plan *pl, int slot) {
     a.sigma2 = (float)(pl->cs_sigma * pl->cs_sigma);
     a.neg_beta = (float)(-pl->cs_beta);
     a.tile_desc = d.tile_desc;
+    a.tile_order = d.tile_order;
     a.blob = d.blob;
     a.comm_tile_begin = d.comm_tile_begin;
     a.full_rowptr = d.full_rowptr;
@@ -586,7 +590,8 @@ CsParams base_params(const cia_plan *pl, int slot) {
 // feature launch.
 size_t stage_smem(const cia_plan *pl, bool features) {
     const size_t win = align_up((size_t)pl->max_comm * sizeof(float4), 16);
-    if (features) return kWeightsBytes + std::max(win, (size_t)kTileMax * CIA_BASIS_HIDDEN * 2);
+    if (features)
+        return kWeightsBytes + std::max({win, (size_t)kTileMax * CIA_BASIS_HIDDEN * 2, (size_t)kTileMax * kFs * 4});
     return win + kMaxChunks * sizeof(float2) + kTileMax * sizeof(float2) + kMaxChunks * 2;
 }
 

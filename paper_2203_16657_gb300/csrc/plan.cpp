@@ -171,32 +171,34 @@ struct MissScheduler {
 // Fill the missing-link vectors of one slice (32 lanes, nvm vectors of 8
 // entries each).  Lane l sums the entries ent[l][0..len[l]); their order is
 // free, so it is chosen such that at every entry position the live lanes of
-// each half-warp use distinct shared-memory bank pairs (community-local index
-// mod 16) whenever their remaining entries allow -- the gathers of one step
-// are then free of bank conflicts.  Lanes with fewer remaining entries pick
-// first, each taking an unused bank pair from its largest bucket.
+// each group of G lanes use distinct shared-memory bank groups (community-
+// local index mod G) whenever their remaining entries allow -- the gathers of
+// one step are then free of bank conflicts.  G = 16 for 8-byte elements (a
+// warp's 8-byte loads are served per half-warp), G = 8 for 16-byte elements
+// (per quarter-warp).  Lanes with fewer remaining entries pick first, each
+// taking an unused bank group from its largest bucket.
 static void schedule_missing(const int32_t *const ent[32], const int64_t len[32], int64_t nvm,
-                             uint16_t sentinel, uint16_t *out, MissScheduler &sc) {
+                             uint16_t sentinel, uint16_t *out, MissScheduler &sc, int G) {
     int remaining[32];
     for (int lane = 0; lane < 32; ++lane) {
         for (auto &b : sc.bucket[lane]) b.clear();
-        for (int64_t e = 0; e < len[lane]; ++e) sc.bucket[lane][ent[lane][e] & 15].push_back(ent[lane][e]);
+        for (int64_t e = 0; e < len[lane]; ++e) sc.bucket[lane][ent[lane][e] & (G - 1)].push_back(ent[lane][e]);
         remaining[lane] = (int)len[lane];
     }
     for (int64_t pos = 0; pos < 8 * nvm; ++pos) {
         const int64_t j = pos / 8, h = pos % 8;
-        for (int half = 0; half < 2; ++half) {
+        for (int grp = 0; grp < 32 / G; ++grp) {
             int order[16];
-            for (int q = 0; q < 16; ++q) order[q] = 16 * half + q;
-            std::stable_sort(order, order + 16, [&](int x, int y) { return remaining[x] < remaining[y]; });
+            for (int q = 0; q < G; ++q) order[q] = G * grp + q;
+            std::stable_sort(order, order + G, [&](int x, int y) { return remaining[x] < remaining[y]; });
             unsigned used = 0;
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < G; ++q) {
                 const int lane = order[q];
                 uint16_t v = sentinel;
                 if (remaining[lane] > 0) {
                     int best = -1;
                     for (int pass = 0; pass < 2 && best < 0; ++pass)
-                        for (int c = 0; c < 16; ++c) {
+                        for (int c = 0; c < G; ++c) {
                             if (sc.bucket[lane][c].empty() || (pass == 0 && (used >> c & 1u))) continue;
                             if (best < 0 || sc.bucket[lane][c].size() > sc.bucket[lane][best].size()) best = c;
                         }
@@ -221,7 +223,7 @@ struct TileBlob {
 
 static int64_t chunks_of(int64_t entries) { return std::max<int64_t>(1, (entries + kChunk - 1) / kChunk); }
 
-static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inter_sent,
+static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inter_sent, int bank_lanes,
                             const std::vector<int64_t> &miss_cnt, const std::vector<int64_t> &miss_off,
                             const std::vector<int32_t> &miss_local, const std::vector<int64_t> &inter_cnt,
                             const std::vector<int64_t> &inter_off, const std::vector<int32_t> &inter_col,
@@ -289,7 +291,7 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inte
                     ivec[4 * (iv + 32 * j + lane) + h] = has ? inter_col[inter_off[f + ir] + e] : inter_sent;
                 }
         }
-        schedule_missing(ent, len, nvm[s], msent, mvec + 8 * mv, sc);
+        schedule_missing(ent, len, nvm[s], msent, mvec + 8 * mv, sc, bank_lanes);
         mv += 32 * nvm[s];
         iv += 32 * nvi[s];
     }
@@ -651,7 +653,9 @@ static cia_status build_tiles(cia_plan *pl) {
             for (int64_t t = 0; t < T; ++t) {
                 const int32_t c = tile_comm[t];
                 const uint16_t msent = c >= 0 ? (uint16_t)(pl->off[c + 1] - pl->off[c]) : 0;
-                build_tile_blob(tile_first[t], tile_count[t], msent, (int32_t)n, miss_cnt, miss_off, miss_local,
+                // the Cucker--Smale kernels gather 16-byte states, the Kuramoto ones 8-byte phasors
+                const int bank_lanes = pl->model == CIA_MODEL_CUCKER_SMALE ? 8 : 16;
+                build_tile_blob(tile_first[t], tile_count[t], msent, (int32_t)n, bank_lanes, miss_cnt, miss_off, miss_local,
                                 inter_cnt, inter_off, inter_col, tbs[t], sched);
             }
         }

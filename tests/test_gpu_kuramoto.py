@@ -247,3 +247,22 @@ def test_error_paths(cia, torch_mod):
     with pytest.raises(cia.CiaError) as e:
         plan.integrate(x, float("nan"), 3)
     assert e.value.status_name == "CIA_ERR_NUMERIC"
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(cia, oracle_mod, torch_mod):
+    """Failure detection without a fault: a wait that nothing completes gives
+    up after its bound, the next sync reports CIA_ERR_TIMEOUT once, and the
+    plan keeps computing correct results afterwards."""
+    w = S.kuramoto_sbm_small()
+    g = w.graph
+    plan = cia.Plan(g.rowptr, g.col, g.labels, w.omega, K=w.K)
+    plan.selftest_bounded_wait(2_000_000)      # 2 ms
+    with pytest.raises(cia.CiaError) as e:
+        plan.sync()
+    assert e.value.status_name == "CIA_ERR_TIMEOUT"
+    plan.sync()                                # the flag was cleared
+    ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
+    assert coupling_rel_err(gpu_rhs(torch_mod, plan, w.theta0, "cia"), ref, w.omega) < FP64_TOL
+    with pytest.raises(cia.CiaError) as e:
+        plan.selftest_bounded_wait(10)         # out of range
+    assert e.value.status_name == "CIA_ERR_INVALID_ARG"

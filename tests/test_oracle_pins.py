@@ -270,11 +270,13 @@ def _params(rng, H=8, R=4):
 
 
 def test_mlp_forward_hand_evaluated(oracle_mod):
-    """H = R = 1: phi(x) = w2 silu(w1 . x + b1) + b2; silu(0) = 0 and
-    silu(1) = 1/(1 + e^-1)."""
+    """H = R = 1: phi(x) = w2 act(w1 . x + b1) + b2.  sin: w1 . x + b1 = 0 and
+    pi/2 give 0 and 1; SiLU: silu(0) = 0 and silu(1) = 1/(1 + e^-1)."""
     p = {"W1": np.array([[1.0, -2.0]]), "b1": np.array([0.0]),
          "W2": np.array([[3.0]]), "b2": np.array([0.25])}
-    out, _ = oracle_mod.mlp_forward(p, np.array([[2.0, 1.0], [1.0, 0.0]]))
+    out, _ = oracle_mod.mlp_forward(p, np.array([[2.0, 1.0], [np.pi / 2, 0.0]]))
+    np.testing.assert_allclose(out[:, 0], [0.25, 3.25], rtol=0, atol=1e-15)
+    out, _ = oracle_mod.mlp_forward(p, np.array([[2.0, 1.0], [1.0, 0.0]]), act="silu")
     np.testing.assert_allclose(out[:, 0], [0.25, 3.0 / (1.0 + math.exp(-1.0)) + 0.25],
                                rtol=0, atol=1e-15)
 
@@ -284,17 +286,22 @@ def test_mlp_gradient_central_differences(oracle_mod):
     p = _params(rng)
     a, c = rng.normal(size=(16, 2)), rng.normal(size=(16, 2))
     t = oracle_mod.cs_kernel_weight(((a - c) ** 2).sum(axis=1))
-    loss, grads = oracle_mod.pair_loss_grad(p, a, c, t)
-    assert abs(loss - oracle_mod.pair_loss(p, a, c, t)) < 1e-15
+    for act in ("sin", "silu"):
+        _check_pair_gradient(oracle_mod, p, a, c, t, act)
+
+
+def _check_pair_gradient(oracle_mod, p, a, c, t, act):
+    loss, grads = oracle_mod.pair_loss_grad(p, a, c, t, act=act)
+    assert abs(loss - oracle_mod.pair_loss(p, a, c, t, act=act)) < 1e-15
     h = 1e-6
     for k in p:
         flat = p[k].reshape(-1)
         for idx in range(flat.size):
             old = flat[idx]
             flat[idx] = old + h
-            lp = oracle_mod.pair_loss(p, a, c, t)
+            lp = oracle_mod.pair_loss(p, a, c, t, act=act)
             flat[idx] = old - h
-            lm = oracle_mod.pair_loss(p, a, c, t)
+            lm = oracle_mod.pair_loss(p, a, c, t, act=act)
             flat[idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - grads[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), (k, idx)
@@ -323,3 +330,50 @@ def test_param_packing_round_trip(oracle_mod):
     assert p["W1"].shape == (128, 2) and p["W2"].shape == (64, 128)
     assert p["W1"][5, 1] == vec[11] and p["b1"][0] == vec[256] and p["W2"][1, 0] == vec[384 + 128]
     np.testing.assert_array_equal(oracle_mod.pack_params(p), vec)
+
+
+def test_fourier_coefficients_of_a_gaussian(oracle_mod):
+    """A narrow Gaussian on a wide box: the periodic coefficients are samples
+    of its continuous Fourier transform, c_alpha = (2 pi s^2 / (2L)^2)
+    exp(-pi^2 s^2 |alpha|^2 / (2 L^2)) (periodisation error ~ e^{-L^2/2s^2})."""
+    L, sg = 10.0, 1.3
+    g2 = lambda X, Y: np.exp(-(X * X + Y * Y) / (2 * sg * sg))
+    alpha, c = oracle_mod.fourier_coefficients(g2, L, 128)
+    want = (2 * np.pi * sg * sg / (2 * L) ** 2) * np.exp(
+        -np.pi ** 2 * sg * sg * (alpha ** 2).sum(axis=1) / (2 * L * L))
+    assert np.abs(c - want).max() < 1e-12
+
+
+def test_fourier_features_reproduce_trigonometric_weights(oracle_mod):
+    """g(d) = 1 + cos(pi d_x / L) + 0.5 cos(2 pi d_y / L) has exactly three
+    mode pairs: the rank-5 basis reproduces it for any two positions."""
+    L = 7.0
+    g2 = lambda X, Y: 1.0 + np.cos(np.pi * X / L) + 0.5 * np.cos(2 * np.pi * Y / L)
+    alpha, c = oracle_mod.fourier_basis(g2, L, rank=5, grid=64)
+    got = {tuple(a): v for a, v in zip(alpha.tolist(), c)}
+    assert set(got) == {(0, 0), (1, 0), (0, 2)}
+    assert abs(got[(0, 0)] - 1.0) < 1e-12 and abs(got[(1, 0)] - 0.5) < 1e-12
+    assert abs(got[(0, 2)] - 0.25) < 1e-12
+    rng = np.random.default_rng(8)
+    s1, s2 = rng.uniform(-3, 3, (50, 2)), rng.uniform(-3, 3, (50, 2))
+    f1 = oracle_mod.fourier_features(s1, alpha, c, L)
+    f2 = oracle_mod.fourier_features(s2, alpha, c, L)
+    d = s1 - s2
+    np.testing.assert_allclose((f1 * f2).sum(axis=1), g2(d[:, 0], d[:, 1]), rtol=0, atol=1e-12)
+
+
+def test_fourier_basis_of_the_cs_weight_converges(oracle_mod):
+    """More modes, smaller error of the separable approximation of
+    (1 + r^2)^-0.4 over differences of positions in a 10 x 10 box."""
+    eta = lambda d2: oracle_mod.cs_kernel_weight(d2, 1.0, 1.0, 0.4)
+    rng = np.random.default_rng(9)
+    s1, s2 = rng.uniform(0, 10, (2000, 2)), rng.uniform(0, 10, (2000, 2))
+    ref = eta(((s1 - s2) ** 2).sum(axis=1))
+    errs = []
+    for rank in (9, 25, 64, 121):
+        alpha, c = oracle_mod.fourier_basis(oracle_mod.radial(eta), 10.0, rank)
+        f1 = oracle_mod.fourier_features(s1, alpha, c, 10.0)
+        f2 = oracle_mod.fourier_features(s2, alpha, c, 10.0)
+        assert f1.shape[1] <= rank
+        errs.append(np.sqrt((((f1 * f2).sum(axis=1) - ref) ** 2).mean()))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
