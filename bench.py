@@ -153,6 +153,17 @@ def direct_stage_bytes(info: dict, precision: str) -> float:
     return info["n"] * per_node + info["nnz_graph"] * 4
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one stage-1..3 launch of cia_window_kernel on
+# the full workload, from an ncu --set full capture on one GB300.  Valid for that kernel at
+# scale 1 only; it has to be measured again whenever the kernel changes.
+WINDOW_KERNEL_TRAFFIC = 61.19e6 + 0.62e6
+
+
+def stage_kernel_name(info: dict) -> str:
+    return {1: "cia_stage_kernel (plain loads)", 2: "cia_window_kernel (TMA community window)",
+            3: "cia_pipeline_kernel (persistent TMA pipeline)"}.get(info["staging"], "?") + ", one RK4 stage"
+
+
 def peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -522,8 +533,9 @@ def main():
             "value": g.n * args.steps / e2e_s, "unit": UNIT,
             "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "stage_kernel (CIA RK4 stage)", "bytes_per_launch": sb,
+                     "frac": achieved / pk["hbm_gbs"],
+                     "traffic": WINDOW_KERNEL_TRAFFIC if (info["staging"] == 2 and args.scale == 1.0) else None,
+                     "kernel": stage_kernel_name(info), "bytes_per_launch": sb,
                      "avg_launch_ms": stage_avg_ms, "peak_source": pk["source"]},
         "gpu_launches": int(prof["stage_launches"] + prof["other_launches"]),
         "clocks": clk.summary(),
