@@ -611,7 +611,10 @@ cudaError_t launch_stage_t(const cia_plan *pl, const CsParams &a, cudaStream_t s
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cs_stage_kernel<MODE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     bps = std::max(1, std::min(bps, 8));   // at most 8 x 64 tensor-memory columns per SM
-    const int64_t grid = std::min<int64_t>(pl->n_tiles, (int64_t)bps * pl->n_sms);
+    // the feature launch keeps one resident CTA per slot (it loads the weights
+    // and allocates tensor memory once); the stage launches take one CTA per
+    // tile and let the hardware start the next tile wherever a slot frees up
+    const int64_t grid = MODE == kLoad ? std::min<int64_t>(pl->n_tiles, (int64_t)bps * pl->n_sms) : pl->n_tiles;
     void *args[] = {const_cast<CsParams *>(&a)};
     return cudaLaunchKernel((const void *)cs_stage_kernel<MODE>, dim3((unsigned)std::max<int64_t>(grid, 1)),
                             dim3(kThreads), args, smem, s);

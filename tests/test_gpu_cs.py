@@ -362,3 +362,47 @@ def test_learned_basis_beats_fourier_at_equal_rank(P, oracle_mod):
     got = plan.rhs(xd).cpu().numpy().reshape(-1, 4)
     e_learned = _rel_v(got, ref)
     assert e_learned < e_fourier, (e_learned, e_fourier)
+
+
+@pytest.mark.parametrize("case", ["free_nodes", "singletons", "no_edges", "all_free"])
+def test_cia_degenerate_graphs(P, oracle_mod, case):
+    """Unlabelled agents (all their links sparse), one-agent communities,
+    an empty graph and a graph without communities: with a constant feature
+    map (exact for a constant weight) the CIA equals the direct sum."""
+    import torch
+    import synthetic as S
+    if case == "free_nodes":
+        g = S.random_labels_graph(90, 0.2, 4, seed=41, free_frac=0.3)
+    elif case == "singletons":
+        g = S.random_labels_graph(40, 0.3, 1, seed=42, free_frac=0.0)
+        g.labels = np.arange(g.n, dtype=np.int32)
+    elif case == "no_edges":
+        g = S.random_labels_graph(30, 0.0, 3, seed=43, free_frac=0.1)
+    else:
+        g = S.random_labels_graph(50, 0.3, 1, seed=44, free_frac=1.0)
+    rng = np.random.default_rng(45)
+    x = S.as_fp32_values(np.concatenate([rng.uniform(0, 10, (g.n, 2)), rng.normal(size=(g.n, 2))], axis=1))
+    vec = oracle_mod.pack_params(_params(46, const=True)).astype(np.float32)
+    b2 = oracle_mod.bf16_round(vec[-R:])
+    K = float((b2 * b2).sum())
+    plan = P.Plan(g.rowptr, g.col, g.labels, None, K=K, sigma=1.0, beta=0.0, precision="fp32",
+                  model="cucker_smale", build_direct=True, tile_nodes=32)
+    plan.set_basis(P.Basis(vec))
+    xd = torch.from_numpy(x.ravel().copy()).cuda()
+    ref = oracle_mod.cs_direct(g.rowptr, g.col, x, K, 1.0, 0.0)
+    # FP32 rounding is relative to the terms summed: a whole community's block
+    # (K lambda max|v| / N) even where the exact result is zero (no links)
+    lam = np.bincount(g.labels[g.labels >= 0]).max() if (g.labels >= 0).any() else 1
+    terms = K * lam * np.abs(x[:, 2:]).max() / g.n
+    for method in ("cia", "direct"):
+        out = plan.rhs(xd, method=method).cpu().numpy().reshape(-1, 4)
+        np.testing.assert_array_equal(out[:, :2], x[:, 2:])
+        tol = 1e-5 * max(np.abs(ref[:, 2:]).max(), terms)
+        assert np.abs(out[:, 2:] - ref[:, 2:]).max() <= tol, method
+    # a few steps through the stage kernels (features launch included)
+    xs = xd.clone()
+    plan.integrate(xs, 0.01, 3)
+    plan.sync()
+    rhs = lambda y: oracle_mod.cs_direct(g.rowptr, g.col, y, K, 1.0, 0.0)
+    want, _ = oracle_mod.integrate(rhs, x, 0.01, 3, wrap=False)
+    assert np.abs(xs.cpu().numpy().reshape(-1, 4) - want).max() <= 1e-5 * np.abs(want).max()
