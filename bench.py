@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble secondary workload")
     ap.add_argument("--ens-instances", type=int, default=32,
                     help="instances of the seeded 4096-network ensemble to run")
-    ap.add_argument("--only", choices=["cs", "ensemble"], default=None,
+    ap.add_argument("--no-small-configs", action="store_true",
+                    help="skip the small FP64 and the higher-order Kuramoto workloads")
+    ap.add_argument("--only", choices=["cs", "ensemble", "small"], default=None,
                     help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
 
@@ -389,6 +391,79 @@ def ensemble_leg(args, torch, cia, flush) -> dict:
     }
 
 
+# ------------------------------------------------------------------ small FP64 and higher-order workloads
+
+def _time_method(torch, plan, x0, dt, steps, warmup, method, flush) -> float:
+    ms, _ = timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, False)
+    return float(sum(ms))
+
+
+def small_configs_leg(args, torch, cia, flush) -> dict:
+    """CIA vs direct at equal accuracy on the two remaining Kuramoto workloads:
+    the 1000-node FP64 network (launch-latency bound, no roofline claim) and the
+    higher-order network (pairwise + triadic term on community hyperedges),
+    each with its RHS error against the FP64 oracle."""
+    import oracle
+    import synthetic as S
+    oracle.set_num_threads(host_cores())
+    out = {}
+    # FP64, N = 1000: errors on every node; steps replayed as CUDA graphs
+    w = S.kuramoto_sbm_small()
+    g = w.graph
+    plan = cia.Plan(g.rowptr, g.col, g.labels, w.omega, K=w.K, precision="fp64", build_direct=True)
+    x0 = torch.from_numpy(w.theta0.copy()).cuda()
+    ref = oracle.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
+    err = {m: coupling_rel_err(plan.rhs(x0, method=m).cpu().numpy(), ref, w.omega) for m in ("cia", "direct")}
+    steps = w.steps
+    res = {}
+    for m in ("cia", "direct"):
+        plan.state_load(x0)
+        plan.advance(w.dt, args.warmup, method=m)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.advance(w.dt, steps, method=m)
+        b.record()
+        torch.cuda.synchronize()
+        res[m] = a.elapsed_time(b)
+    out["kuramoto_sbm_small"] = {
+        "workload": "N=1000, 5x200 SBM p_in 0.9 p_out 0.01, K=4, RK4 dt 0.01, FP64 (100 steps, "
+                    "one CUDA graph per step, L2 warm: the whole problem is 2 MB)",
+        "cia": {"value": g.n * steps / (res["cia"] / 1e3), "unit": UNIT, "ms_per_step": res["cia"] / steps},
+        "direct": {"value": g.n * steps / (res["direct"] / 1e3), "unit": UNIT,
+                   "ms_per_step": res["direct"] / steps},
+        "error_vs_fp64_oracle": {"cia_rhs_coupling_rel": err["cia"], "direct_rhs_coupling_rel": err["direct"]}}
+    # higher-order, N = 65536, FP32; triadic oracle on 512 sampled nodes
+    w = S.kuramoto_ho()
+    g = w.graph
+    plan = cia.Plan(g.rowptr, g.col, g.labels, w.omega, K=w.K, model="kuramoto_ho", K2=w.K2,
+                    precision="fp32", build_direct=True)
+    x0 = torch.from_numpy(w.theta0.copy()).cuda()
+    sp = oracle.split(g.rowptr, g.col, g.labels)
+    nodes = np.linspace(0, g.n - 1, 512).astype(np.int64)
+    pair = oracle.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
+    tri = oracle.ho_triadic_direct(sp, w.theta0[sp.perm], w.K2, sp.iperm[nodes])
+    ref = pair[nodes] + tri
+    err = {}
+    for m in ("cia", "direct"):
+        got = plan.rhs(x0, method=m).cpu().numpy()[nodes]
+        err[m] = coupling_rel_err(got, ref, w.omega[nodes])
+    steps = 3
+    t_cia = _time_method(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush)
+    t_dir = _time_method(torch, plan, x0, w.dt, steps, 1, "direct", flush)
+    out["kuramoto_ho"] = {
+        "workload": "N=65536, 64x1024 SBM p_in 0.9, inter degree 4, pairwise K1=1 + triadic K2=2 on "
+                    "community hyperedges, RK4 dt 0.005, FP32 + FP64 accumulation (L2 flushed between steps)",
+        "steps": steps,
+        "cia": {"value": g.n * steps / (t_cia / 1e3), "unit": UNIT, "ms_per_step": t_cia / steps},
+        "direct": {"value": g.n * steps / (t_dir / 1e3), "unit": UNIT, "ms_per_step": t_dir / steps,
+                   "note": "triadic term summed pair by pair, O(lambda^2) per node"},
+        "speedup_cia_over_direct": t_dir / max(t_cia, 1e-12),
+        "error_vs_fp64_oracle_512_sampled_nodes": {"cia_rhs_coupling_rel": err["cia"],
+                                                   "direct_rhs_coupling_rel": err["direct"]}}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, profile: bool):
@@ -434,7 +509,7 @@ def main():
     import paper_2203_16657_gb300 as cia
     if args.only:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-        leg = cs_leg if args.only == "cs" else ensemble_leg
+        leg = {"cs": cs_leg, "ensemble": ensemble_leg, "small": small_configs_leg}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, torch, cia, flush)}), flush=True)
         return 0
     w = S.kuramoto_lognormal(scale=args.scale)
@@ -498,6 +573,9 @@ def main():
     ens = None
     if not args.no_ensemble and world == 1:
         ens = ensemble_leg(args, torch, cia, flush)
+    small = None
+    if not args.no_small_configs and world == 1:
+        small = small_configs_leg(args, torch, cia, flush)
 
     pk = peaks()
     stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
@@ -546,6 +624,8 @@ def main():
         line["cucker_smale"] = cs
     if ens is not None:
         line["ensemble"] = ens
+    if small is not None:
+        line.update(small)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
