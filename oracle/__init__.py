@@ -15,6 +15,10 @@ Contents, each following the paper (arXiv 2203.16657):
 * ``ho_triadic_direct`` / ``ho_triadic_cia``: the triadic term of the
   higher-order Kuramoto model (App. A.7) on complete community hyperedges.
 * ``cs_direct`` / ``cs_cia``: Cucker--Smale (App. A.6) with a separable basis.
+* ``poly_direct`` / ``poly_cia``: polynomial difference coupling with a
+  potential (App. A.3 and the Desai--Zwanzig model, App. A.5), the CIA by
+  polynomial moments.
+* ``fourier_*``: the Fourier basis of a radial pair weight (App. A.6).
 * ``rk4_step`` / ``euler_step``: classical RK4 (textbook; the paper allows any
   Runge--Kutta method, Sec. 3) and explicit Euler (Sec. 4).
 * ``order_parameter``: r = |sum_l e^{i theta_l}| / N (eq. KuramotoFirstOP).
@@ -64,6 +68,9 @@ def _load():
         lib.ora_ho_triadic_cia.argtypes = [I64, I64, P, P, D, P, P, P, P, P]
         lib.ora_cs_direct.argtypes = [I64, P, P, P, D, D, D, P]
         lib.ora_cs_cia.argtypes = [I64, I64, P, P, P, P, P, P, I64, D, D, D, P, P, P]
+        lib.ora_poly_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P]
+        lib.ora_poly_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
+                                     P, P]
         _lib = lib
     return _lib
 
@@ -281,6 +288,30 @@ def cs_cia(sp: Split, x_perm, feat_perm, K=1.0, sigma=1.0, beta=0.4) -> np.ndarr
     return out
 
 
+def poly_direct(rowptr, col, x, K, c, dv) -> np.ndarray:
+    """x' = -V'(x_m) + (K/N) sum_l a_ml h(x_l - x_m) with h = sum_a c[a] x^a and
+    V' = sum_j dv[j] x^j (polynomial difference coupling, Desai--Zwanzig)."""
+    lib = _load()
+    x = _f64(x)
+    c, dv = _f64(c), _f64(dv)
+    out = np.empty_like(x)
+    lib.ora_poly_direct(len(x), _p(_i64(rowptr)), _p(_i32(col)), _p(x), float(K), len(c) - 1, _p(c),
+                        len(dv) - 1, _p(dv), _p(out))
+    return out
+
+
+def poly_cia(sp: Split, x_perm, K, c, dv) -> np.ndarray:
+    """The same right-hand side by the CIA with polynomial moments (permuted order)."""
+    lib = _load()
+    x = _f64(x_perm)
+    c, dv = _f64(c), _f64(dv)
+    w = np.zeros(max(1, sp.M * len(c)))
+    out = np.empty_like(x)
+    lib.ora_poly_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
+                     float(K), len(c) - 1, _p(c), len(dv) - 1, _p(dv), _p(w), _p(out))
+    return out
+
+
 # --------------------------------------------------------------------------
 # Time stepping and observables
 # --------------------------------------------------------------------------
@@ -338,7 +369,7 @@ from .fourier import fourier_coefficients, fourier_basis, fourier_features, radi
 __all__ = [
     "build", "num_threads", "set_num_threads", "Split", "split", "rebuild_b",
     "kuramoto_direct", "kuramoto_cia", "ho_triadic_direct", "ho_triadic_cia",
-    "cs_direct", "cs_cia", "rk4_step", "euler_step", "wrap_phase", "order_parameter",
+    "cs_direct", "cs_cia", "poly_direct", "poly_cia", "rk4_step", "euler_step", "wrap_phase", "order_parameter",
     "integrate", "angle_diff", "mlp_forward", "mlp_backward", "pair_loss",
     "pair_loss_grad", "silu", "silu_grad", "cs_kernel_weight", "bf16_round",
     "unpack_params", "pack_params", "fourier_coefficients", "fourier_basis", "fourier_features",

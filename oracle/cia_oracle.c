@@ -300,3 +300,77 @@ void ora_cs_cia(int64_t n, int64_t M, const int64_t *off,
         out[4 * m + 3] = dy + invN * sy;
     }
 }
+
+/* ---- polynomial difference coupling with a potential --------------------
+ * x_m' = -V'(x_m) + (K/N) sum_l a_ml h(x_l - x_m)
+ * (eq. GeneralNetworkPolyDifference, App. A.3, with the potential term of the
+ * Desai-Zwanzig model, eq. DesaiZwanzig, App. A.5), where
+ *   h(x)  = sum_{a=0..p} c[a] x^a,   V'(x) = sum_{j=0..q} dv[j] x^j.
+ * Desai-Zwanzig: p = 1, c = (0, 1). */
+static double poly_eval(const double *c, int p, double x) {
+    double s = 0.0;
+    for (int a = p; a >= 0; --a) s = s * x + c[a];
+    return s;
+}
+
+/* Direct RHS: the CSR neighbours of m one by one. */
+void ora_poly_direct(int64_t n, const int64_t *rowptr, const int32_t *col, const double *x, double K,
+                     int p, const double *c, int q, const double *dv, double *out) {
+    const double scale = K / (double)n;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int64_t e = rowptr[m]; e < rowptr[m + 1]; ++e) acc += poly_eval(c, p, x[col[e]] - x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + scale * acc;
+    }
+}
+
+/* CIA RHS in the paper's steps (permuted state, communities [off[c], off[c+1]),
+ * S with values +1 / -1 including the diagonal -1 of every community node):
+ * (E1.1) w[c][k] = (1/N) sum_{l in c} x_l^k, k = 0..p            (eq. PolyMoments)
+ * (E1.2) dense_m = sum_a c_a sum_{k=0..a} binom(a, k) w[c][k] (-x_m)^{a-k}
+ *                                                               (eq. PolyDifferenceRHSfast)
+ * (E2)   sparse_m = (1/N) sum_l s_ml h(x_l - x_m)
+ *        out_m = -V'(x_m) + K (dense_m + sparse_m).
+ * w: caller scratch of M * (p + 1) doubles. */
+void ora_poly_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_rowptr, const int32_t *s_col,
+                  const int8_t *s_val, const double *x, double K, int p, const double *c, int q,
+                  const double *dv, double *w, double *out) {
+    const double invN = 1.0 / (double)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t cc = 0; cc < M; ++cc) {
+        for (int k = 0; k <= p; ++k) {
+            double s = 0.0;
+            for (int64_t l = off[cc]; l < off[cc + 1]; ++l) s += pow(x[l], (double)k);
+            w[cc * (p + 1) + k] = invN * s;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        int64_t cc = -1;
+        if (m < off[M]) {
+            int64_t lo = 0, hi = M;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) / 2;
+                if (off[mid] <= m) lo = mid;
+                else hi = mid;
+            }
+            cc = lo;
+        }
+        double dense = 0.0;
+        if (cc >= 0) {
+            for (int a = 0; a <= p; ++a) {
+                double inner = 0.0, binom = 1.0;
+                for (int k = 0; k <= a; ++k) {
+                    inner += binom * w[cc * (p + 1) + k] * pow(-x[m], (double)(a - k));
+                    binom = binom * (double)(a - k) / (double)(k + 1);
+                }
+                dense += c[a] * inner;
+            }
+        }
+        double sparse = 0.0;
+        for (int64_t e = s_rowptr[m]; e < s_rowptr[m + 1]; ++e)
+            sparse += (double)s_val[e] * poly_eval(c, p, x[s_col[e]] - x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
+    }
+}

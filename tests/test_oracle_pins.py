@@ -377,3 +377,43 @@ def test_fourier_basis_of_the_cs_weight_converges(oracle_mod):
         assert f1.shape[1] <= rank
         errs.append(np.sqrt((((f1 * f2).sum(axis=1) - ref) ** 2).mean()))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
+
+
+def test_desai_zwanzig_hand_values(oracle_mod):
+    """One uncoupled particle in the double well V = x^4/4 - x^2/2:
+    x' = x - x^3 (0 at the minima +-1 and the maximum 0, 3/8 at x = 1/2)."""
+    rowptr, col = np.zeros(2, np.int64), np.zeros(0, np.int32)
+    for x, want in [(1.0, 0.0), (-1.0, 0.0), (0.0, 0.0), (0.5, 0.375)]:
+        out = oracle_mod.poly_direct(rowptr, col, np.array([x]), 2.0, [0.0, 1.0], [0.0, -1.0, 0.0, 1.0])
+        assert out[0] == want
+
+
+def test_linear_consensus_decays_by_the_rk4_polynomial(oracle_mod):
+    """V' = 0, h(x) = x on a complete graph: x' = K (xbar - x_m) exactly, so the
+    mean is kept and every deviation is multiplied by R(-K dt) per RK4 step."""
+    n, K, dt, steps = 12, 1.7, 0.05, 30
+    rowptr, col = complete_csr(n)
+    x0 = np.random.default_rng(11).normal(size=n)
+    rhs = lambda y: oracle_mod.poly_direct(rowptr, col, y, K, [0.0, 1.0], [0.0])
+    got, _ = oracle_mod.integrate(rhs, x0, dt, steps, wrap=False)
+    z = -K * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    want = x0.mean() + (x0 - x0.mean()) * R ** steps
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_polynomial_cia_equals_direct(oracle_mod, seed):
+    """The moment formula (binomial expansion of h) plus the exact sparse
+    corrections reaches the direct sum on random graphs with unlabelled nodes,
+    for a cubic coupling and a quartic potential."""
+    import synthetic as S
+    g = S.random_labels_graph(45, 0.3, 3, seed=60 + seed, free_frac=0.2)
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=g.n)
+    c = rng.normal(size=4)
+    dv = rng.normal(size=5)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 1.3, c, dv)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    got = oracle_mod.poly_cia(sp, x[sp.perm], 1.3, c, dv)[sp.iperm]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
