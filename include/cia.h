@@ -54,7 +54,8 @@ typedef enum {
 typedef enum {
     CIA_MODEL_KURAMOTO = 0,     /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
     CIA_MODEL_KURAMOTO_HO = 1,  /* the same plus a triadic term on complete community hyperedges (App. A.7) */
-    CIA_MODEL_CUCKER_SMALE = 2  /* 2-D flocking agents (App. A.6), state (s_x, s_y, v_x, v_y) per node */
+    CIA_MODEL_CUCKER_SMALE = 2, /* 2-D flocking agents (App. A.6), state (s_x, s_y, v_x, v_y) per node */
+    CIA_MODEL_POLYNOMIAL = 3    /* polynomial difference coupling with a potential (App. A.3, A.5) */
 } cia_model;
 
 typedef enum {
@@ -68,6 +69,7 @@ typedef enum {
 } cia_method;
 
 #define CIA_MAX_HARMONICS 4
+#define CIA_MAX_POLY 4
 
 /* Undirected, unweighted graph without self loops as a symmetric CSR (host).
  * Columns of each row must be strictly increasing.  A is 0/1 (Sec. 2). */
@@ -96,7 +98,16 @@ typedef struct {
  * Its CIA needs a separable basis of eta (step P2): a learned feature map set
  * with cia_plan_set_basis (include/cia_basis.h).  The links of S (missing and
  * inter-community) are summed with the exact eta.  FP32 only; p, d_sin,
- * d_cos and K2 are ignored. */
+ * d_cos and K2 are ignored.
+ * CIA_MODEL_POLYNOMIAL (eq. GeneralNetworkPolyDifference, App. A.3, with the
+ * potential of the Desai-Zwanzig model, eq. DesaiZwanzig, App. A.5):
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml h(x_l - x_m),
+ *   h(x) = sum_{a=0..p} poly_c[a] x^a,   V'(x) = sum_{j=0..4} dV[j] x^j,
+ * p in [0, CIA_MAX_POLY].  The CIA uses the community moments
+ * W_ck = sum_{l in c} x_l^k, k <= p (eq. PolyMoments) and the binomial
+ * expansion of h (eq. PolyDifferenceRHSfast); the links of S are summed with
+ * h itself.  Desai-Zwanzig: p = 1, poly_c = (0, 1).  FP64 only; omega must be
+ * NULL. */
 typedef struct {
     int model;                  /* cia_model */
     int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
@@ -105,6 +116,8 @@ typedef struct {
     double K;                   /* coupling constant multiplying (1/N) sum */
     double K2;                  /* triadic coupling (CIA_MODEL_KURAMOTO_HO), multiplies (1/N^2) sum */
     double sigma, beta;         /* Cucker--Smale weight eta(y) = K (sigma^2 + y)^-beta, sigma > 0 */
+    double poly_c[CIA_MAX_POLY + 1];   /* polynomial model: coefficients of h, degree p */
+    double dV[CIA_MAX_POLY + 1];       /* polynomial model: coefficients of V' */
 } cia_coupling;
 
 typedef struct {

@@ -46,16 +46,19 @@ class Plan:
     model="kuramoto_ho" adds the triadic term on community hyperedges, scaled by K2/N^2.
     model="cucker_smale": state [n, 4] = (s_x, s_y, v_x, v_y) per node, weight
     eta(y) = K (sigma^2 + y)^-beta; the CIA needs a basis (set_basis / learn_fit).
+    model="polynomial": x' = -V'(x) + (K/N) sum_l a_ml h(x_l - x_m) with
+    h(x) = sum_a poly_c[a] x^a (degree <= 4) and V'(x) = sum_j dV[j] x^j, FP64,
+    omega None (Desai-Zwanzig: dV = (0, -1, 0, 1), poly_c = (0, 1)).
     """
 
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
                  tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0, sigma=1.0,
-                 beta=0.0, use_graphs=True, _batch=None):
+                 beta=0.0, poly_c=(0.0, 1.0), dV=(0.0,), use_graphs=True, _batch=None):
         lib = load()
         self._lib = lib
         self._keep = []
-        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta)
+        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c, dV)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
                            int(group_size), int(tile_index_bytes), _abi.STAGING[staging],
                            0 if use_graphs else 1)
@@ -119,11 +122,11 @@ class Plan:
         return cls(None, None, None, _batch=(list(graphs), list(labels), list(omegas)), **kw)
 
     @staticmethod
-    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta):
+    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,)):
         d_sin = list(d_sin)
         d_cos = list(d_cos)
         p = len(d_sin)
-        if len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS:
+        if model != "polynomial" and (len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS):
             raise ValueError("d_sin and d_cos must have the same length in [1, %d]"
                              % _abi.CIA_MAX_HARMONICS)
         cp = _abi.Coupling()
@@ -136,6 +139,16 @@ class Plan:
         cp.K2 = float(K2)
         cp.sigma = float(sigma)
         cp.beta = float(beta)
+        if model == "polynomial":
+            poly_c, dV = list(poly_c), list(dV)
+            if not 1 <= len(poly_c) <= _abi.CIA_MAX_POLY + 1 or len(dV) > _abi.CIA_MAX_POLY + 1:
+                raise ValueError("poly_c needs 1..%d and dV at most %d coefficients"
+                                 % (_abi.CIA_MAX_POLY + 1, _abi.CIA_MAX_POLY + 1))
+            cp.p = len(poly_c) - 1
+            for a, v in enumerate(poly_c):
+                cp.poly_c[a] = float(v)
+            for j, v in enumerate(dV):
+                cp.dV[j] = float(v)
         return cp
 
     # ------------------------------------------------------------ bookkeeping

@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libcia.so")
 
 CIA_MAX_HARMONICS = 4
+CIA_MAX_POLY = 4
 
 STATUS = {
     0: "CIA_OK", 1: "CIA_ERR_INVALID_ARG", 2: "CIA_ERR_INVALID_GRAPH", 3: "CIA_ERR_UNSUPPORTED",
@@ -21,7 +22,7 @@ STATUS = {
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
 STAGING = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}
-MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2}
+MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2, "polynomial": 3}
 
 
 class CiaError(RuntimeError):
@@ -40,7 +41,9 @@ class Coupling(ctypes.Structure):
                 ("d_sin", ctypes.c_double * CIA_MAX_HARMONICS),
                 ("d_cos", ctypes.c_double * CIA_MAX_HARMONICS),
                 ("K", ctypes.c_double), ("K2", ctypes.c_double),
-                ("sigma", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
+                ("poly_c", ctypes.c_double * (CIA_MAX_POLY + 1)),
+                ("dV", ctypes.c_double * (CIA_MAX_POLY + 1))]
 
 
 class Options(ctypes.Structure):

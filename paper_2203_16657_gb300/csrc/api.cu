@@ -57,6 +57,13 @@ cia_status check_plan(cia_plan *pl, int method) {
         return fail(CIA_ERR_UNSUPPORTED, "communities above 65536 nodes are not supported");
     int optin = 0;
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+    if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        // the stage kernel's static shared memory is under 4 KB
+        if (method == CIA_METHOD_CIA && poly_stage_smem_bytes(pl) > (size_t)optin - 4096)
+            return fail(CIA_ERR_UNSUPPORTED, "largest community (" + std::to_string(pl->max_comm) +
+                                                 " nodes) does not fit the shared-memory community window");
+        return CIA_OK;
+    }
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
         if (method == CIA_METHOD_CIA && !pl->cs_has_basis)
             return fail(CIA_ERR_INVALID_ARG, "the Cucker-Smale CIA needs a basis (cia_plan_set_basis)");
@@ -87,6 +94,11 @@ cia_status rhs_common(cia_plan *pl, int method, const double *x, double *dxdt, v
     cudaStream_t s = (cudaStream_t)stream;
     // the slot not holding the resident state is free between calls
     const int slot = pl->state_slot ^ 1;
+    if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        CIA_CUDA_TRY(poly_launch_load(pl, x, false, slot, s));
+        CIA_CUDA_TRY(poly_launch_rhs(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA, slot, dxdt, s));
+        return CIA_OK;
+    }
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
         CIA_CUDA_TRY(cs_launch_load(pl, x, false, slot, s));
         if (method == CIA_METHOD_CIA) {
@@ -129,6 +141,7 @@ cia_status stage_launch(cia_plan *pl, int m, int stage, int slot, double dt, cud
     const bool rec = pl->prof_on && pl->prof_used < pl->prof_cap;
     if (rec) CIA_CUDA_TRY(cudaEventRecord(pl->prof_ev[2 * pl->prof_used], s));
     if (pl->model == CIA_MODEL_CUCKER_SMALE) CIA_CUDA_TRY(cs_launch_stage(pl, m, stage, slot, dt, s));
+    else if (pl->model == CIA_MODEL_POLYNOMIAL) CIA_CUDA_TRY(poly_launch_stage(pl, m, stage, slot, dt, s));
     else CIA_CUDA_TRY(launch_rk4_stage(pl, m, stage, slot, dt, s));
     if (rec) {
         CIA_CUDA_TRY(cudaEventRecord(pl->prof_ev[2 * pl->prof_used + 1], s));
@@ -209,7 +222,8 @@ cia_status ensure_step_graph(cia_plan *pl, int m, int slot, double dt, double *r
     cudaError_t err = cudaSuccess;
     int sl = slot;
     for (int stage = 1; stage <= 4 && err == cudaSuccess; ++stage) {
-        err = launch_rk4_stage(pl, m, stage, sl, dt, cs);
+        err = pl->model == CIA_MODEL_POLYNOMIAL ? poly_launch_stage(pl, m, stage, sl, dt, cs)
+                                                : launch_rk4_stage(pl, m, stage, sl, dt, cs);
         sl ^= 1;
     }
     if (err == cudaSuccess && r_out) err = launch_order_parameters(pl, sl, r_out, cs);
@@ -250,6 +264,8 @@ extern "C" cia_status cia_state_load(cia_plan_t *pl, const double *x, void *stre
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
         CIA_CUDA_TRY(cs_launch_load(pl, x, true, 0, (cudaStream_t)stream));
         pl->cs_feat_valid = false;   // features are computed by the first CIA step
+    } else if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        CIA_CUDA_TRY(poly_launch_load(pl, x, true, 0, (cudaStream_t)stream));
     } else {
         CIA_CUDA_TRY(launch_phasors_from_x(pl, x, true, 0, (cudaStream_t)stream));
     }
@@ -279,8 +295,12 @@ extern "C" cia_status cia_advance(cia_plan_t *pl, int method, double dt, int64_t
     cudaStream_t s = (cudaStream_t)stream;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) return cs_advance(pl, method, dt, nsteps, r_out, s);
     const int m = method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA;
-    st = ensure_omega_constants(pl, dt, s);
-    if (st != CIA_OK) return st;
+    if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        if (r_out) return fail(CIA_ERR_INVALID_ARG, "r_out must be NULL for the polynomial model");
+    } else {
+        st = ensure_omega_constants(pl, dt, s);
+        if (st != CIA_OK) return st;
+    }
     if (r_out) CIA_CUDA_TRY(cudaMemsetAsync(pl->d.r_counter, 0, sizeof(int64_t), s));
     const bool profiling = pl->prof_on && pl->prof_used < pl->prof_cap;
     const bool graphs = pl->use_graphs == 0 && nsteps >= 2 && !profiling;
@@ -413,6 +433,7 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
     if (st != CIA_OK && st != CIA_ERR_UNSUPPORTED) return st;
     if (!x) return fail(CIA_ERR_INVALID_ARG, "x is NULL");
     if (steps < 1 || !std::isfinite(dt)) return fail(CIA_ERR_INVALID_ARG, "need steps >= 1 and a finite dt");
+    if (pl->model == CIA_MODEL_POLYNOMIAL) return fail(CIA_ERR_UNSUPPORTED, "no tuning candidates for the polynomial model");
     struct Cand { int tn, tib, staging; };
     std::vector<Cand> cands;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {

@@ -93,6 +93,9 @@ struct DeviceBuffers {
     int32_t *cs_check_comm = nullptr;         // their communities
     double *cs_check_out = nullptr;           // [check_count][2] error, reference
     float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
+    // polynomial coupling (FP64 stage states and tile power sums)
+    double *pl_y[2] = {nullptr, nullptr};     // [n+1] stage states
+    double *pl_part[2] = {nullptr, nullptr};  // [T][p+1] sums of y^k per tile
     // ensembles of independent networks
     void *tile_kn = nullptr;                  // [T] K / N_i of the tile's instance, compute precision
     int32_t *inst_tiles = nullptr;            // [B][4] community tiles [0,1), free tiles [2,3) of instance i
@@ -169,6 +172,10 @@ struct cia_plan {
     // Cucker--Smale
     int state_dim = 1;                  // FP64 values per node at the boundary
     double cs_sigma = 1.0, cs_beta = 0.0;
+    // polynomial coupling
+    int poly_p = 0;
+    double poly_c[CIA_MAX_POLY + 1] = {0};
+    double poly_dv[CIA_MAX_POLY + 1] = {0};
     bool cs_has_basis = false;          // a basis was set (cia_plan_set_basis)
     bool cs_feat_valid = false;         // features/partials match the resident state
     int64_t cs_check_count = 0;
@@ -213,5 +220,11 @@ cudaError_t cs_launch_store(cia_plan *pl, double *x, cudaStream_t s);
 cudaError_t cs_launch_check(cia_plan *pl, int slot, cudaStream_t s);
 cudaError_t cs_launch_sample(cia_plan *pl, int slot, int64_t count, uint64_t seed, float *pairs, cudaStream_t s);
 size_t cs_stage_smem_bytes(const cia_plan *pl);
+
+// Polynomial-coupling launchers (polynomial.cu).
+cudaError_t poly_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
+cudaError_t poly_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
+cudaError_t poly_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
+size_t poly_stage_smem_bytes(const cia_plan *pl);
 
 }  // namespace cia

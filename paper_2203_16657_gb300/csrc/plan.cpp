@@ -319,9 +319,29 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     pl->use_graphs = opt ? opt->use_graphs : 0;
     if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
-        cp->model != CIA_MODEL_CUCKER_SMALE)
+        cp->model != CIA_MODEL_CUCKER_SMALE && cp->model != CIA_MODEL_POLYNOMIAL)
         return fail(CIA_ERR_UNSUPPORTED, "unknown model");
-    if (cp->model == CIA_MODEL_CUCKER_SMALE) {
+    if (cp->model == CIA_MODEL_POLYNOMIAL) {
+        if (pl->precision != CIA_FP64)
+            return fail(CIA_ERR_UNSUPPORTED, "the polynomial model runs in FP64 (precision CIA_FP64)");
+        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial model");
+        if (cp->p < 0 || cp->p > CIA_MAX_POLY) return fail(CIA_ERR_INVALID_ARG, "p must be in [0, CIA_MAX_POLY]");
+        if (!std::isfinite(cp->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
+        for (int k = 0; k <= CIA_MAX_POLY; ++k)
+            if (!std::isfinite(cp->poly_c[k]) || !std::isfinite(cp->dV[k]))
+                return fail(CIA_ERR_NUMERIC, "a polynomial coefficient is not finite");
+        if (pl->tile_nodes > 256)
+            return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be <= 256 for the polynomial model");
+        pl->model = cp->model;
+        pl->p = 1;
+        pl->poly_p = cp->p;
+        for (int k = 0; k <= CIA_MAX_POLY; ++k) {
+            pl->poly_c[k] = k <= cp->p ? cp->poly_c[k] : 0.0;
+            pl->poly_dv[k] = cp->dV[k];
+        }
+        pl->K = cp->K;
+        pl->staging = 1;   // its own one-CTA-per-tile kernel
+    } else if (cp->model == CIA_MODEL_CUCKER_SMALE) {
         if (pl->precision != CIA_FP32)
             return fail(CIA_ERR_UNSUPPORTED, "the Cucker-Smale model runs in FP32 (precision CIA_FP32)");
         if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the Cucker-Smale model");
@@ -559,7 +579,12 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
             CIA_OK)
             return s2;
     }
-    if (pl->model != CIA_MODEL_CUCKER_SMALE) {
+    if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
+        if ((s2 = alloc_bytes(pl, &d.acc, n * sizeof(double))) != CIA_OK) return s2;
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = upload<double>(pl, &d.pl_y[b], nullptr, (size_t)n + 1)) != CIA_OK) return s2;
+    } else if (pl->model != CIA_MODEL_CUCKER_SMALE) {
         if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
         if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
         for (int b = 0; b < 2; ++b)
@@ -709,6 +734,10 @@ static cia_status build_tiles(cia_plan *pl) {
             if ((s2 = upload<double>(pl, &d.cs_part[b], nullptr, (size_t)T * 3 * CIA_BASIS_RANK, true)) != CIA_OK)
                 return s2;
         pl->cs_feat_valid = false;
+    } else if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = upload<double>(pl, &d.pl_part[b], nullptr, (size_t)T * (pl->poly_p + 1), true)) != CIA_OK)
+                return s2;
     } else {
         for (int b = 0; b < 2; ++b)
             if ((s2 = upload<double>(pl, &d.part[b], nullptr, (size_t)T * pl->p * 2, true)) != CIA_OK) return s2;
@@ -743,7 +772,7 @@ static cia_status build_tiles(cia_plan *pl) {
         d.tile_kn = pk;
         UPT(d.inst_tiles, itab.data(), itab.size());
     }
-    if (pl->model == CIA_MODEL_CUCKER_SMALE) {
+    if (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) {
         UPT(d.tile_desc, tdesc.data(), tdesc.size());
         CIA_CUDA_TRY(cudaDeviceSynchronize());
         return CIA_OK;
@@ -946,7 +975,8 @@ extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_i
     clear_error();
     if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
     const int tn = tile_nodes ? tile_nodes : (pl->model == CIA_MODEL_CUCKER_SMALE ? 128 : 256);
-    if (tn < 32 || tn > 1024 || tn % 32 || (pl->model == CIA_MODEL_CUCKER_SMALE && tn > 128))
+    if (tn < 32 || tn > 1024 || tn % 32 || (pl->model == CIA_MODEL_CUCKER_SMALE && tn > 128) ||
+        (pl->model == CIA_MODEL_POLYNOMIAL && tn > 256))
         return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024] (<= 128 for Cucker-Smale)");
     const int tib = tile_index_bytes ? tile_index_bytes : 65536;
     if (tib < 256 || tib % 16) return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
@@ -957,7 +987,7 @@ extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_i
     CIA_CUDA_TRY(cudaDeviceSynchronize());
     pl->tile_nodes = tn;
     pl->tile_index_bytes = tib;
-    pl->staging_req = pl->model == CIA_MODEL_CUCKER_SMALE ? 1 : staging;
+    pl->staging_req = (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) ? 1 : staging;
     cia_status st;
     try {
         st = build_tiles(pl);

@@ -1,0 +1,225 @@
+"""Parity of the CUDA polynomial-coupling path (moments of x, App. A.3;
+Desai--Zwanzig, App. A.5) with the FP64 oracle, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic): the path is FP64
+throughout; the moment expansion cancels terms of size lambda max|x|^p against
+each other, so the coupling part of the RHS is compared norm-wise within
+1e-12 relative (inf-norm); trajectories of 100 RK4 steps within 1e-11 of the
+largest state; the linear-consensus closed form within 1e-12.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from helpers import coupling_rel_err, cuda_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+FP64_TOL = 1e-12
+DW_DV = (0.0, -1.0, 0.0, 1.0)      # V(x) = x^4/4 - x^2/2: V'(x) = x^3 - x
+
+
+@pytest.fixture(scope="module")
+def cia():
+    import paper_2203_16657_gb300 as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    torch.cuda.init()
+    return torch
+
+
+def make_plan(cia, g, K, c, dv, **kw):
+    return cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", K=K, poly_c=c, dV=dv,
+                    precision="fp64", build_direct=True, **kw)
+
+
+def gpu_rhs(torch_mod, plan, x, method):
+    xd = torch_mod.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    out = plan.rhs(xd, method=method)
+    torch_mod.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def coupling_err(oracle_mod, g, x, got, ref, c, dv):
+    # the potential term alone: the oracle with K = 0
+    pot = oracle_mod.poly_direct(g.rowptr, g.col, x, 0.0, c, dv)
+    return coupling_rel_err(got, ref, pot)
+
+
+# ------------------------------------------------------------------ RHS parity
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+def test_rhs_degrees(cia, oracle_mod, torch_mod, p):
+    rng = np.random.default_rng(100 + p)
+    g = S.sbm_graph([40, 70, 33, 64], 0.8, inter_degree=5.0, seed=70 + p, n_free=9)
+    c = rng.normal(size=p + 1)
+    dv = rng.normal(size=5)
+    x = rng.normal(size=g.n)
+    plan = make_plan(cia, g, 1.7, c, dv, tile_nodes=32)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 1.7, c, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        if p == 0:
+            # h constant: the coupling is K/N c_0 deg(m), no cancellation
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), method
+        else:
+            assert coupling_err(oracle_mod, g, x, got, ref, c, dv) < FP64_TOL, method
+
+
+@pytest.mark.parametrize("group_size", [4, 16, 32])
+@pytest.mark.parametrize("tile_nodes,tile_index_bytes", [(32, 0), (96, 0), (256, 0), (256, 256),
+                                                         (128, 4096)])
+def test_rhs_launch_shapes(cia, oracle_mod, torch_mod, group_size, tile_nodes, tile_index_bytes):
+    """Several tiles per community with a ragged tail, index budgets that cut
+    tiles at single rows, every group width of the direct kernel."""
+    g = S.sbm_graph([300, 129, 31, 700], 0.9, inter_degree=6.0, seed=7, n_free=40)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(-1.5, 1.5, g.n)
+    c, dv = (0.1, 1.0, -0.3, 0.2), DW_DV
+    plan = make_plan(cia, g, 2.5, c, dv, tile_nodes=tile_nodes, group_size=group_size,
+                     tile_index_bytes=tile_index_bytes)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 2.5, c, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert coupling_err(oracle_mod, g, x, got, ref, c, dv) < FP64_TOL, method
+
+
+@pytest.mark.parametrize("case", ["all_free", "no_edges", "single_node", "empty_labels",
+                                  "singletons", "complete"])
+def test_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
+    rng = np.random.default_rng(5)
+    if case == "all_free":
+        g = S.random_labels_graph(30, 0.3, 1, seed=1, free_frac=1.0)
+    elif case == "no_edges":
+        g = S.random_labels_graph(20, 0.0, 3, seed=2, free_frac=0.1)
+    elif case == "single_node":
+        g = S.Graph(1, np.array([0, 0], np.int64), np.zeros(0, np.int32),
+                    np.array([0], np.int32), np.array([1], np.int64))
+    elif case == "empty_labels":
+        g = S.random_labels_graph(40, 0.4, 3, seed=4, free_frac=0.0)
+        g.labels = (g.labels * 3 + 2).astype(np.int32)
+    elif case == "singletons":
+        g = S.random_labels_graph(25, 0.5, 1, seed=5, free_frac=0.0)
+        g.labels = np.arange(g.n, dtype=np.int32)
+    else:
+        g = S.complete_graph_communities([17, 5, 1], seed=6)
+    x = rng.normal(size=g.n)
+    c, dv = (0.2, -1.0, 0.5, 0.25, -0.1), (0.3, -1.0, 0.1, 1.0, 0.05)
+    plan = make_plan(cia, g, 1.5, c, dv)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 1.5, c, dv)
+    pot = oracle_mod.poly_direct(g.rowptr, g.col, x, 0.0, c, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        if np.abs(ref - pot).max() == 0:
+            assert np.abs(got - ref).max() <= 1e-15 * max(1.0, np.abs(ref).max()), method
+        else:
+            assert coupling_rel_err(got, ref, pot) < FP64_TOL, method
+
+
+def test_rhs_matches_oracle_cia_permuted(cia, oracle_mod, torch_mod):
+    """The oracle's own moment formula (permuted order) agrees with the device
+    CIA too: the same E1/E2 split, evaluated independently."""
+    g = S.sbm_graph([64, 200, 90], 0.85, inter_degree=4.0, seed=12, n_free=11)
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=g.n)
+    c, dv = (0.0, 1.0, 0.0, -0.2), DW_DV
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    ref = oracle_mod.poly_cia(sp, x[sp.perm], 0.9, c, dv)[sp.iperm]
+    plan = make_plan(cia, g, 0.9, c, dv)
+    got = gpu_rhs(torch_mod, plan, x, "cia")
+    assert coupling_err(oracle_mod, g, x, got, ref, c, dv) < FP64_TOL
+
+
+# ------------------------------------------------------------------ integration
+
+def test_integrate_desai_zwanzig(cia, oracle_mod, torch_mod):
+    """Double-well units (V' = x^3 - x) with linear attraction on a community
+    graph: 100 RK4 steps of dt = 0.01 against the oracle's RK4 of the direct sum."""
+    g = S.sbm_graph([120, 300, 57, 200], 0.7, inter_degree=5.0, seed=21, n_free=23)
+    rng = np.random.default_rng(9)
+    x0 = rng.normal(0.0, 1.2, g.n)
+    c, K, dt, steps = (0.0, 1.0), 4.0, 0.01, 100
+    rhs = lambda y: oracle_mod.poly_direct(g.rowptr, g.col, y, K, c, DW_DV)
+    ref, _ = oracle_mod.integrate(rhs, x0, dt, steps, wrap=False)
+    plan = make_plan(cia, g, K, c, DW_DV)
+    for method in ("cia", "direct"):
+        x = torch_mod.from_numpy(x0.copy()).cuda()
+        plan.integrate(x, dt, steps, method=method)
+        got = x.cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max(), method
+
+
+def test_integrate_cubic_coupling_graph_replay(cia, oracle_mod, torch_mod):
+    """A cubic h on a larger graph (several tiles per community) through
+    several advance calls: CUDA-graph replay and plain launches agree with the
+    oracle's RK4."""
+    g = S.sbm_graph([700, 300, 129], 0.9, inter_degree=6.0, seed=31, n_free=17)
+    rng = np.random.default_rng(10)
+    x0 = rng.uniform(-1.0, 1.0, g.n)
+    c, dv, K, dt = (0.0, 0.5, 0.0, -0.3), (0.0, -1.0, 0.0, 1.0), 3.0, 0.02
+    rhs = lambda y: oracle_mod.poly_direct(g.rowptr, g.col, y, K, c, dv)
+    ref, _ = oracle_mod.integrate(rhs, x0, dt, 40, wrap=False)
+    for graphs in (True, False):
+        plan = make_plan(cia, g, K, c, dv, tile_nodes=128, use_graphs=graphs)
+        x = torch_mod.from_numpy(x0.copy()).cuda()
+        plan.state_load(x)
+        for _ in range(4):
+            plan.advance(dt, 10)
+        plan.state_store(x)
+        got = x.cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max(), graphs
+
+
+def test_linear_consensus_closed_form(cia, torch_mod):
+    """V' = 0, h(x) = x on one complete community: x' = K (mean - x_m) exactly,
+    so each RK4 step keeps the mean and scales every deviation by the RK4
+    stability polynomial R(-K dt)."""
+    n, K, dt, steps = 300, 1.3, 0.05, 25
+    g = S.complete_graph_communities([n], seed=1)
+    x0 = np.random.default_rng(4).normal(size=n)
+    plan = make_plan(cia, g, K, (0.0, 1.0), (0.0,))
+    z = -K * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    want = x0.mean() + (x0 - x0.mean()) * R ** steps
+    for method in ("cia", "direct"):
+        x = torch_mod.from_numpy(x0.copy()).cuda()
+        plan.integrate(x, dt, steps, method=method)
+        assert np.abs(x.cpu().numpy() - want).max() < 1e-12, method
+
+
+def test_integrate_host_buffers(cia, torch_mod):
+    g = S.sbm_graph([50, 80], 0.8, inter_degree=3.0, seed=3, n_free=5)
+    x0 = np.random.default_rng(6).normal(size=g.n)
+    plan = make_plan(cia, g, 2.0, (0.0, 1.0), DW_DV)
+    x_dev = torch_mod.from_numpy(x0.copy()).cuda()
+    plan.integrate(x_dev, 0.01, 10)
+    x_host = x0.copy()
+    plan.integrate_host(x_host, 0.01, 10)
+    assert np.array_equal(x_host, x_dev.cpu().numpy())
+
+
+# ------------------------------------------------------------------ errors
+
+def test_plan_rejections(cia, torch_mod):
+    g = S.sbm_graph([40, 30], 0.8, inter_degree=2.0, seed=1, n_free=3)
+    with pytest.raises(cia.CiaError, match="omega"):
+        cia.Plan(g.rowptr, g.col, g.labels, np.zeros(g.n), model="polynomial", poly_c=(0.0, 1.0))
+    with pytest.raises(cia.CiaError, match="FP64"):
+        cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", precision="fp32")
+    with pytest.raises(cia.CiaError, match="tile_nodes"):
+        cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", tile_nodes=512)
+    with pytest.raises(ValueError):
+        cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", poly_c=tuple(range(6)))
+    plan = make_plan(cia, g, 1.0, (0.0, 1.0), DW_DV)
+    x = torch_mod.zeros(g.n, dtype=torch_mod.float64, device="cuda")
+    r = torch_mod.zeros(3, dtype=torch_mod.float64, device="cuda")
+    with pytest.raises(cia.CiaError, match="r_out"):
+        plan.integrate(x, 0.01, 3, r_out=r)
+    with pytest.raises(cia.CiaError):
+        plan.autotune(x, 0.01, 1)
