@@ -71,6 +71,9 @@ def _load():
         lib.ora_poly_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P]
         lib.ora_poly_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
                                      P, P]
+        lib.ora_polyg_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P]
+        lib.ora_polyg_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
+                                      P, P]
         _lib = lib
     return _lib
 
@@ -309,6 +312,38 @@ def poly_cia(sp: Split, x_perm, K, c, dv) -> np.ndarray:
     out = np.empty_like(x)
     lib.ora_poly_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
                      float(K), len(c) - 1, _p(c), len(dv) - 1, _p(dv), _p(w), _p(out))
+    return out
+
+
+def _square(G) -> np.ndarray:
+    G = _f64(G)
+    if G.ndim != 2 or G.shape[0] != G.shape[1] or G.shape[0] < 1:
+        raise ValueError("G must be a square (p+1) x (p+1) array")
+    return np.ascontiguousarray(G)
+
+
+def polyg_direct(rowptr, col, x, K, G, dv) -> np.ndarray:
+    """x' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m) with the general polynomial
+    g(u, y) = sum_{a,b} G[a, b] u^a y^b (eq. PolyApprox)."""
+    lib = _load()
+    x = _f64(x)
+    G, dv = _square(G), _f64(dv)
+    out = np.empty_like(x)
+    lib.ora_polyg_direct(len(x), _p(_i64(rowptr)), _p(_i32(col)), _p(x), float(K), G.shape[0] - 1,
+                         _p(G), len(dv) - 1, _p(dv), _p(out))
+    return out
+
+
+def polyg_cia(sp: Split, x_perm, K, G, dv) -> np.ndarray:
+    """The same right-hand side by the CIA: moments w_a (eq. PolyMoments), the
+    dense term sum_{a,b} G[a, b] w_a x_m^b (eq. PolyRHS), the sparse sum over S."""
+    lib = _load()
+    x = _f64(x_perm)
+    G, dv = _square(G), _f64(dv)
+    w = np.zeros(max(1, sp.M * G.shape[0]))
+    out = np.empty_like(x)
+    lib.ora_polyg_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
+                      float(K), G.shape[0] - 1, _p(G), len(dv) - 1, _p(dv), _p(w), _p(out))
     return out
 
 

@@ -374,3 +374,70 @@ void ora_poly_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_row
         out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
     }
 }
+
+/* ------------------------------------------------------------------------
+ * General polynomial coupling (Sec. "General Network Model - Polynomial
+ * Expansion", eq. PolyApprox, eq. PolyMoments, eq. PolyRHS):
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m),
+ *   g(u, y) = sum_{a=0..p} sum_{b=0..p} G[a][b] u^a y^b   (u: the neighbour),
+ * G row-major with p + 1 columns. */
+static double poly2_eval(const double *G, int p, double u, double y) {
+    double s = 0.0;
+    for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) s += G[a * (p + 1) + b] * pow(u, (double)a) * pow(y, (double)b);
+    return s;
+}
+
+/* Direct RHS: the CSR neighbours of m one by one. */
+void ora_polyg_direct(int64_t n, const int64_t *rowptr, const int32_t *col, const double *x, double K,
+                      int p, const double *G, int q, const double *dv, double *out) {
+    const double scale = K / (double)n;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int64_t e = rowptr[m]; e < rowptr[m + 1]; ++e) acc += poly2_eval(G, p, x[col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + scale * acc;
+    }
+}
+
+/* CIA RHS (permuted state, S with its diagonal -1 entries):
+ * (E1.1) w[c][a] = (1/N) sum_{l in c} x_l^a, a = 0..p          (eq. PolyMoments)
+ * (E1.2) dense_m = sum_a sum_b G[a][b] w[c][a] x_m^b            (eq. PolyRHS)
+ * (E2)   sparse_m = (1/N) sum_l s_ml g(x_l, x_m)
+ *        out_m = -V'(x_m) + K (dense_m + sparse_m).
+ * w: caller scratch of M * (p + 1) doubles. */
+void ora_polyg_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_rowptr, const int32_t *s_col,
+                   const int8_t *s_val, const double *x, double K, int p, const double *G, int q,
+                   const double *dv, double *w, double *out) {
+    const double invN = 1.0 / (double)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t cc = 0; cc < M; ++cc) {
+        for (int a = 0; a <= p; ++a) {
+            double s = 0.0;
+            for (int64_t l = off[cc]; l < off[cc + 1]; ++l) s += pow(x[l], (double)a);
+            w[cc * (p + 1) + a] = invN * s;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        int64_t cc = -1;
+        if (m < off[M]) {
+            int64_t lo = 0, hi = M;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) / 2;
+                if (off[mid] <= m) lo = mid;
+                else hi = mid;
+            }
+            cc = lo;
+        }
+        double dense = 0.0;
+        if (cc >= 0)
+            for (int a = 0; a <= p; ++a)
+                for (int b = 0; b <= p; ++b)
+                    dense += G[a * (p + 1) + b] * w[cc * (p + 1) + a] * pow(x[m], (double)b);
+        double sparse = 0.0;
+        for (int64_t e = s_rowptr[m]; e < s_rowptr[m + 1]; ++e)
+            sparse += (double)s_val[e] * poly2_eval(G, p, x[s_col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
+    }
+}

@@ -417,3 +417,90 @@ def test_polynomial_cia_equals_direct(oracle_mod, seed):
     sp = oracle_mod.split(g.rowptr, g.col, g.labels)
     got = oracle_mod.poly_cia(sp, x[sp.perm], 1.3, c, dv)[sp.iperm]
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------ general polynomial g(x_l, x_m)
+
+def test_general_polynomial_linear_neighbour_term_is_a_sparse_matvec(oracle_mod):
+    """g(u, y) = u: x' = (K/N) A x, checked against scipy's CSR product."""
+    sp_mod = pytest.importorskip("scipy.sparse")
+    import synthetic as S
+    g = S.random_labels_graph(60, 0.2, 3, seed=3, free_frac=0.1)
+    x = np.random.default_rng(1).normal(size=g.n)
+    A = sp_mod.csr_matrix((np.ones(len(g.col)), g.col, g.rowptr), shape=(g.n, g.n))
+    G = np.zeros((2, 2))
+    G[1, 0] = 1.0
+    got = oracle_mod.polyg_direct(g.rowptr, g.col, x, 2.0, G, [0.0])
+    np.testing.assert_allclose(got, (2.0 / g.n) * (A @ x), rtol=1e-14, atol=1e-15)
+
+
+def test_general_polynomial_own_term_scales_with_degree(oracle_mod):
+    """g(u, y) = y^2 does not depend on the neighbour: x' = (K/N) deg(m) x_m^2."""
+    import synthetic as S
+    g = S.random_labels_graph(50, 0.3, 2, seed=4, free_frac=0.2)
+    x = np.random.default_rng(2).normal(size=g.n)
+    G = np.zeros((3, 3))
+    G[0, 2] = 1.0
+    got = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.5, G, [0.0])
+    deg = np.diff(g.rowptr)
+    np.testing.assert_allclose(got, (1.5 / g.n) * deg * x * x, rtol=1e-14, atol=0)
+
+
+def test_general_polynomial_of_a_difference_matches_the_difference_form(oracle_mod):
+    """h(u - y) = sum_a c_a (u - y)^a expands to G[a, b] = c_{a+b} binom(a+b, a)
+    (-1)^b: the general form reaches the difference oracle (eq. PolyApprox with
+    g(x, y) = h(x - y))."""
+    from math import comb
+    import synthetic as S
+    g = S.random_labels_graph(40, 0.3, 3, seed=5, free_frac=0.2)
+    rng = np.random.default_rng(3)
+    c = rng.normal(size=5)
+    p = len(c) - 1
+    G = np.zeros((p + 1, p + 1))
+    for a in range(p + 1):
+        for b in range(p + 1 - a):
+            G[a, b] = c[a + b] * comb(a + b, a) * (-1) ** b
+    x = rng.uniform(-1, 1, g.n)
+    dv = rng.normal(size=3)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 1.1, c, dv)
+    got = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.1, G, dv)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_general_polynomial_brute_force_tiny(oracle_mod):
+    """A 6-node graph with a dense adjacency matrix, summed in plain Python."""
+    A = np.array([[0, 1, 1, 0, 0, 1], [1, 0, 1, 0, 0, 0], [1, 1, 0, 1, 0, 0],
+                  [0, 0, 1, 0, 1, 1], [0, 0, 0, 1, 0, 1], [1, 0, 0, 1, 1, 0]])
+    rowptr = np.concatenate([[0], np.cumsum(A.sum(1))]).astype(np.int64)
+    col = np.concatenate([np.nonzero(r)[0] for r in A]).astype(np.int32)
+    rng = np.random.default_rng(4)
+    G = rng.normal(size=(3, 3))
+    dv = [0.5, -1.0]
+    x = rng.normal(size=6)
+    K, n = 0.7, 6
+    want = np.zeros(n)
+    for m in range(n):
+        s = 0.0
+        for l in range(n):
+            if A[m, l]:
+                s += sum(G[a, b] * x[l] ** a * x[m] ** b for a in range(3) for b in range(3))
+        want[m] = -(dv[0] + dv[1] * x[m]) + K / n * s
+    got = oracle_mod.polyg_direct(rowptr, col, x, K, G, dv)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_general_polynomial_cia_equals_direct(oracle_mod, seed):
+    """Moments w_a with the dense term sum G[a, b] w_a x_m^b (eq. PolyRHS) plus
+    the exact sparse corrections over S reach the direct sum."""
+    import synthetic as S
+    g = S.random_labels_graph(45, 0.3, 3, seed=80 + seed, free_frac=0.2)
+    rng = np.random.default_rng(seed)
+    p = 1 + seed
+    G = rng.normal(size=(p + 1, p + 1))
+    dv = rng.normal(size=4)
+    x = rng.normal(size=g.n)
+    ref = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.3, G, dv)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    got = oracle_mod.polyg_cia(sp, x[sp.perm], 1.3, G, dv)[sp.iperm]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
