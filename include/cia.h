@@ -55,7 +55,8 @@ typedef enum {
     CIA_MODEL_KURAMOTO = 0,     /* phase oscillators, h = sum_k d_sin[k] sin kx + d_cos[k] cos kx (App. A.4) */
     CIA_MODEL_KURAMOTO_HO = 1,  /* the same plus a triadic term on complete community hyperedges (App. A.7) */
     CIA_MODEL_CUCKER_SMALE = 2, /* 2-D flocking agents (App. A.6), state (s_x, s_y, v_x, v_y) per node */
-    CIA_MODEL_POLYNOMIAL = 3    /* polynomial difference coupling with a potential (App. A.3, A.5) */
+    CIA_MODEL_POLYNOMIAL = 3,   /* polynomial difference coupling with a potential (App. A.3, A.5) */
+    CIA_MODEL_POLYNOMIAL_GENERAL = 4 /* general polynomial coupling g(x_l, x_m) with a potential (App. A.3) */
 } cia_model;
 
 typedef enum {
@@ -107,7 +108,15 @@ typedef struct {
  * W_ck = sum_{l in c} x_l^k, k <= p (eq. PolyMoments) and the binomial
  * expansion of h (eq. PolyDifferenceRHSfast); the links of S are summed with
  * h itself.  Desai-Zwanzig: p = 1, poly_c = (0, 1).  FP64 only; omega must be
- * NULL. */
+ * NULL.
+ * CIA_MODEL_POLYNOMIAL_GENERAL (eq. GeneralNetworkPoly with eq. PolyApprox,
+ * App. A.3): the same with a general polynomial coupling
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m),
+ *   g(u, y) = sum_{a=0..p} sum_{b=0..p} poly_g[a * (CIA_MAX_POLY + 1) + b] u^a y^b
+ * (u is the neighbour's state; entries with a or b above p are ignored).  The
+ * CIA evaluates the dense term sum_{a,b} poly_g[a][b] W_ca x_m^b (eq. PolyRHS)
+ * from the same moments; the links of S are summed with g itself.  poly_c is
+ * ignored.  FP64 only; omega must be NULL. */
 typedef struct {
     int model;                  /* cia_model */
     int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
@@ -117,7 +126,8 @@ typedef struct {
     double K2;                  /* triadic coupling (CIA_MODEL_KURAMOTO_HO), multiplies (1/N^2) sum */
     double sigma, beta;         /* Cucker--Smale weight eta(y) = K (sigma^2 + y)^-beta, sigma > 0 */
     double poly_c[CIA_MAX_POLY + 1];   /* polynomial model: coefficients of h, degree p */
-    double dV[CIA_MAX_POLY + 1];       /* polynomial model: coefficients of V' */
+    double dV[CIA_MAX_POLY + 1];       /* polynomial models: coefficients of V' */
+    double poly_g[(CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)]; /* general polynomial model: g[a][b], row-major */
 } cia_coupling;
 
 typedef struct {

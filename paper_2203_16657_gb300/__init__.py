@@ -49,16 +49,18 @@ class Plan:
     model="polynomial": x' = -V'(x) + (K/N) sum_l a_ml h(x_l - x_m) with
     h(x) = sum_a poly_c[a] x^a (degree <= 4) and V'(x) = sum_j dV[j] x^j, FP64,
     omega None (Desai-Zwanzig: dV = (0, -1, 0, 1), poly_c = (0, 1)).
+    model="polynomial_general": the same with g(x_l, x_m) = sum_{a,b} poly_g[a][b] x_l^a x_m^b,
+    poly_g a square (p+1) x (p+1) array.
     """
 
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
                  tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0, sigma=1.0,
-                 beta=0.0, poly_c=(0.0, 1.0), dV=(0.0,), use_graphs=True, _batch=None):
+                 beta=0.0, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None, use_graphs=True, _batch=None):
         lib = load()
         self._lib = lib
         self._keep = []
-        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c, dV)
+        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c, dV, poly_g)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
                            int(group_size), int(tile_index_bytes), _abi.STAGING[staging],
                            0 if use_graphs else 1)
@@ -122,11 +124,12 @@ class Plan:
         return cls(None, None, None, _batch=(list(graphs), list(labels), list(omegas)), **kw)
 
     @staticmethod
-    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,)):
+    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None):
         d_sin = list(d_sin)
         d_cos = list(d_cos)
         p = len(d_sin)
-        if model != "polynomial" and (len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS):
+        poly = model in ("polynomial", "polynomial_general")
+        if not poly and (len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS):
             raise ValueError("d_sin and d_cos must have the same length in [1, %d]"
                              % _abi.CIA_MAX_HARMONICS)
         cp = _abi.Coupling()
@@ -139,16 +142,28 @@ class Plan:
         cp.K2 = float(K2)
         cp.sigma = float(sigma)
         cp.beta = float(beta)
-        if model == "polynomial":
-            poly_c, dV = list(poly_c), list(dV)
-            if not 1 <= len(poly_c) <= _abi.CIA_MAX_POLY + 1 or len(dV) > _abi.CIA_MAX_POLY + 1:
-                raise ValueError("poly_c needs 1..%d and dV at most %d coefficients"
-                                 % (_abi.CIA_MAX_POLY + 1, _abi.CIA_MAX_POLY + 1))
-            cp.p = len(poly_c) - 1
-            for a, v in enumerate(poly_c):
-                cp.poly_c[a] = float(v)
+        if poly:
+            S = _abi.CIA_MAX_POLY + 1
+            dV = list(dV)
+            if len(dV) > S:
+                raise ValueError("dV takes at most %d coefficients" % S)
             for j, v in enumerate(dV):
                 cp.dV[j] = float(v)
+            if model == "polynomial":
+                poly_c = list(poly_c)
+                if not 1 <= len(poly_c) <= S:
+                    raise ValueError("poly_c needs 1..%d coefficients" % S)
+                cp.p = len(poly_c) - 1
+                for a, v in enumerate(poly_c):
+                    cp.poly_c[a] = float(v)
+            else:
+                G = np.asarray(poly_g, dtype=np.float64) if poly_g is not None else None
+                if G is None or G.ndim != 2 or G.shape[0] != G.shape[1] or not 1 <= G.shape[0] <= S:
+                    raise ValueError("poly_g must be a square (p+1) x (p+1) array, p <= %d" % (S - 1))
+                cp.p = G.shape[0] - 1
+                for a in range(G.shape[0]):
+                    for b in range(G.shape[1]):
+                        cp.poly_g[a * S + b] = float(G[a, b])
         return cp
 
     # ------------------------------------------------------------ bookkeeping

@@ -57,13 +57,8 @@ cia_status check_plan(cia_plan *pl, int method) {
         return fail(CIA_ERR_UNSUPPORTED, "communities above 65536 nodes are not supported");
     int optin = 0;
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
-    if (pl->model == CIA_MODEL_POLYNOMIAL) {
-        // the stage kernel's static shared memory is under 4 KB
-        if (method == CIA_METHOD_CIA && poly_stage_smem_bytes(pl) > (size_t)optin - 4096)
-            return fail(CIA_ERR_UNSUPPORTED, "largest community (" + std::to_string(pl->max_comm) +
-                                                 " nodes) does not fit the shared-memory community window");
-        return CIA_OK;
-    }
+    // the polynomial stage kernel reads oversized communities from global memory
+    if (pl->model == CIA_MODEL_POLYNOMIAL) return CIA_OK;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
         if (method == CIA_METHOD_CIA && !pl->cs_has_basis)
             return fail(CIA_ERR_INVALID_ARG, "the Cucker-Smale CIA needs a basis (cia_plan_set_basis)");

@@ -174,8 +174,11 @@ struct cia_plan {
     double cs_sigma = 1.0, cs_beta = 0.0;
     // polynomial coupling
     int poly_p = 0;
+    int smem_optin = 0;                 // opt-in shared memory per block of the device
     double poly_c[CIA_MAX_POLY + 1] = {0};
     double poly_dv[CIA_MAX_POLY + 1] = {0};
+    bool poly_general = false;          // g(x_l, x_m) instead of h(x_l - x_m)
+    double poly_g[(CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)] = {0};
     bool cs_has_basis = false;          // a basis was set (cia_plan_set_basis)
     bool cs_feat_valid = false;         // features/partials match the resident state
     int64_t cs_check_count = 0;
@@ -225,6 +228,6 @@ size_t cs_stage_smem_bytes(const cia_plan *pl);
 cudaError_t poly_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
 cudaError_t poly_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
 cudaError_t poly_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
-size_t poly_stage_smem_bytes(const cia_plan *pl);
+bool poly_window_fits(const cia_plan *pl);
 
 }  // namespace cia

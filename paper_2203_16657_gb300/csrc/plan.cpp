@@ -319,28 +319,37 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     pl->use_graphs = opt ? opt->use_graphs : 0;
     if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
-        cp->model != CIA_MODEL_CUCKER_SMALE && cp->model != CIA_MODEL_POLYNOMIAL)
+        cp->model != CIA_MODEL_CUCKER_SMALE && cp->model != CIA_MODEL_POLYNOMIAL &&
+        cp->model != CIA_MODEL_POLYNOMIAL_GENERAL)
         return fail(CIA_ERR_UNSUPPORTED, "unknown model");
-    if (cp->model == CIA_MODEL_POLYNOMIAL) {
+    if (cp->model == CIA_MODEL_POLYNOMIAL || cp->model == CIA_MODEL_POLYNOMIAL_GENERAL) {
+        const bool general = cp->model == CIA_MODEL_POLYNOMIAL_GENERAL;
         if (pl->precision != CIA_FP64)
             return fail(CIA_ERR_UNSUPPORTED, "the polynomial model runs in FP64 (precision CIA_FP64)");
         if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial model");
         if (cp->p < 0 || cp->p > CIA_MAX_POLY) return fail(CIA_ERR_INVALID_ARG, "p must be in [0, CIA_MAX_POLY]");
         if (!std::isfinite(cp->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
-        for (int k = 0; k <= CIA_MAX_POLY; ++k)
-            if (!std::isfinite(cp->poly_c[k]) || !std::isfinite(cp->dV[k]))
+        constexpr int S = CIA_MAX_POLY + 1;
+        for (int k = 0; k < S; ++k) {
+            if ((!general && !std::isfinite(cp->poly_c[k])) || !std::isfinite(cp->dV[k]))
                 return fail(CIA_ERR_NUMERIC, "a polynomial coefficient is not finite");
+            for (int b = 0; general && b < S; ++b)
+                if (!std::isfinite(cp->poly_g[k * S + b]))
+                    return fail(CIA_ERR_NUMERIC, "a polynomial coefficient is not finite");
+        }
         if (pl->tile_nodes > 256)
             return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be <= 256 for the polynomial model");
-        pl->model = cp->model;
+        pl->model = CIA_MODEL_POLYNOMIAL;
+        pl->poly_general = general;
         pl->p = 1;
         pl->poly_p = cp->p;
-        for (int k = 0; k <= CIA_MAX_POLY; ++k) {
-            pl->poly_c[k] = k <= cp->p ? cp->poly_c[k] : 0.0;
+        for (int k = 0; k < S; ++k) {
+            pl->poly_c[k] = !general && k <= cp->p ? cp->poly_c[k] : 0.0;
             pl->poly_dv[k] = cp->dV[k];
+            for (int b = 0; b < S; ++b)
+                pl->poly_g[k * S + b] = general && k <= cp->p && b <= cp->p ? cp->poly_g[k * S + b] : 0.0;
         }
         pl->K = cp->K;
-        pl->staging = 1;   // its own one-CTA-per-tile kernel
     } else if (cp->model == CIA_MODEL_CUCKER_SMALE) {
         if (pl->precision != CIA_FP32)
             return fail(CIA_ERR_UNSUPPORTED, "the Cucker-Smale model runs in FP32 (precision CIA_FP32)");
@@ -551,6 +560,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     }
     cia_status s2;
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, pl->device));
+    CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
@@ -772,6 +782,11 @@ static cia_status build_tiles(cia_plan *pl) {
         d.tile_kn = pk;
         UPT(d.inst_tiles, itab.data(), itab.size());
     }
+    if (pl->model == CIA_MODEL_POLYNOMIAL) {
+        // its own one-CTA-per-tile kernel: community window in shared memory
+        // (auto, window, pipeline) or plain loads (plain, or when it does not fit)
+        pl->staging = (pl->staging == 1 || !poly_window_fits(pl)) ? 1 : 2;
+    }
     if (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) {
         UPT(d.tile_desc, tdesc.data(), tdesc.size());
         CIA_CUDA_TRY(cudaDeviceSynchronize());
@@ -987,7 +1002,7 @@ extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_i
     CIA_CUDA_TRY(cudaDeviceSynchronize());
     pl->tile_nodes = tn;
     pl->tile_index_bytes = tib;
-    pl->staging_req = (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) ? 1 : staging;
+    pl->staging_req = pl->model == CIA_MODEL_CUCKER_SMALE ? 1 : staging;
     cia_status st;
     try {
         st = build_tiles(pl);
@@ -1025,7 +1040,7 @@ extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *inf
     info->staging = pl->staging;
     info->group_size_direct = pl->group_size_direct;
     info->max_tile_index_bytes = pl->max_tile_idx_bytes;
-    info->model = pl->model;
+    info->model = pl->poly_general ? CIA_MODEL_POLYNOMIAL_GENERAL : pl->model;
     info->state_dim = pl->state_dim;
     info->instances = pl->B;
     return CIA_OK;

@@ -1,13 +1,19 @@
-// Device kernels of the polynomial difference coupling with a potential
-// (eq. GeneralNetworkPolyDifference, App. A.3; Desai-Zwanzig, App. A.5):
-//   x_m' = -V'(x_m) + (K/N) sum_l a_ml h(x_l - x_m),
-//   h(x) = sum_{a=0..p} c_a x^a,   V'(x) = sum_{j=0..4} v_j x^j,   FP64.
+// Device kernels of the polynomial couplings with a potential, FP64:
+//   difference form (eq. GeneralNetworkPolyDifference, App. A.3; Desai-Zwanzig,
+//   App. A.5):  x_m' = -V'(x_m) + (K/N) sum_l a_ml h(x_l - x_m),
+//               h(x) = sum_{a=0..p} c_a x^a;
+//   general form (eq. GeneralNetworkPoly, eq. PolyApprox):
+//               x_m' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m),
+//               g(u, y) = sum_{a,b=0..p} G_ab u^a y^b;
+//   V'(x) = sum_{j=0..4} v_j x^j.
 //
 // CIA (steps E1 + E2) for m in community c with moments W_ck = sum_{l in c} x_l^k:
-//   sum_{l in c} h(x_l - x_m) = sum_a c_a sum_{k=0..a} binom(a, k) W_ck (-x_m)^{a-k}
-//   (eq. PolyDifferenceRHSfast without the 1/N), minus the diagonal l = m
-//   (h(0) = c_0, a_mm = 0), minus h(x_l - x_m) over the missing links, plus
-//   h(x_l - x_m) over the inter-community links.
+//   difference: sum_{l in c} h(x_l - x_m) = sum_a c_a sum_{k=0..a} binom(a, k)
+//   W_ck (-x_m)^{a-k} (eq. PolyDifferenceRHSfast without the 1/N);
+//   general: sum_{l in c} g(x_l, x_m) = sum_a W_ca e_a(x_m) with
+//   e_a(y) = sum_b G_ab y^b (eq. PolyRHS without the 1/N);
+//   then minus the diagonal l = m (a_mm = 0), minus the coupling over the
+//   missing links, plus the coupling over the inter-community links.
 //
 // One CTA (256 threads) per tile and launch: (0) the community's moments from
 // the previous launch's tile sums and its states in shared memory, (A) the
@@ -38,9 +44,11 @@ struct PolyParams {
     int p;                       // degree of h
     double c[kMaxP + 1];         // h
     double v[kMaxP + 1];         // V'
+    double g[kMaxP + 1][kMaxP + 1];  // general form: G_ab, zero above degree p
     double k_over_n;
     int group;                   // threads per row of the direct kernel
-    int win_cap;                 // shared-memory window capacity (nodes)
+    int win_cap;                 // shared-memory window capacity (nodes); 0 = read the
+                                 // community's states from global memory
     const TileDesc *tile_desc;
     const unsigned char *blob;
     const int32_t *comm_tile_begin;
@@ -62,6 +70,39 @@ __device__ __forceinline__ double horner(const double *c, int p, double x) {
     for (int a = p; a >= 0; --a) s = fma(s, x, c[a]);
     return s;
 }
+
+// The coupling of one node y against its neighbours u: h(u - y) (difference
+// form) or g(u, y) = sum_a e_a(y) u^a (general form, e_a precomputed per node).
+// Coefficients above degree p are zero, so the full-degree Horner chain gives
+// the degree-p value exactly.
+template <bool GEN>
+struct Coupling {
+    double e[kMaxP + 1];
+    double y;
+    __device__ __forceinline__ Coupling(const PolyParams &a, double y_) : y(y_) {
+        if (GEN) {
+#pragma unroll
+            for (int al = 0; al <= kMaxP; ++al) {
+                double s = 0.0;
+#pragma unroll
+                for (int b = kMaxP; b >= 0; --b) s = fma(s, y_, a.g[al][b]);
+                e[al] = s;
+            }
+        }
+    }
+    __device__ __forceinline__ double operator()(const PolyParams &a, double u) const {
+        double s = 0.0;
+        if (GEN) {
+#pragma unroll
+            for (int al = kMaxP; al >= 0; --al) s = fma(s, u, e[al]);
+        } else {
+            const double d = u - y;
+#pragma unroll
+            for (int al = kMaxP; al >= 0; --al) s = fma(s, d, a.c[al]);
+        }
+        return s;
+    }
+};
 
 // RK4 stage update from the derivative k; returns the next stage state.
 template <int MODE>
@@ -109,9 +150,18 @@ __device__ __forceinline__ void tile_power_sums(int p, double *part_out, int til
     }
 }
 
-// Dense term of node state x: sum_{l in c} h(x_l - x) from the moments W
-// (binomial expansion), without the diagonal term h(0) = c_0.
+// Dense term of node state x: the community sum of the coupling from the
+// moments W, without the diagonal term (h(0) = c_0, or g(x, x)).
+template <bool GEN>
 __device__ __forceinline__ double dense_from_moments(const PolyParams &a, const double *W, double x) {
+    if (GEN) {
+        const Coupling<true> cx(a, x);
+        double dense = 0.0;
+#pragma unroll
+        for (int al = 0; al <= kMaxP; ++al)
+            if (al <= a.p) dense = fma(W[al], cx.e[al], dense);
+        return dense - cx(a, x);
+    }
     double dense = 0.0;
     for (int al = 0; al <= a.p; ++al) {
         double inner = 0.0, binom = 1.0, negx = 1.0;
@@ -126,7 +176,7 @@ __device__ __forceinline__ double dense_from_moments(const PolyParams &a, const 
     return dense - a.c[0];
 }
 
-template <int MODE>
+template <int MODE, bool GEN>
 __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double yrow[kTileMax];
@@ -144,8 +194,10 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned char *b = a.blob + d.blob_off;
     const uint32_t *vtab = reinterpret_cast<const uint32_t *>(b + d.vtab_off);
+    const double *cw = a.win_cap ? win : a.y_in + d.lo;
     // (0) window, own rows, moments (FP64 over the community's tiles), chunk table
-    for (int i = threadIdx.x; i < lam; i += kThreads) win[i] = a.y_in[d.lo + i];
+    if (a.win_cap)
+        for (int i = threadIdx.x; i < lam; i += kThreads) win[i] = a.y_in[d.lo + i];
     if (threadIdx.x < count) {
         yrow[threadIdx.x] = a.y_in[d.first + threadIdx.x];
         const uint32_t vt = __ldg(vtab + threadIdx.x);
@@ -172,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
         const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
         double ms = 0.0, is = 0.0;
         {
-            const double own = yrow[mrow != 0xffffu ? chunk_row[mrow] : 0];
+            const Coupling<GEN> cp(a, yrow[mrow != 0xffffu ? chunk_row[mrow] : 0]);
             const uint4 *mv = mvec + sd.x + lane;
             for (uint32_t j = 0; j < sd.y; ++j) {
                 const uint4 q = __ldg(mv + 32 * j);
@@ -180,20 +232,20 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int l0 = (int)(w4[e] & 0xffffu), l1 = (int)(w4[e] >> 16);
-                    if (l0 < lam) ms += horner(a.c, a.p, win[l0] - own);
-                    if (l1 < lam) ms += horner(a.c, a.p, win[l1] - own);
+                    if (l0 < lam) ms += cp(a, cw[l0]);
+                    if (l1 < lam) ms += cp(a, cw[l1]);
                 }
             }
         }
         {
-            const double own = yrow[irow != 0xffffu ? irow : 0];
+            const Coupling<GEN> cp(a, yrow[irow != 0xffffu ? irow : 0]);
             const int4 *iv = ivec + sd.z + lane;
             for (uint32_t j = 0; j < sd.w; ++j) {
                 const int4 q = __ldg(iv + 32 * j);
                 const int l4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (l4[e] < a.n) is += horner(a.c, a.p, __ldg(a.y_in + l4[e]) - own);
+                    if (l4[e] < a.n) is += cp(a, __ldg(a.y_in + l4[e]));
             }
         }
         if (mrow != 0xffffu) sWm[mrow] = ms;
@@ -210,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
         double sparse = sWi[r];
         const uint32_t vt = __ldg(vtab + r);
         for (uint32_t c = vt & 0xffffu; c < (vt & 0xffffu) + (vt >> 16); ++c) sparse -= sWm[c];
-        const double dense = comm ? dense_from_moments(a, W, x) : 0.0;
+        const double dense = comm ? dense_from_moments<GEN>(a, W, x) : 0.0;
         const double k = -horner(a.v, kMaxP, x) + a.k_over_n * (dense + sparse);
         ynext = rk4_update<MODE>(a, m, k);
     }
@@ -221,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
 // Direct method, one CTA per tile: `group` threads per row sum h(x_l - x_m)
 // over the row's CSR neighbours (rows padded to 4-entry vectors with the
 // sentinel n), then the same update and power sums as the CIA.
-template <int MODE>
+template <int MODE, bool GEN>
 __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams a) {
     __shared__ double sW[kTileMax];
     __shared__ double red[kWarps][kMaxP + 1];
@@ -232,14 +284,14 @@ __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams 
     const int4 *col4 = reinterpret_cast<const int4 *>(a.full_col);
     for (int r = grp; r < d.count; r += ngrp) {
         const int64_t m = d.first + r;
-        const double own = a.y_in[m];
+        const Coupling<GEN> cp(a, a.y_in[m]);
         double s = 0.0;
         for (int64_t v = a.full_rowptr[m] / 4 + gl; v < a.full_rowptr[m + 1] / 4; v += G) {
             const int4 q = __ldg(col4 + v);
             const int l4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                if (l4[e] < a.n) s += horner(a.c, a.p, __ldg(a.y_in + l4[e]) - own);
+                if (l4[e] < a.n) s += cp(a, __ldg(a.y_in + l4[e]));
         }
         for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (gl == 0) sW[r] = s;
@@ -274,6 +326,17 @@ __global__ void __launch_bounds__(kThreads) poly_load_kernel(const PolyParams a,
     tile_power_sums(a.p, a.part_out, t, live, y, red);
 }
 
+size_t window_cap(const cia_plan *pl) { return (size_t)((pl->max_comm + 1) & ~(int64_t)1); }
+constexpr size_t kTables = kMaxChunks * 8 + kTileMax * 8 + kMaxChunks * 2;
+
+// The largest community fits the shared-memory window (the kernel's static
+// shared memory is under 4 KB).
+bool window_fits(const cia_plan *pl) {
+    return window_cap(pl) * 8 + kTables + 4096 <= (size_t)pl->smem_optin;
+}
+
+size_t stage_smem(const cia_plan *pl) { return (pl->staging == 2 ? window_cap(pl) * 8 : 0) + kTables; }
+
 PolyParams base_params(const cia_plan *pl, int slot) {
     PolyParams a{};
     const auto &d = pl->d;
@@ -282,10 +345,11 @@ PolyParams base_params(const cia_plan *pl, int slot) {
     for (int k = 0; k <= kMaxP; ++k) {
         a.c[k] = k <= pl->poly_p ? pl->poly_c[k] : 0.0;
         a.v[k] = pl->poly_dv[k];
+        for (int b = 0; b <= kMaxP; ++b) a.g[k][b] = pl->poly_g[k * (kMaxP + 1) + b];
     }
     a.k_over_n = pl->K / (double)pl->n;
     a.group = pl->group_size_direct;
-    a.win_cap = (int)((pl->max_comm + 1) & ~(int64_t)1);
+    a.win_cap = pl->staging == 2 ? (int)window_cap(pl) : 0;
     a.tile_desc = d.tile_desc;
     a.blob = d.blob;
     a.comm_tile_begin = d.comm_tile_begin;
@@ -301,10 +365,6 @@ PolyParams base_params(const cia_plan *pl, int slot) {
     return a;
 }
 
-size_t stage_smem(const cia_plan *pl) {
-    const size_t cap = (size_t)((pl->max_comm + 1) & ~(int64_t)1);
-    return cap * 8 + kMaxChunks * 8 + kTileMax * 8 + kMaxChunks * 2;
-}
 
 // One launch of `kernel`, one tile per CTA; ID tells the instantiations apart
 // so that each kernel keeps its own configured shared-memory limit.
@@ -321,15 +381,21 @@ cudaError_t launch(void (*kernel)(PolyParams), const cia_plan *pl, size_t smem, 
     return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_tiles), dim3(kThreads), args, smem, s);
 }
 
+template <int MODE, bool GEN>
+cudaError_t launch_form(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
+    constexpr int id = 2 * MODE + (GEN ? 1 : 0);
+    if (method == Method::DIRECT) return launch<id + 6>(poly_direct_kernel<MODE, GEN>, pl, 0, a, s);
+    return launch<id>(poly_stage_kernel<MODE, GEN>, pl, stage_smem(pl), a, s);
+}
+
 template <int MODE>
 cudaError_t launch_mode(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
-    if (method == Method::DIRECT) return launch<MODE + 3>(poly_direct_kernel<MODE>, pl, 0, a, s);
-    return launch<MODE>(poly_stage_kernel<MODE>, pl, stage_smem(pl), a, s);
+    return pl->poly_general ? launch_form<MODE, true>(pl, method, a, s) : launch_form<MODE, false>(pl, method, a, s);
 }
 
 }  // namespace
 
-size_t poly_stage_smem_bytes(const cia_plan *pl) { return stage_smem(pl); }
+bool poly_window_fits(const cia_plan *pl) { return window_fits(pl); }
 
 cudaError_t poly_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
     // the load writes the state and its power sums into slot `slot`

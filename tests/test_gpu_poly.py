@@ -72,18 +72,22 @@ def test_rhs_degrees(cia, oracle_mod, torch_mod, p):
             assert coupling_err(oracle_mod, g, x, got, ref, c, dv) < FP64_TOL, method
 
 
+@pytest.mark.parametrize("staging", ["auto", "plain"])
 @pytest.mark.parametrize("group_size", [4, 16, 32])
 @pytest.mark.parametrize("tile_nodes,tile_index_bytes", [(32, 0), (96, 0), (256, 0), (256, 256),
                                                          (128, 4096)])
-def test_rhs_launch_shapes(cia, oracle_mod, torch_mod, group_size, tile_nodes, tile_index_bytes):
+def test_rhs_launch_shapes(cia, oracle_mod, torch_mod, group_size, tile_nodes, tile_index_bytes,
+                           staging):
     """Several tiles per community with a ragged tail, index budgets that cut
-    tiles at single rows, every group width of the direct kernel."""
+    tiles at single rows, every group width of the direct kernel, the community
+    window in shared memory (auto) and read from global memory (plain)."""
     g = S.sbm_graph([300, 129, 31, 700], 0.9, inter_degree=6.0, seed=7, n_free=40)
     rng = np.random.default_rng(2)
     x = rng.uniform(-1.5, 1.5, g.n)
     c, dv = (0.1, 1.0, -0.3, 0.2), DW_DV
     plan = make_plan(cia, g, 2.5, c, dv, tile_nodes=tile_nodes, group_size=group_size,
-                     tile_index_bytes=tile_index_bytes)
+                     tile_index_bytes=tile_index_bytes, staging=staging)
+    assert plan.info()["staging"] == (1 if staging == "plain" else 2)
     ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 2.5, c, dv)
     for method in ("cia", "direct"):
         got = gpu_rhs(torch_mod, plan, x, method)
@@ -204,6 +208,105 @@ def test_integrate_host_buffers(cia, torch_mod):
     assert np.array_equal(x_host, x_dev.cpu().numpy())
 
 
+# ------------------------------------------------------------------ general g(x_l, x_m)
+
+def make_general(cia, g, K, G, dv, **kw):
+    return cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial_general", K=K, poly_g=G,
+                    dV=dv, precision="fp64", build_direct=True, **kw)
+
+
+def general_err(oracle_mod, g, x, got, ref, G, dv):
+    pot = oracle_mod.polyg_direct(g.rowptr, g.col, x, 0.0, G, dv)
+    return coupling_rel_err(got, ref, pot)
+
+
+@pytest.mark.parametrize("staging", ["auto", "plain"])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+def test_general_rhs_degrees(cia, oracle_mod, torch_mod, p, staging):
+    rng = np.random.default_rng(200 + p)
+    g = S.sbm_graph([40, 70, 33, 64], 0.8, inter_degree=5.0, seed=90 + p, n_free=9)
+    G = rng.normal(size=(p + 1, p + 1))
+    dv = rng.normal(size=4)
+    x = rng.uniform(-1.2, 1.2, g.n)
+    plan = make_general(cia, g, 1.4, G, dv, tile_nodes=32, staging=staging)
+    assert plan.info()["model"] == 4
+    ref = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.4, G, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert general_err(oracle_mod, g, x, got, ref, G, dv) < FP64_TOL, method
+
+
+@pytest.mark.parametrize("tile_nodes,tile_index_bytes", [(64, 0), (256, 256), (128, 4096)])
+def test_general_rhs_launch_shapes(cia, oracle_mod, torch_mod, tile_nodes, tile_index_bytes):
+    g = S.sbm_graph([300, 129, 31, 700], 0.9, inter_degree=6.0, seed=8, n_free=40)
+    rng = np.random.default_rng(3)
+    G = rng.normal(size=(4, 4))
+    x = rng.uniform(-1.0, 1.0, g.n)
+    plan = make_general(cia, g, 2.0, G, DW_DV, tile_nodes=tile_nodes, tile_index_bytes=tile_index_bytes)
+    ref = oracle_mod.polyg_direct(g.rowptr, g.col, x, 2.0, G, DW_DV)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert general_err(oracle_mod, g, x, got, ref, G, DW_DV) < FP64_TOL, method
+
+
+@pytest.mark.parametrize("case", ["all_free", "single_node", "singletons", "complete"])
+def test_general_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
+    if case == "all_free":
+        g = S.random_labels_graph(30, 0.3, 1, seed=1, free_frac=1.0)
+    elif case == "single_node":
+        g = S.Graph(1, np.array([0, 0], np.int64), np.zeros(0, np.int32),
+                    np.array([0], np.int32), np.array([1], np.int64))
+    elif case == "singletons":
+        g = S.random_labels_graph(25, 0.5, 1, seed=5, free_frac=0.0)
+        g.labels = np.arange(g.n, dtype=np.int32)
+    else:
+        g = S.complete_graph_communities([17, 5, 1], seed=6)
+    rng = np.random.default_rng(6)
+    G = rng.normal(size=(3, 3))
+    x = rng.normal(size=g.n)
+    plan = make_general(cia, g, 1.5, G, (0.3, -1.0))
+    ref = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.5, G, (0.3, -1.0))
+    pot = oracle_mod.polyg_direct(g.rowptr, g.col, x, 0.0, G, (0.3, -1.0))
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        if np.abs(ref - pot).max() == 0:
+            assert np.abs(got - ref).max() <= 1e-15 * max(1.0, np.abs(ref).max()), method
+        else:
+            assert coupling_rel_err(got, ref, pot) < FP64_TOL, method
+
+
+def test_general_matches_difference_plan(cia, torch_mod):
+    """g(u, y) = h(u - y) written out as G_ab = c_{a+b} binom(a+b, a) (-1)^b:
+    the general and the difference plans agree on the device."""
+    from math import comb
+    g = S.sbm_graph([200, 90, 31], 0.85, inter_degree=4.0, seed=13, n_free=7)
+    c = (0.2, 1.0, -0.5, 0.3)
+    p = len(c) - 1
+    G = np.zeros((p + 1, p + 1))
+    for a in range(p + 1):
+        for b in range(p + 1 - a):
+            G[a, b] = c[a + b] * comb(a + b, a) * (-1) ** b
+    x = np.random.default_rng(5).uniform(-1, 1, g.n)
+    gen = gpu_rhs(torch_mod, make_general(cia, g, 1.2, G, DW_DV), x, "cia")
+    dif = gpu_rhs(torch_mod, make_plan(cia, g, 1.2, c, DW_DV), x, "cia")
+    assert np.abs(gen - dif).max() < 1e-12 * np.abs(dif).max()
+
+
+def test_general_integrate(cia, oracle_mod, torch_mod):
+    g = S.sbm_graph([120, 300, 57], 0.7, inter_degree=5.0, seed=22, n_free=13)
+    rng = np.random.default_rng(11)
+    x0 = rng.uniform(-0.8, 0.8, g.n)
+    G = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, -0.2], [0.1, 0.0, 0.0]])
+    K, dt, steps = 2.0, 0.01, 60
+    rhs = lambda y: oracle_mod.polyg_direct(g.rowptr, g.col, y, K, G, DW_DV)
+    ref, _ = oracle_mod.integrate(rhs, x0, dt, steps, wrap=False)
+    plan = make_general(cia, g, K, G, DW_DV)
+    for method in ("cia", "direct"):
+        x = torch_mod.from_numpy(x0.copy()).cuda()
+        plan.integrate(x, dt, steps, method=method)
+        assert np.abs(x.cpu().numpy() - ref).max() < 1e-11 * np.abs(ref).max(), method
+
+
 # ------------------------------------------------------------------ errors
 
 def test_plan_rejections(cia, torch_mod):
@@ -216,6 +319,11 @@ def test_plan_rejections(cia, torch_mod):
         cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", tile_nodes=512)
     with pytest.raises(ValueError):
         cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial", poly_c=tuple(range(6)))
+    with pytest.raises(ValueError):
+        cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial_general", poly_g=np.zeros((2, 3)))
+    with pytest.raises(cia.CiaError, match="finite"):
+        cia.Plan(g.rowptr, g.col, g.labels, None, model="polynomial_general",
+                 poly_g=np.array([[0.0, np.nan], [1.0, 0.0]]))
     plan = make_plan(cia, g, 1.0, (0.0, 1.0), DW_DV)
     x = torch_mod.zeros(g.n, dtype=torch_mod.float64, device="cuda")
     r = torch_mod.zeros(3, dtype=torch_mod.float64, device="cuda")
