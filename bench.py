@@ -57,7 +57,8 @@ def parse():
                     help="instances of the seeded 4096-network ensemble to run")
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the small FP64 and the higher-order Kuramoto workloads")
-    ap.add_argument("--only", choices=["cs", "ensemble", "small"], default=None,
+    ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-coupling workloads")
+    ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly"], default=None,
                     help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
 
@@ -391,6 +392,67 @@ def ensemble_leg(args, torch, cia, flush) -> dict:
     }
 
 
+# ------------------------------------------------------------------ polynomial couplings (secondary line)
+
+POLY_WORKLOAD = ("desai_zwanzig: the kuramoto_lognormal graph (N=262144, 256 lognormal communities, "
+                 "p_in=0.95, inter ER degree 8), x' = -V'(x) + (K/N) sum a_ml (x_l - x_m), "
+                 "V(x) = x^4/4 - x^2/2, K=1, x0~N(0,1), RK4 dt=0.01, FP64")
+
+
+def poly_stage_bytes(info: dict) -> float:
+    """Algorithmic bytes of one polynomial CIA stage launch (FP64), averaged
+    over the four RK4 stages.  Per node: stage state read once (8 B; window
+    and inter-link gathers reuse it), next state written (8 B), FP64 master
+    read (8 B; written in the final stage: +2 B on average), accumulator read
+    and written in 3 of 4 stages (6 + 6 B): 38 B.  Per missing link a 16-bit
+    index, per inter link a 32-bit index."""
+    return info["n"] * 38 + info["nnz_missing"] * info["missing_index_bytes"] + info["nnz_inter"] * 4
+
+
+def poly_leg(args, torch, cia, flush) -> dict:
+    """CIA vs direct on the Desai--Zwanzig model (difference coupling h(x) = x,
+    first moment only) and on a general quadratic coupling g(x_l, x_m) over the
+    headline graph, with RHS errors against the FP64 oracle."""
+    import oracle
+    import synthetic as S
+    oracle.set_num_threads(host_cores())
+    w = S.kuramoto_lognormal(scale=args.scale)
+    g = w.graph
+    x0np = np.random.default_rng(2203166576).normal(size=g.n)
+    x0 = torch.from_numpy(x0np.copy()).cuda()
+    dv, dt = (0.0, -1.0, 0.0, 1.0), 0.01
+    G = np.array([[0.0, -1.0, 0.2], [1.0, 0.0, 0.0], [-0.1, 0.0, 0.0]])
+    out = {"workload": POLY_WORKLOAD, "n": g.n}
+    steps = max(3, args.steps // 2)
+    for name, kw, ref_fn in (
+            ("desai_zwanzig", dict(model="polynomial", poly_c=(0.0, 1.0)),
+             lambda: oracle.poly_direct(g.rowptr, g.col, x0np, 1.0, (0.0, 1.0), dv)),
+            ("general_quadratic_g", dict(model="polynomial_general", poly_g=G),
+             lambda: oracle.polyg_direct(g.rowptr, g.col, x0np, 1.0, G, dv))):
+        plan = cia.Plan(g.rowptr, g.col, g.labels, None, K=1.0, dV=dv, precision="fp64",
+                        build_direct=True, **kw)
+        info = plan.info()
+        ref = ref_fn()
+        pot = oracle.poly_direct(g.rowptr, g.col, x0np, 0.0, (0.0,), dv)   # -V'(x) alone
+        err = {m: coupling_rel_err(plan.rhs(x0, method=m).cpu().numpy(), ref, pot) for m in ("cia", "direct")}
+        ms, prof = timed_steps(torch, plan, x0, dt, steps, args.warmup, "cia", flush, True)
+        dms, _ = timed_steps(torch, plan, x0, dt, steps, args.warmup, "direct", flush, False)
+        total, dtotal = float(sum(ms)), float(sum(dms))
+        stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+        sb = poly_stage_bytes(info)
+        out[name] = {
+            "steps": steps, "degree": 1 if name == "desai_zwanzig" else len(G) - 1,
+            "cia": {"value": g.n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
+                    "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
+                    "staging": {1: "plain loads", 2: "shared-memory community window"}[info["staging"]]},
+            "direct": {"value": g.n * steps / (dtotal / 1e3), "unit": UNIT, "ms_per_step": dtotal / steps},
+            "speedup_cia_over_direct": dtotal / max(total, 1e-12),
+            "error_vs_fp64_oracle": {"cia_rhs_coupling_rel": err["cia"], "direct_rhs_coupling_rel": err["direct"]},
+        }
+        plan.close()
+    return out
+
+
 # ------------------------------------------------------------------ small FP64 and higher-order workloads
 
 def _time_method(torch, plan, x0, dt, steps, warmup, method, flush) -> float:
@@ -509,7 +571,7 @@ def main():
     import paper_2203_16657_gb300 as cia
     if args.only:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-        leg = {"cs": cs_leg, "ensemble": ensemble_leg, "small": small_configs_leg}[args.only]
+        leg = {"cs": cs_leg, "ensemble": ensemble_leg, "small": small_configs_leg, "poly": poly_leg}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, torch, cia, flush)}), flush=True)
         return 0
     w = S.kuramoto_lognormal(scale=args.scale)
@@ -576,6 +638,9 @@ def main():
     small = None
     if not args.no_small_configs and world == 1:
         small = small_configs_leg(args, torch, cia, flush)
+    poly = None
+    if not args.no_poly and world == 1:
+        poly = poly_leg(args, torch, cia, flush)
 
     pk = peaks()
     stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
@@ -626,6 +691,8 @@ def main():
         line["ensemble"] = ens
     if small is not None:
         line.update(small)
+    if poly is not None:
+        line["polynomial"] = poly
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -342,7 +342,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         pl->model = CIA_MODEL_POLYNOMIAL;
         pl->poly_general = general;
         pl->p = 1;
-        pl->poly_p = cp->p;
+        pl->poly_p = std::max(cp->p, 1);   // kernels of degree 1..4; coefficients above p are zero
         for (int k = 0; k < S; ++k) {
             pl->poly_c[k] = !general && k <= cp->p ? cp->poly_c[k] : 0.0;
             pl->poly_dv[k] = cp->dV[k];

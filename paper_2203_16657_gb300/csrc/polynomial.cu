@@ -7,20 +7,32 @@
 //               g(u, y) = sum_{a,b=0..p} G_ab u^a y^b;
 //   V'(x) = sum_{j=0..4} v_j x^j.
 //
-// CIA (steps E1 + E2) for m in community c with moments W_ck = sum_{l in c} x_l^k:
-//   difference: sum_{l in c} h(x_l - x_m) = sum_a c_a sum_{k=0..a} binom(a, k)
-//   W_ck (-x_m)^{a-k} (eq. PolyDifferenceRHSfast without the 1/N);
-//   general: sum_{l in c} g(x_l, x_m) = sum_a W_ca e_a(x_m) with
-//   e_a(y) = sum_b G_ab y^b (eq. PolyRHS without the 1/N);
-//   then minus the diagonal l = m (a_mm = 0), minus the coupling over the
-//   missing links, plus the coupling over the inter-community links.
+// Both forms are sums of the neighbours' powers: sum_l a_ml g(x_l, x_m) =
+// sum_a T_a(m) e_a(x_m) with T_a(m) = sum_l a_ml x_l^a and e_a(y) = sum_b E_ab y^b,
+// where E = G for the general form (eq. PolyRHS) and E_ab = c_{a+b} binom(a+b, a)
+// (-1)^b for the difference form (eq. PolyDifferenceRHSfast, its sum over a
+// regrouped by the power of the moment).  The CIA splits T_a(m) as in steps
+// E1 + E2: the community moment W_ca = sum_{l in c} x_l^a (eq. PolyMoments,
+// without the 1/N), minus the diagonal x_m^a (a_mm = 0), minus the power sums
+// over the missing links, plus those over the inter-community links.  Every
+// link therefore costs p - 1 multiplications and p additions in FP64 (one
+// addition for Desai-Zwanzig), not an evaluation of g.
+//
+// FP64 additions are scarce on this GPU (a few per clock and SM), so the
+// missing-link sums, the bulk of the work, are exact integer sums: the tile's
+// window holds each power of the community's states as a 64-bit fixed-point
+// number, u^a = M 2^E_a with |M| < 2^55 and E_a set by the community's largest
+// |u^a|, so that a chunk of at most 64 links sums without overflow.  The
+// rounding to the grid 2^E_a (at most 2^-56 of the largest value) is below the
+// rounding error of an FP64 sum of the same values.
 //
 // One CTA (256 threads) per tile and launch: (0) the community's moments from
-// the previous launch's tile sums and its states in shared memory, (A) the
-// sparse sums over the tile's sliced-ELL blob (missing links from shared
-// memory), (B) one thread per node: dense term, RK4 stage update and the
-// tile's sums of the powers of the next stage state.  The direct method's
-// kernel has the same epilogue, so either method leaves valid moments.
+// the previous launch's tile sums and the powers of its states in shared
+// memory, (A) the sparse power sums over the tile's sliced-ELL blob,
+// (B) one thread per node: T_a, the coupling, RK4 stage update and the tile's
+// sums of the powers of the next stage state.  The direct method's kernel
+// evaluates g link by link and has the same epilogue, so either method leaves
+// valid moments.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,68 +53,43 @@ enum PolyMode { kRhs = 0, kStage = 1, kFinal = 2 };
 
 struct PolyParams {
     int64_t n;
-    int p;                       // degree of h
-    double c[kMaxP + 1];         // h
-    double v[kMaxP + 1];         // V'
-    double g[kMaxP + 1][kMaxP + 1];  // general form: G_ab, zero above degree p
+    double c[kMaxP + 1];             // difference form: h, zero above degree p
+    double e[kMaxP + 1][kMaxP + 1];  // E_ab (both forms), zero above degree p
+    double v[kMaxP + 1];             // V'
     double k_over_n;
-    int group;                   // threads per row of the direct kernel
-    int win_cap;                 // shared-memory window capacity (nodes); 0 = read the
-                                 // community's states from global memory
+    int group;                       // threads per row of the direct kernel
+    int win_cap;                     // shared-memory window capacity (nodes); 0 = read the
+                                     // community's states from global memory
     const TileDesc *tile_desc;
     const unsigned char *blob;
     const int32_t *comm_tile_begin;
     const int64_t *full_rowptr;
     const int32_t *full_col;
-    const double *y_in;          // [n] stage state (permuted)
-    double *y_out;               // [n] next stage state
-    const double *part_in;       // [tiles][p+1] sums of y_in^k
-    double *part_out;            // [tiles][p+1] sums of y_out^k
-    double *acc, *theta;         // RK4 accumulator, FP64 master
+    const double *y_in;              // [n] stage state (permuted)
+    double *y_out;                   // [n] next stage state
+    const double *part_in;           // [tiles][P+1] sums of y_in^a
+    double *part_out;                // [tiles][P+1] sums of y_out^a
+    double *acc, *theta;             // RK4 accumulator, FP64 master
     const int32_t *perm;
-    double *rhs_out;             // kRhs: original order
+    double *rhs_out;                 // kRhs: original order
     double c_next_dt, b_s, dt;
     int first_stage;
 };
 
-__device__ __forceinline__ double horner(const double *c, int p, double x) {
-    double s = 0.0;
-    for (int a = p; a >= 0; --a) s = fma(s, x, c[a]);
+template <int P>
+__device__ __forceinline__ double horner(const double *c, double x) {
+    double s = c[P];
+#pragma unroll
+    for (int a = P - 1; a >= 0; --a) s = fma(s, x, c[a]);
     return s;
 }
 
-// The coupling of one node y against its neighbours u: h(u - y) (difference
-// form) or g(u, y) = sum_a e_a(y) u^a (general form, e_a precomputed per node).
-// Coefficients above degree p are zero, so the full-degree Horner chain gives
-// the degree-p value exactly.
-template <bool GEN>
-struct Coupling {
-    double e[kMaxP + 1];
-    double y;
-    __device__ __forceinline__ Coupling(const PolyParams &a, double y_) : y(y_) {
-        if (GEN) {
+// e_a(y) = sum_b E_ab y^b, a = 0..P.
+template <int P>
+__device__ __forceinline__ void coefficients(const PolyParams &a, double y, double (&e)[P + 1]) {
 #pragma unroll
-            for (int al = 0; al <= kMaxP; ++al) {
-                double s = 0.0;
-#pragma unroll
-                for (int b = kMaxP; b >= 0; --b) s = fma(s, y_, a.g[al][b]);
-                e[al] = s;
-            }
-        }
-    }
-    __device__ __forceinline__ double operator()(const PolyParams &a, double u) const {
-        double s = 0.0;
-        if (GEN) {
-#pragma unroll
-            for (int al = kMaxP; al >= 0; --al) s = fma(s, u, e[al]);
-        } else {
-            const double d = u - y;
-#pragma unroll
-            for (int al = kMaxP; al >= 0; --al) s = fma(s, d, a.c[al]);
-        }
-        return s;
-    }
-};
+    for (int al = 0; al <= P; ++al) e[al] = horner<P>(a.e[al], y);
+}
 
 // RK4 stage update from the derivative k; returns the next stage state.
 template <int MODE>
@@ -124,96 +111,157 @@ __device__ __forceinline__ double rk4_update(const PolyParams &a, int64_t m, dou
     return y;
 }
 
-// Sums over the tile of y^k, k = 0..p (each thread contributes its node's
+// Sums over the tile of y^a, a = 0..P (each thread contributes its node's
 // value, nothing when it has no node), in a fixed order, to part_out[tile].
-__device__ __forceinline__ void tile_power_sums(int p, double *part_out, int tile, bool live, double y,
+template <int P>
+__device__ __forceinline__ void tile_power_sums(double *part_out, int tile, bool live, double y,
                                                 double (*red)[kMaxP + 1]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double pw[kMaxP + 1];
+    double pw[P + 1];
     double q = 1.0;
 #pragma unroll
-    for (int k = 0; k <= kMaxP; ++k) {
+    for (int k = 0; k <= P; ++k) {
         pw[k] = live ? q : 0.0;
         q *= y;
     }
 #pragma unroll
-    for (int k = 0; k <= kMaxP; ++k)
+    for (int k = 0; k <= P; ++k)
         for (int o = 16; o > 0; o >>= 1) pw[k] += __shfl_xor_sync(0xffffffffu, pw[k], o);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k <= kMaxP; ++k) red[warp][k] = pw[k];
+        for (int k = 0; k <= P; ++k) red[warp][k] = pw[k];
     __syncthreads();
-    if (threadIdx.x <= p) {
+    if (threadIdx.x <= P) {
         double s = 0.0;
         for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-        part_out[(int64_t)tile * (p + 1) + threadIdx.x] = s;
+        part_out[(int64_t)tile * (P + 1) + threadIdx.x] = s;
     }
 }
 
-// Dense term of node state x: the community sum of the coupling from the
-// moments W, without the diagonal term (h(0) = c_0, or g(x, x)).
-template <bool GEN>
-__device__ __forceinline__ double dense_from_moments(const PolyParams &a, const double *W, double x) {
-    if (GEN) {
-        const Coupling<true> cx(a, x);
-        double dense = 0.0;
+// The tile's sums of y^a, a = 0..P, through shared memory: every thread
+// stores its powers in scratch ([P+1][kThreads] doubles, free at this point),
+// then warp a adds row a in a fixed order.  Fewer FP64 additions than a
+// shuffle tree in every warp.
+template <int P>
+__device__ __forceinline__ void tile_power_sums_smem(double *part_out, int tile, bool live, double y,
+                                                     double *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();   // scratch was read before
+    double q = 1.0;
 #pragma unroll
-        for (int al = 0; al <= kMaxP; ++al)
-            if (al <= a.p) dense = fma(W[al], cx.e[al], dense);
-        return dense - cx(a, x);
+    for (int k = 0; k <= P; ++k) {
+        scratch[k * kThreads + threadIdx.x] = live ? q : 0.0;
+        q *= y;
     }
-    double dense = 0.0;
-    for (int al = 0; al <= a.p; ++al) {
-        double inner = 0.0, binom = 1.0, negx = 1.0;
-        // sum_{k=0..al} binom(al, k) W_k (-x)^{al-k}, accumulated from k = al down
-        for (int k = al; k >= 0; --k) {
-            inner = fma(binom * W[k], negx, inner);
-            negx *= -x;
-            binom = binom * (double)k / (double)(al - k + 1);
-        }
-        dense = fma(a.c[al], inner, dense);
+    __syncthreads();
+    if (warp <= P) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < kThreads / 32; ++j) s += scratch[warp * kThreads + j * 32 + lane];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) part_out[(int64_t)tile * (P + 1) + warp] = s;
     }
-    return dense - a.c[0];
 }
 
-template <int MODE, bool GEN>
+// Round u 2^sh to the nearest integer (ties away from zero) with integer
+// operations only; the caller picks sh so that |u| 2^sh < 2^55.
+__device__ __forceinline__ long long to_fixed(double u, int sh) {
+    const long long bits = __double_as_longlong(u);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const long long mant = (bits & 0xfffffffffffffLL) | (e ? (1LL << 52) : 0LL);
+    const int k = min((e ? e : 1) - 1075 + sh, 2);   // u 2^sh = mant 2^k
+    long long m;
+    if (k >= 0) m = mant << k;
+    else if (k < -62) m = 0;
+    else m = (mant + (1LL << (-k - 1))) >> (-k);
+    return bits < 0 ? -m : m;
+}
+
+// Adds u^1..u^P to s[0..P-1].
+template <int P>
+__device__ __forceinline__ void add_powers(double (&s)[P], double u) {
+    double q = u;
+#pragma unroll
+    for (int al = 0; al < P; ++al) {
+        s[al] += q;
+        if (al + 1 < P) q *= u;
+    }
+}
+
+template <int MODE, int P>
 __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double yrow[kTileMax];
     __shared__ double W[kMaxP + 1];
     __shared__ double red[kWarps][kMaxP + 1];
-    double *win = reinterpret_cast<double *>(smem_raw);            // [win_cap] community states
-    double *sWm = win + a.win_cap;                                  // [kMaxChunks] missing-chunk sums
-    double *sWi = sWm + kMaxChunks;                                 // [kTileMax] inter sums per row
-    uint16_t *chunk_row = reinterpret_cast<uint16_t *>(sWi + kTileMax);
+    double *win = reinterpret_cast<double *>(smem_raw);        // [P][win_cap] powers of the community's states
+    static_assert(P * kMaxChunks >= (P + 1) * kThreads, "the tile sums reuse the chunk table");
+    double *sWm = win + (size_t)P * a.win_cap;                  // [P][kMaxChunks] missing-chunk power sums
+    double *sWi = sWm + P * kMaxChunks;                         // [P][kTileMax] inter power sums per row
+    int *smc = reinterpret_cast<int *>(sWi + P * kTileMax);     // [kMaxChunks] missing links per chunk
+    int *sic = smc + kMaxChunks;                                // [kTileMax] inter links per row
     const int t = blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const bool comm = d.comm >= 0;
     const int lam = comm ? (int)d.lam : 0;
-    const int count = d.count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned char *b = a.blob + d.blob_off;
-    const uint32_t *vtab = reinterpret_cast<const uint32_t *>(b + d.vtab_off);
-    const double *cw = a.win_cap ? win : a.y_in + d.lo;
-    // (0) window, own rows, moments (FP64 over the community's tiles), chunk table
-    if (a.win_cap)
-        for (int i = threadIdx.x; i < lam; i += kThreads) win[i] = a.y_in[d.lo + i];
-    if (threadIdx.x < count) {
-        yrow[threadIdx.x] = a.y_in[d.first + threadIdx.x];
-        const uint32_t vt = __ldg(vtab + threadIdx.x);
-        for (uint32_t c = vt & 0xffffu; c < (vt & 0xffffu) + (vt >> 16); ++c) chunk_row[c] = (uint16_t)threadIdx.x;
+    const int cap = a.win_cap;
+    const double *cy = a.y_in + d.lo;
+    long long *wfix = reinterpret_cast<long long *>(win);   // the window after conversion
+    double unit[P];                                          // 2^E_a
+    // (0) window of powers and their largest magnitudes, moments (FP64 over
+    // the community's tiles)
+    if (cap) {
+        // largest |u^a| as the integer order of the magnitude's bits
+        unsigned long long mx[P];
+#pragma unroll
+        for (int al = 0; al < P; ++al) mx[al] = 0ull;
+        for (int i = threadIdx.x; i < lam; i += kThreads) {
+            const double u = cy[i];
+            double q = u;
+#pragma unroll
+            for (int al = 0; al < P; ++al) {
+                win[al * cap + i] = q;
+                mx[al] = max(mx[al], (unsigned long long)__double_as_longlong(q) & 0x7fffffffffffffffull);
+                if (al + 1 < P) q *= u;
+            }
+        }
+#pragma unroll
+        for (int al = 0; al < P; ++al) {
+            for (int o = 16; o > 0; o >>= 1) mx[al] = max(mx[al], __shfl_xor_sync(0xffffffffu, mx[al], o));
+            if (lane == 0) red[warp][al] = __longlong_as_double((long long)mx[al]);
+        }
     }
     if (comm && warp == 0) {
         const int u0 = a.comm_tile_begin[d.comm], u1 = a.comm_tile_begin[d.comm + 1];
-        for (int k = 0; k <= a.p; ++k) {
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
             double s = 0.0;
-            for (int u = u0 + lane; u < u1; u += 32) s += a.part_in[(int64_t)u * (a.p + 1) + k];
+            for (int u = u0 + lane; u < u1; u += 32) s += a.part_in[(int64_t)u * (P + 1) + k];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) W[k] = s;
         }
     }
     __syncthreads();
-    // (A) sparse sums: warp per slice, lane per missing chunk and inter row
+    if (cap) {
+        // E_a from the community's largest |u^a| (the same in every thread),
+        // then each thread converts the entries it wrote
+        int sh[P];
+#pragma unroll
+        for (int al = 0; al < P; ++al) {
+            unsigned long long m = 0ull;
+            for (int w = 0; w < kWarps; ++w) m = max(m, (unsigned long long)__double_as_longlong(red[w][al]));
+            const int em = (int)(m >> 52);
+            const int ex = (em ? em : 1) - 1022;   // largest |u^a| < 2^ex
+            sh[al] = min(55 - ex, 1000);           // |u^a| 2^sh < 2^55
+            unit[al] = ldexp(1.0, -sh[al]);
+        }
+        for (int i = threadIdx.x; i < lam; i += kThreads)
+#pragma unroll
+            for (int al = 0; al < P; ++al) wfix[al * cap + i] = to_fixed(win[al * cap + i], sh[al]);
+        __syncthreads();
+    }
+    // (A) sparse power sums: warp per slice, lane per missing chunk and inter row
     const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
     const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
     const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
@@ -222,58 +270,103 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
         const uint4 sd = __ldg(sdesc + s);
         const uint32_t rows = __ldg(srows + s * 32 + lane);
         const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
-        double ms = 0.0, is = 0.0;
-        {
-            const Coupling<GEN> cp(a, yrow[mrow != 0xffffu ? chunk_row[mrow] : 0]);
-            const uint4 *mv = mvec + sd.x + lane;
-            for (uint32_t j = 0; j < sd.y; ++j) {
-                const uint4 q = __ldg(mv + 32 * j);
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        double ms[P], is[P];
+        long long mfix[P];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int l0 = (int)(w4[e] & 0xffffu), l1 = (int)(w4[e] >> 16);
-                    if (l0 < lam) ms += cp(a, cw[l0]);
-                    if (l1 < lam) ms += cp(a, cw[l1]);
+        for (int al = 0; al < P; ++al) {
+            ms[al] = is[al] = 0.0;
+            mfix[al] = 0;
+        }
+        int mc = 0, ic = 0;
+        const uint4 *mv = mvec + sd.x + lane;
+        for (uint32_t j = 0; j < sd.y; ++j) {
+            const uint4 q = __ldg(mv + 32 * j);
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int l = (int)(h ? w4[e] >> 16 : w4[e] & 0xffffu);
+                    if (l < lam) {
+                        ++mc;
+                        if (cap) {
+#pragma unroll
+                            for (int al = 0; al < P; ++al) mfix[al] += wfix[al * cap + l];
+                        } else {
+                            add_powers<P>(ms, cy[l]);
+                        }
+                    }
                 }
             }
         }
-        {
-            const Coupling<GEN> cp(a, yrow[irow != 0xffffu ? irow : 0]);
-            const int4 *iv = ivec + sd.z + lane;
-            for (uint32_t j = 0; j < sd.w; ++j) {
-                const int4 q = __ldg(iv + 32 * j);
-                const int l4[4] = {q.x, q.y, q.z, q.w};
+        const int4 *iv = ivec + sd.z + lane;
+        for (uint32_t j = 0; j < sd.w; ++j) {
+            const int4 q = __ldg(iv + 32 * j);
+            const int l4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (l4[e] < a.n) is += cp(a, __ldg(a.y_in + l4[e]));
-            }
+            for (int e = 0; e < 4; ++e)
+                if (l4[e] < a.n) {
+                    ++ic;
+                    add_powers<P>(is, __ldg(a.y_in + l4[e]));
+                }
         }
-        if (mrow != 0xffffu) sWm[mrow] = ms;
-        if (irow != 0xffffu) sWi[irow] = is;
+        if (mrow != 0xffffu) {
+#pragma unroll
+            for (int al = 0; al < P; ++al)
+                sWm[al * kMaxChunks + mrow] = cap ? (double)mfix[al] * unit[al] : ms[al];
+            smc[mrow] = mc;
+        }
+        if (irow != 0xffffu) {
+#pragma unroll
+            for (int al = 0; al < P; ++al) sWi[al * kTileMax + irow] = is[al];
+            sic[irow] = ic;
+        }
     }
     __syncthreads();
-    // (B) thread per node
-    const bool live = threadIdx.x < count;
+    // (B) thread per node: T_a = W_a - x^a - missing + inter, then sum_a T_a e_a(x)
+    const bool live = threadIdx.x < d.count;
     double ynext = 0.0;
     if (live) {
         const int r = threadIdx.x;
         const int64_t m = d.first + r;
-        const double x = yrow[r];
-        double sparse = sWi[r];
-        const uint32_t vt = __ldg(vtab + r);
-        for (uint32_t c = vt & 0xffffu; c < (vt & 0xffffu) + (vt >> 16); ++c) sparse -= sWm[c];
-        const double dense = comm ? dense_from_moments<GEN>(a, W, x) : 0.0;
-        const double k = -horner(a.v, kMaxP, x) + a.k_over_n * (dense + sparse);
+        const double x = a.y_in[m];
+        double T[P + 1];
+        int deg = sic[r];
+#pragma unroll
+        for (int al = 0; al < P; ++al) T[al + 1] = sWi[al * kTileMax + r];
+        const uint32_t vt = __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r);
+        for (uint32_t c = vt & 0xffffu; c < (vt & 0xffffu) + (vt >> 16); ++c) {
+            deg -= smc[c];
+#pragma unroll
+            for (int al = 0; al < P; ++al) T[al + 1] -= sWm[al * kMaxChunks + c];
+        }
+        T[0] = (double)deg;
+        if (comm) {
+            T[0] += W[0] - 1.0;
+            double q = x;
+#pragma unroll
+            for (int al = 1; al <= P; ++al) {
+                T[al] += W[al] - q;
+                q *= x;
+            }
+        }
+        double e[P + 1];
+        coefficients<P>(a, x, e);
+        double coup = 0.0;
+#pragma unroll
+        for (int al = 0; al <= P; ++al) coup = fma(T[al], e[al], coup);
+        const double k = -horner<kMaxP>(a.v, x) + a.k_over_n * coup;
         ynext = rk4_update<MODE>(a, m, k);
     }
     if (MODE == kRhs) return;
-    tile_power_sums(a.p, a.part_out, t, live, ynext, red);
+    tile_power_sums_smem<P>(a.part_out, t, live, ynext, sWm);
 }
 
-// Direct method, one CTA per tile: `group` threads per row sum h(x_l - x_m)
-// over the row's CSR neighbours (rows padded to 4-entry vectors with the
-// sentinel n), then the same update and power sums as the CIA.
-template <int MODE, bool GEN>
+// Direct method, one CTA per tile: `group` threads per row evaluate the
+// coupling link by link over the row's CSR neighbours (rows padded to 4-entry
+// vectors with the sentinel n): h(x_l - x_m), or g(x_l, x_m) = sum_a e_a(x_m)
+// x_l^a; then the same update and power sums as the CIA.
+template <int MODE, bool GEN, int P>
 __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams a) {
     __shared__ double sW[kTileMax];
     __shared__ double red[kWarps][kMaxP + 1];
@@ -284,14 +377,19 @@ __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams 
     const int4 *col4 = reinterpret_cast<const int4 *>(a.full_col);
     for (int r = grp; r < d.count; r += ngrp) {
         const int64_t m = d.first + r;
-        const Coupling<GEN> cp(a, a.y_in[m]);
+        const double y = a.y_in[m];
+        double e[P + 1];
+        if (GEN) coefficients<P>(a, y, e);
         double s = 0.0;
         for (int64_t v = a.full_rowptr[m] / 4 + gl; v < a.full_rowptr[m + 1] / 4; v += G) {
             const int4 q = __ldg(col4 + v);
             const int l4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (l4[e] < a.n) s += cp(a, __ldg(a.y_in + l4[e]));
+            for (int k = 0; k < 4; ++k)
+                if (l4[k] < a.n) {
+                    const double u = __ldg(a.y_in + l4[k]);
+                    s += GEN ? horner<P>(e, u) : horner<P>(a.c, u - y);
+                }
         }
         for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (gl == 0) sW[r] = s;
@@ -302,15 +400,16 @@ __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams 
     if (live) {
         const int64_t m = d.first + threadIdx.x;
         const double x = a.y_in[m];
-        const double k = -horner(a.v, kMaxP, x) + a.k_over_n * sW[threadIdx.x];
+        const double k = -horner<kMaxP>(a.v, x) + a.k_over_n * sW[threadIdx.x];
         ynext = rk4_update<MODE>(a, m, k);
     }
     if (MODE == kRhs) return;
-    tile_power_sums(a.p, a.part_out, t, live, ynext, red);
+    tile_power_sums<P>(a.part_out, t, live, ynext, red);
 }
 
 // State load: x (original order) -> master (optional) and stage state,
 // with the tile sums of its powers.  One CTA per tile.
+template <int P>
 __global__ void __launch_bounds__(kThreads) poly_load_kernel(const PolyParams a, const double *x, double *master) {
     __shared__ double red[kWarps][kMaxP + 1];
     const int t = blockIdx.x;
@@ -323,30 +422,45 @@ __global__ void __launch_bounds__(kThreads) poly_load_kernel(const PolyParams a,
         if (master) master[m] = y;
         a.y_out[m] = y;
     }
-    tile_power_sums(a.p, a.part_out, t, live, y, red);
+    tile_power_sums<P>(a.part_out, t, live, y, red);
 }
 
 size_t window_cap(const cia_plan *pl) { return (size_t)((pl->max_comm + 1) & ~(int64_t)1); }
-constexpr size_t kTables = kMaxChunks * 8 + kTileMax * 8 + kMaxChunks * 2;
 
-// The largest community fits the shared-memory window (the kernel's static
-// shared memory is under 4 KB).
+size_t tables_bytes(int P) { return (size_t)P * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
+
+// The powers of the largest community's states fit the shared-memory window
+// (the kernel's static shared memory is under 4 KB).
 bool window_fits(const cia_plan *pl) {
-    return window_cap(pl) * 8 + kTables + 4096 <= (size_t)pl->smem_optin;
+    const int P = pl->poly_p;
+    return window_cap(pl) * 8 * P + tables_bytes(P) + 4096 <= (size_t)pl->smem_optin;
 }
 
-size_t stage_smem(const cia_plan *pl) { return (pl->staging == 2 ? window_cap(pl) * 8 : 0) + kTables; }
+size_t stage_smem(const cia_plan *pl) {
+    const int P = pl->poly_p;
+    return (pl->staging == 2 ? window_cap(pl) * 8 * P : 0) + tables_bytes(P);
+}
 
 PolyParams base_params(const cia_plan *pl, int slot) {
     PolyParams a{};
     const auto &d = pl->d;
+    constexpr int S = kMaxP + 1;
     a.n = pl->n;
-    a.p = pl->poly_p;
-    for (int k = 0; k <= kMaxP; ++k) {
-        a.c[k] = k <= pl->poly_p ? pl->poly_c[k] : 0.0;
+    for (int k = 0; k < S; ++k) {
+        a.c[k] = pl->poly_c[k];
         a.v[k] = pl->poly_dv[k];
-        for (int b = 0; b <= kMaxP; ++b) a.g[k][b] = pl->poly_g[k * (kMaxP + 1) + b];
     }
+    // E_ab: G itself, or the regrouped binomial expansion of h
+    for (int al = 0; al < S; ++al)
+        for (int b = 0; b < S; ++b) {
+            if (pl->poly_general) {
+                a.e[al][b] = pl->poly_g[al * S + b];
+            } else if (al + b < S) {
+                double binom = 1.0;   // binom(al + b, al)
+                for (int j = 1; j <= al; ++j) binom = binom * (double)(b + j) / (double)j;
+                a.e[al][b] = pl->poly_c[al + b] * binom * ((b & 1) ? -1.0 : 1.0);
+            }
+        }
     a.k_over_n = pl->K / (double)pl->n;
     a.group = pl->group_size_direct;
     a.win_cap = pl->staging == 2 ? (int)window_cap(pl) : 0;
@@ -359,12 +473,11 @@ PolyParams base_params(const cia_plan *pl, int slot) {
     a.y_out = d.pl_y[slot ^ 1];
     a.part_in = d.pl_part[slot];
     a.part_out = d.pl_part[slot ^ 1];
-    a.acc = d.theta == nullptr ? nullptr : static_cast<double *>(d.acc);
+    a.acc = static_cast<double *>(d.acc);
     a.theta = d.theta;
     a.perm = d.perm;
     return a;
 }
-
 
 // One launch of `kernel`, one tile per CTA; ID tells the instantiations apart
 // so that each kernel keeps its own configured shared-memory limit.
@@ -381,16 +494,23 @@ cudaError_t launch(void (*kernel)(PolyParams), const cia_plan *pl, size_t smem, 
     return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_tiles), dim3(kThreads), args, smem, s);
 }
 
-template <int MODE, bool GEN>
-cudaError_t launch_form(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
-    constexpr int id = 2 * MODE + (GEN ? 1 : 0);
-    if (method == Method::DIRECT) return launch<id + 6>(poly_direct_kernel<MODE, GEN>, pl, 0, a, s);
-    return launch<id>(poly_stage_kernel<MODE, GEN>, pl, stage_smem(pl), a, s);
+template <int MODE, int P>
+cudaError_t launch_degree(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
+    constexpr int id = 3 * (P - 1) + MODE;   // stage kernels 0..11, direct kernels 12..35
+    if (method == Method::DIRECT)
+        return pl->poly_general ? launch<12 + 2 * id>(poly_direct_kernel<MODE, true, P>, pl, 0, a, s)
+                                : launch<13 + 2 * id>(poly_direct_kernel<MODE, false, P>, pl, 0, a, s);
+    return launch<id>(poly_stage_kernel<MODE, P>, pl, stage_smem(pl), a, s);
 }
 
 template <int MODE>
 cudaError_t launch_mode(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
-    return pl->poly_general ? launch_form<MODE, true>(pl, method, a, s) : launch_form<MODE, false>(pl, method, a, s);
+    switch (pl->poly_p) {
+        case 1: return launch_degree<MODE, 1>(pl, method, a, s);
+        case 2: return launch_degree<MODE, 2>(pl, method, a, s);
+        case 3: return launch_degree<MODE, 3>(pl, method, a, s);
+        default: return launch_degree<MODE, 4>(pl, method, a, s);
+    }
 }
 
 }  // namespace
@@ -400,7 +520,14 @@ bool poly_window_fits(const cia_plan *pl) { return window_fits(pl); }
 cudaError_t poly_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
     // the load writes the state and its power sums into slot `slot`
     PolyParams a = base_params(pl, slot ^ 1);
-    poly_load_kernel<<<(unsigned)pl->n_tiles, kThreads, 0, s>>>(a, x, write_master ? pl->d.theta : nullptr);
+    double *master = write_master ? pl->d.theta : nullptr;
+    const unsigned grid = (unsigned)pl->n_tiles;
+    switch (pl->poly_p) {
+        case 1: poly_load_kernel<1><<<grid, kThreads, 0, s>>>(a, x, master); break;
+        case 2: poly_load_kernel<2><<<grid, kThreads, 0, s>>>(a, x, master); break;
+        case 3: poly_load_kernel<3><<<grid, kThreads, 0, s>>>(a, x, master); break;
+        default: poly_load_kernel<4><<<grid, kThreads, 0, s>>>(a, x, master); break;
+    }
     return cudaGetLastError();
 }
 

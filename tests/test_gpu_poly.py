@@ -126,6 +126,27 @@ def test_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
             assert coupling_rel_err(got, ref, pot) < FP64_TOL, method
 
 
+@pytest.mark.parametrize("staging", ["auto", "plain"])
+def test_rhs_wide_dynamic_range_and_zero_communities(cia, oracle_mod, torch_mod, staging):
+    """States spanning eight decades inside one community (the shared-memory
+    window holds fixed-point powers scaled by the community's largest one),
+    and a community whose states are all zero."""
+    g = S.sbm_graph([300, 129, 64], 0.9, inter_degree=6.0, seed=17, n_free=20)
+    rng = np.random.default_rng(12)
+    x = rng.choice([-1.0, 1.0], g.n) * 10.0 ** rng.uniform(-6, 2, g.n)
+    x[g.labels == 2] = 0.0
+    c, dv = (0.3, -1.0, 0.2, 0.01), (0.0, 1.0)
+    plan = make_plan(cia, g, 1.0, c, dv, staging=staging)
+    ref = oracle_mod.poly_direct(g.rowptr, g.col, x, 1.0, c, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert coupling_err(oracle_mod, g, x, got, ref, c, dv) < FP64_TOL, method
+    G = rng.normal(size=(4, 4))
+    gplan = make_general(cia, g, 1.0, G, dv, staging=staging)
+    gref = oracle_mod.polyg_direct(g.rowptr, g.col, x, 1.0, G, dv)
+    assert general_err(oracle_mod, g, x, gpu_rhs(torch_mod, gplan, x, "cia"), gref, G, dv) < FP64_TOL
+
+
 def test_rhs_matches_oracle_cia_permuted(cia, oracle_mod, torch_mod):
     """The oracle's own moment formula (permuted order) agrees with the device
     CIA too: the same E1/E2 split, evaluated independently."""
