@@ -74,6 +74,9 @@ def _load():
         lib.ora_polyg_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P]
         lib.ora_polyg_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
                                       P, P]
+        lib.ora_polyw_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P, P, P]
+        lib.ora_polyw_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
+                                      P, P, P, P]
         _lib = lib
     return _lib
 
@@ -344,6 +347,37 @@ def polyg_cia(sp: Split, x_perm, K, G, dv) -> np.ndarray:
     out = np.empty_like(x)
     lib.ora_polyg_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
                       float(K), G.shape[0] - 1, _p(G), len(dv) - 1, _p(dv), _p(w), _p(out))
+    return out
+
+
+def polyw_direct(rowptr, col, x, K, G, dv, alpha, beta) -> np.ndarray:
+    """Rank-one weighted links (eq. rank1system on a graph): x' = -V'(x_m) +
+    (K/N) sum_l a_ml alpha_m beta_l g(x_l, x_m), g as in polyg_direct."""
+    lib = _load()
+    x = _f64(x)
+    G, dv = _square(G), _f64(dv)
+    alpha, beta = _f64(alpha), _f64(beta)
+    if len(alpha) != len(x) or len(beta) != len(x):
+        raise ValueError("alpha and beta need n entries")
+    out = np.empty_like(x)
+    lib.ora_polyw_direct(len(x), _p(_i64(rowptr)), _p(_i32(col)), _p(x), float(K), G.shape[0] - 1,
+                         _p(G), len(dv) - 1, _p(dv), _p(alpha), _p(beta), _p(out))
+    return out
+
+
+def polyw_cia(sp: Split, x_perm, K, G, dv, alpha_perm, beta_perm) -> np.ndarray:
+    """The same by the CIA: weighted moments r_a = (1/N) sum_{l in c} beta_l x_l^a
+    (eq. rank1precompute), dense term alpha_m sum G[a, b] r_a x_m^b (eq. rank1fast),
+    the sparse sum over S with the link weights (permuted order)."""
+    lib = _load()
+    x = _f64(x_perm)
+    G, dv = _square(G), _f64(dv)
+    alpha, beta = _f64(alpha_perm), _f64(beta_perm)
+    w = np.zeros(max(1, sp.M * G.shape[0]))
+    out = np.empty_like(x)
+    lib.ora_polyw_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
+                      float(K), G.shape[0] - 1, _p(G), len(dv) - 1, _p(dv), _p(alpha), _p(beta), _p(w),
+                      _p(out))
     return out
 
 

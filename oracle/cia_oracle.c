@@ -441,3 +441,66 @@ void ora_polyg_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_ro
         out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Rank-one weighted couplings (Sec. "Rank One Coupling", eq. rank1system,
+ * eq. rank1precompute, eq. rank1fast) on a graph: the weights of the links
+ * factor as a_ml alpha_m beta_l,
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml alpha_m beta_l g(x_l, x_m),
+ * with the general polynomial g of eq. PolyApprox (G as above). */
+void ora_polyw_direct(int64_t n, const int64_t *rowptr, const int32_t *col, const double *x, double K,
+                      int p, const double *G, int q, const double *dv, const double *alpha,
+                      const double *beta, double *out) {
+    const double scale = K / (double)n;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int64_t e = rowptr[m]; e < rowptr[m + 1]; ++e)
+            acc += alpha[m] * beta[col[e]] * poly2_eval(G, p, x[col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + scale * acc;
+    }
+}
+
+/* CIA RHS (permuted state and weights, S with its diagonal -1 entries):
+ * (E1.1) r[c][a] = (1/N) sum_{l in c} beta_l x_l^a, a = 0..p   (eq. rank1precompute,
+ *        one weighted moment per power as in eq. PolyMoments)
+ * (E1.2) dense_m = alpha_m sum_a sum_b G[a][b] r[c][a] x_m^b     (eq. rank1fast with eq. PolyRHS)
+ * (E2)   sparse_m = (1/N) sum_l s_ml alpha_m beta_l g(x_l, x_m)
+ *        out_m = -V'(x_m) + K (dense_m + sparse_m).
+ * w: caller scratch of M * (p + 1) doubles. */
+void ora_polyw_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_rowptr, const int32_t *s_col,
+                   const int8_t *s_val, const double *x, double K, int p, const double *G, int q,
+                   const double *dv, const double *alpha, const double *beta, double *w, double *out) {
+    const double invN = 1.0 / (double)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t cc = 0; cc < M; ++cc) {
+        for (int a = 0; a <= p; ++a) {
+            double s = 0.0;
+            for (int64_t l = off[cc]; l < off[cc + 1]; ++l) s += beta[l] * pow(x[l], (double)a);
+            w[cc * (p + 1) + a] = invN * s;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        int64_t cc = -1;
+        if (m < off[M]) {
+            int64_t lo = 0, hi = M;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) / 2;
+                if (off[mid] <= m) lo = mid;
+                else hi = mid;
+            }
+            cc = lo;
+        }
+        double dense = 0.0;
+        if (cc >= 0)
+            for (int a = 0; a <= p; ++a)
+                for (int b = 0; b <= p; ++b)
+                    dense += G[a * (p + 1) + b] * w[cc * (p + 1) + a] * pow(x[m], (double)b);
+        dense *= alpha[m];
+        double sparse = 0.0;
+        for (int64_t e = s_rowptr[m]; e < s_rowptr[m + 1]; ++e)
+            sparse += (double)s_val[e] * alpha[m] * beta[s_col[e]] * poly2_eval(G, p, x[s_col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
+    }
+}

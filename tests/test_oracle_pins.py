@@ -504,3 +504,54 @@ def test_general_polynomial_cia_equals_direct(oracle_mod, seed):
     sp = oracle_mod.split(g.rowptr, g.col, g.labels)
     got = oracle_mod.polyg_cia(sp, x[sp.perm], 1.3, G, dv)[sp.iperm]
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------ rank-one weighted links
+
+def test_rank_one_weights_brute_force_dense_matrix(oracle_mod):
+    """A 40-node graph as a dense 0/1 matrix: sum over l of A_ml alpha_m beta_l
+    g(x_l, x_m) by numpy broadcasting, independent of the oracle's loops."""
+    import synthetic as S
+    g = S.random_labels_graph(40, 0.3, 3, seed=9, free_frac=0.2)
+    A = np.zeros((g.n, g.n))
+    for m in range(g.n):
+        A[m, g.col[g.rowptr[m]:g.rowptr[m + 1]]] = 1.0
+    rng = np.random.default_rng(21)
+    x, al, be = rng.normal(size=g.n), rng.uniform(0.2, 2, g.n), rng.normal(size=g.n)
+    G = rng.normal(size=(3, 3))
+    U, Y = x[None, :], x[:, None]                  # U[m, l] = x_l, Y[m, l] = x_m
+    gmat = sum(G[a, b] * U ** a * Y ** b for a in range(3) for b in range(3))
+    want = -(0.5 * x ** 3) + 1.3 / g.n * (al[:, None] * A * be[None, :] * gmat).sum(1)
+    got = oracle_mod.polyw_direct(g.rowptr, g.col, x, 1.3, G, [0, 0, 0, 0.5], al, be)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14)
+
+
+def test_rank_one_linear_neighbour_term_is_a_weighted_matvec(oracle_mod):
+    """g(u, y) = u: x' = (K/N) diag(alpha) A diag(beta) x (scipy CSR products)."""
+    sp_mod = pytest.importorskip("scipy.sparse")
+    import synthetic as S
+    g = S.random_labels_graph(70, 0.2, 4, seed=10, free_frac=0.1)
+    A = sp_mod.csr_matrix((np.ones(len(g.col)), g.col, g.rowptr), shape=(g.n, g.n))
+    rng = np.random.default_rng(22)
+    x, al, be = rng.normal(size=g.n), rng.normal(size=g.n), rng.normal(size=g.n)
+    G = np.zeros((2, 2))
+    G[1, 0] = 1.0
+    got = oracle_mod.polyw_direct(g.rowptr, g.col, x, 0.8, G, [0.0], al, be)
+    want = (0.8 / g.n) * al * (A @ (be * x))
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_rank_one_cia_equals_direct(oracle_mod, seed):
+    """Weighted moments (eq. rank1precompute) with alpha_m scaling (eq. rank1fast)
+    plus the weighted sparse corrections reach the direct sum."""
+    import synthetic as S
+    g = S.random_labels_graph(50, 0.35, 3, seed=30 + seed, free_frac=0.2)
+    rng = np.random.default_rng(40 + seed)
+    x, al, be = rng.normal(size=g.n), rng.normal(size=g.n), rng.uniform(-1, 2, g.n)
+    G = rng.normal(size=(seed + 2, seed + 2))
+    dv = rng.normal(size=3)
+    ref = oracle_mod.polyw_direct(g.rowptr, g.col, x, 1.1, G, dv, al, be)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    got = oracle_mod.polyw_cia(sp, x[sp.perm], 1.1, G, dv, al[sp.perm], be[sp.perm])[sp.iperm]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
