@@ -218,6 +218,18 @@ cia_status cia_plan_create_batch(int64_t B, const cia_graph *graphs, const int32
                                  const double *const *omegas, const cia_coupling *coupling,
                                  const cia_options *opt, cia_plan_t **out);
 
+/* Rank-one link weights for the polynomial models (Sec. "Rank One Coupling",
+ * eq. rank1system, on the plan's graph): every link's coupling is scaled by
+ * alpha_m beta_l,
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml alpha_m beta_l g(x_l, x_m).
+ * The CIA then uses the weighted moments sum_{l in c} beta_l x_l^a
+ * (eq. rank1precompute) and scales the coupling by alpha_m (eq. rank1fast).
+ * alpha, beta: host, n doubles each in the original node order, copied; NULL
+ * stands for all ones; both NULL removes the weights.  Call cia_state_load
+ * again before cia_advance.  CIA_ERR_UNSUPPORTED for other models,
+ * CIA_ERR_NUMERIC for a weight that is not finite. */
+cia_status cia_plan_set_weights(cia_plan_t *plan, const double *alpha, const double *beta);
+
 /* Cut the plan's communities into tiles again with other tile parameters
  * (the same meaning and limits as in cia_options; 0 = default); the split of
  * S is reused.  The resident state's observables are recomputed on the next

@@ -241,6 +241,22 @@ class Plan:
         self._status(self._lib.cia_advance(self._h, _abi.METHOD[method], float(dt), int(steps), rp,
                                            _stream_handle(stream)))
 
+    def set_weights(self, alpha=None, beta=None):
+        """Rank-one link weights alpha_m beta_l for the polynomial models (host
+        arrays of n entries, original order; None = ones; both None removes
+        them).  Load a state again before advance."""
+        arrs = []
+        for v in (alpha, beta):
+            if v is None:
+                arrs.append(None)
+                continue
+            v = np.ascontiguousarray(v, dtype=np.float64)
+            if v.shape != (self.n,):
+                raise ValueError("weights must have n entries")
+            arrs.append(v)
+        ptr = [a.ctypes.data if a is not None else None for a in arrs]
+        _abi.check(self._lib.cia_plan_set_weights(self._h, ptr[0], ptr[1]))
+
     def retile(self, tile_nodes=0, tile_index_bytes=0, staging="auto"):
         _abi.check(self._lib.cia_plan_retile(self._h, int(tile_nodes), int(tile_index_bytes),
                                              _abi.STAGING[staging]))

@@ -123,6 +123,7 @@ SIGNATURES = {
     "cia_plan_create_batch": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, ctypes.POINTER(Coupling),
                                              ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "cia_plan_retile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cia_plan_set_weights": (ctypes.c_int, [_P, _P, _P]),
     "cia_plan_autotune": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int64,
                                          ctypes.POINTER(TuneReport), _P]),
     "cia_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),

@@ -407,6 +407,39 @@ extern "C" cia_status cia_integrate_host(cia_plan_t *pl, int method, double *x_h
     return st;
 }
 
+extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, const double *beta) {
+    clear_error();
+    cia_status st = check_device(pl);
+    if (st != CIA_OK) return st;
+    if (pl->model != CIA_MODEL_POLYNOMIAL)
+        return fail(CIA_ERR_UNSUPPORTED, "rank-one link weights are for the polynomial models");
+    const int64_t n = pl->n;
+    if (alpha || beta) {
+        std::vector<double> w(2 * n);
+        for (int64_t m = 0; m < n; ++m) {
+            const int32_t i = pl->perm[m];
+            w[m] = alpha ? alpha[i] : 1.0;
+            w[n + m] = beta ? beta[i] : 1.0;
+            if (!std::isfinite(w[m]) || !std::isfinite(w[n + m])) return fail(CIA_ERR_NUMERIC, "a weight is not finite");
+        }
+        if (!pl->d.pl_alpha) {
+            void *p = nullptr;
+            CIA_CUDA_TRY(cudaMalloc(&p, (size_t)2 * n * sizeof(double)));
+            pl->allocations.push_back(p);
+            pl->device_bytes += (int64_t)(2 * n * sizeof(double));
+            pl->d.pl_alpha = static_cast<double *>(p);
+            pl->d.pl_beta = pl->d.pl_alpha + n;
+        }
+        CIA_CUDA_TRY(cudaMemcpy(pl->d.pl_alpha, w.data(), (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    pl->poly_weighted = alpha || beta;
+    // the window holds one more row when weighted; the moments change
+    pl->staging = (pl->staging_req == 1 || !poly_window_fits(pl)) ? 1 : 2;
+    pl->needs_load = true;
+    invalidate_graphs(pl);
+    return CIA_OK;
+}
+
 extern "C" cia_status cia_sync(cia_plan_t *pl, void *stream) {
     clear_error();
     if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");

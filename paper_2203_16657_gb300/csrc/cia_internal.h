@@ -95,7 +95,8 @@ struct DeviceBuffers {
     float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
     // polynomial coupling (FP64 stage states and tile power sums)
     double *pl_y[2] = {nullptr, nullptr};     // [n+1] stage states
-    double *pl_part[2] = {nullptr, nullptr};  // [T][p+1] sums of y^k per tile
+    double *pl_part[2] = {nullptr, nullptr};  // [T][p+1] sums of (beta) y^k per tile
+    double *pl_alpha = nullptr, *pl_beta = nullptr;  // [n] rank-one link weights (permuted)
     // ensembles of independent networks
     void *tile_kn = nullptr;                  // [T] K / N_i of the tile's instance, compute precision
     int32_t *inst_tiles = nullptr;            // [B][4] community tiles [0,1), free tiles [2,3) of instance i
@@ -178,6 +179,7 @@ struct cia_plan {
     double poly_c[CIA_MAX_POLY + 1] = {0};
     double poly_dv[CIA_MAX_POLY + 1] = {0};
     bool poly_general = false;          // g(x_l, x_m) instead of h(x_l - x_m)
+    bool poly_weighted = false;         // rank-one link weights alpha_m beta_l
     double poly_g[(CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)] = {0};
     bool cs_has_basis = false;          // a basis was set (cia_plan_set_basis)
     bool cs_feat_valid = false;         // features/partials match the resident state

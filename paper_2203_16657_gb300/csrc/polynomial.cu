@@ -72,6 +72,7 @@ struct PolyParams {
     double *acc, *theta;             // RK4 accumulator, FP64 master
     const int32_t *perm;
     double *rhs_out;                 // kRhs: original order
+    const double *alpha, *beta;      // rank-one link weights (permuted), or both null
     double c_next_dt, b_s, dt;
     int first_stage;
 };
@@ -111,14 +112,15 @@ __device__ __forceinline__ double rk4_update(const PolyParams &a, int64_t m, dou
     return y;
 }
 
-// Sums over the tile of y^a, a = 0..P (each thread contributes its node's
-// value, nothing when it has no node), in a fixed order, to part_out[tile].
+// Sums over the tile of w y^a, a = 0..P (w = the node's beta, or 1; each thread
+// contributes its node's value, nothing when it has no node), in a fixed
+// order, to part_out[tile].
 template <int P>
-__device__ __forceinline__ void tile_power_sums(double *part_out, int tile, bool live, double y,
+__device__ __forceinline__ void tile_power_sums(double *part_out, int tile, bool live, double y, double wnode,
                                                 double (*red)[kMaxP + 1]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double pw[P + 1];
-    double q = 1.0;
+    double q = wnode;
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
         pw[k] = live ? q : 0.0;
@@ -138,16 +140,16 @@ __device__ __forceinline__ void tile_power_sums(double *part_out, int tile, bool
     }
 }
 
-// The tile's sums of y^a, a = 0..P, through shared memory: every thread
+// The tile's sums of w y^a, a = 0..P (w = the node's beta, or 1), through shared memory: every thread
 // stores its powers in scratch ([P+1][kThreads] doubles, free at this point),
 // then warp a adds row a in a fixed order.  Fewer FP64 additions than a
 // shuffle tree in every warp.
 template <int P>
 __device__ __forceinline__ void tile_power_sums_smem(double *part_out, int tile, bool live, double y,
-                                                     double *scratch) {
+                                                     double wnode, double *scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();   // scratch was read before
-    double q = 1.0;
+    double q = wnode;
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
         scratch[k * kThreads + threadIdx.x] = live ? q : 0.0;
@@ -188,16 +190,23 @@ __device__ __forceinline__ void add_powers(double (&s)[P], double u) {
     }
 }
 
-template <int MODE, int P>
+// WT: rank-one weighted links (eq. rank1system): every power sum carries the
+// neighbour's beta_l (the moments become eq. rank1precompute's weighted
+// sums, the degree a weighted degree) and the coupling is scaled by alpha_m
+// (eq. rank1fast).  Window rows: powers 1..P (unweighted; the degree is an
+// integer count) or 0..P times beta (weighted).
+template <int MODE, int P, bool WT>
 __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a) {
+    constexpr int NR = P + (WT ? 1 : 0);   // window rows / sparse sums per link
+    constexpr int A0 = WT ? 0 : 1;         // power of row 0
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double W[kMaxP + 1];
     __shared__ double red[kWarps][kMaxP + 1];
-    double *win = reinterpret_cast<double *>(smem_raw);        // [P][win_cap] powers of the community's states
-    static_assert(P * kMaxChunks >= (P + 1) * kThreads, "the tile sums reuse the chunk table");
-    double *sWm = win + (size_t)P * a.win_cap;                  // [P][kMaxChunks] missing-chunk power sums
-    double *sWi = sWm + P * kMaxChunks;                         // [P][kTileMax] inter power sums per row
-    int *smc = reinterpret_cast<int *>(sWi + P * kTileMax);     // [kMaxChunks] missing links per chunk
+    static_assert(NR * kMaxChunks >= (P + 1) * kThreads, "the tile sums reuse the chunk table");
+    double *win = reinterpret_cast<double *>(smem_raw);        // [NR][win_cap] powers of the community's states
+    double *sWm = win + (size_t)NR * a.win_cap;                 // [NR][kMaxChunks] missing-chunk power sums
+    double *sWi = sWm + NR * kMaxChunks;                        // [NR][kTileMax] inter power sums per row
+    int *smc = reinterpret_cast<int *>(sWi + NR * kTileMax);    // [kMaxChunks] missing links per chunk
     int *sic = smc + kMaxChunks;                                // [kTileMax] inter links per row
     const int t = blockIdx.x;
     const TileDesc d = a.tile_desc[t];
@@ -207,29 +216,38 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
     const unsigned char *b = a.blob + d.blob_off;
     const int cap = a.win_cap;
     const double *cy = a.y_in + d.lo;
+    const double *cb = WT ? a.beta + d.lo : nullptr;
     long long *wfix = reinterpret_cast<long long *>(win);   // the window after conversion
-    double unit[P];                                          // 2^E_a
+    double unit[NR];                                         // 2^E_a
+    // the terms of one link l: beta_l^[WT] x_l^a for the NR powers
+    auto terms = [&](double u, double wl, double (&q)[NR]) {
+        double v = WT ? wl : u;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            q[r] = v;
+            if (r + 1 < NR) v *= u;
+        }
+    };
     // (0) window of powers and their largest magnitudes, moments (FP64 over
     // the community's tiles)
     if (cap) {
-        // largest |u^a| as the integer order of the magnitude's bits
-        unsigned long long mx[P];
+        // largest |term| as the integer order of the magnitude's bits
+        unsigned long long mx[NR];
 #pragma unroll
-        for (int al = 0; al < P; ++al) mx[al] = 0ull;
+        for (int r = 0; r < NR; ++r) mx[r] = 0ull;
         for (int i = threadIdx.x; i < lam; i += kThreads) {
-            const double u = cy[i];
-            double q = u;
+            double q[NR];
+            terms(cy[i], WT ? cb[i] : 1.0, q);
 #pragma unroll
-            for (int al = 0; al < P; ++al) {
-                win[al * cap + i] = q;
-                mx[al] = max(mx[al], (unsigned long long)__double_as_longlong(q) & 0x7fffffffffffffffull);
-                if (al + 1 < P) q *= u;
+            for (int r = 0; r < NR; ++r) {
+                win[r * cap + i] = q[r];
+                mx[r] = max(mx[r], (unsigned long long)__double_as_longlong(q[r]) & 0x7fffffffffffffffull);
             }
         }
 #pragma unroll
-        for (int al = 0; al < P; ++al) {
-            for (int o = 16; o > 0; o >>= 1) mx[al] = max(mx[al], __shfl_xor_sync(0xffffffffu, mx[al], o));
-            if (lane == 0) red[warp][al] = __longlong_as_double((long long)mx[al]);
+        for (int r = 0; r < NR; ++r) {
+            for (int o = 16; o > 0; o >>= 1) mx[r] = max(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], o));
+            if (lane == 0) red[warp][r] = __longlong_as_double((long long)mx[r]);
         }
     }
     if (comm && warp == 0) {
@@ -244,21 +262,21 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
     }
     __syncthreads();
     if (cap) {
-        // E_a from the community's largest |u^a| (the same in every thread),
+        // E_a from the community's largest |term| (the same in every thread),
         // then each thread converts the entries it wrote
-        int sh[P];
+        int sh[NR];
 #pragma unroll
-        for (int al = 0; al < P; ++al) {
+        for (int r = 0; r < NR; ++r) {
             unsigned long long m = 0ull;
-            for (int w = 0; w < kWarps; ++w) m = max(m, (unsigned long long)__double_as_longlong(red[w][al]));
+            for (int w = 0; w < kWarps; ++w) m = max(m, (unsigned long long)__double_as_longlong(red[w][r]));
             const int em = (int)(m >> 52);
-            const int ex = (em ? em : 1) - 1022;   // largest |u^a| < 2^ex
-            sh[al] = min(55 - ex, 1000);           // |u^a| 2^sh < 2^55
-            unit[al] = ldexp(1.0, -sh[al]);
+            const int ex = (em ? em : 1) - 1022;   // largest |term| < 2^ex
+            sh[r] = min(55 - ex, 1000);            // |term| 2^sh < 2^55
+            unit[r] = ldexp(1.0, -sh[r]);
         }
         for (int i = threadIdx.x; i < lam; i += kThreads)
 #pragma unroll
-            for (int al = 0; al < P; ++al) wfix[al * cap + i] = to_fixed(win[al * cap + i], sh[al]);
+            for (int r = 0; r < NR; ++r) wfix[r * cap + i] = to_fixed(win[r * cap + i], sh[r]);
         __syncthreads();
     }
     // (A) sparse power sums: warp per slice, lane per missing chunk and inter row
@@ -270,12 +288,12 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
         const uint4 sd = __ldg(sdesc + s);
         const uint32_t rows = __ldg(srows + s * 32 + lane);
         const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
-        double ms[P], is[P];
-        long long mfix[P];
+        double ms[NR], is[NR];
+        long long mfix[NR];
 #pragma unroll
-        for (int al = 0; al < P; ++al) {
-            ms[al] = is[al] = 0.0;
-            mfix[al] = 0;
+        for (int r = 0; r < NR; ++r) {
+            ms[r] = is[r] = 0.0;
+            mfix[r] = 0;
         }
         int mc = 0, ic = 0;
         const uint4 *mv = mvec + sd.x + lane;
@@ -291,9 +309,12 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
                         ++mc;
                         if (cap) {
 #pragma unroll
-                            for (int al = 0; al < P; ++al) mfix[al] += wfix[al * cap + l];
+                            for (int r = 0; r < NR; ++r) mfix[r] += wfix[r * cap + l];
                         } else {
-                            add_powers<P>(ms, cy[l]);
+                            double tq[NR];
+                            terms(cy[l], WT ? cb[l] : 1.0, tq);
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) ms[r] += tq[r];
                         }
                     }
                 }
@@ -307,45 +328,49 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
             for (int e = 0; e < 4; ++e)
                 if (l4[e] < a.n) {
                     ++ic;
-                    add_powers<P>(is, __ldg(a.y_in + l4[e]));
+                    double tq[NR];
+                    terms(__ldg(a.y_in + l4[e]), WT ? __ldg(a.beta + l4[e]) : 1.0, tq);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) is[r] += tq[r];
                 }
         }
         if (mrow != 0xffffu) {
 #pragma unroll
-            for (int al = 0; al < P; ++al)
-                sWm[al * kMaxChunks + mrow] = cap ? (double)mfix[al] * unit[al] : ms[al];
+            for (int r = 0; r < NR; ++r)
+                sWm[r * kMaxChunks + mrow] = cap ? (double)mfix[r] * unit[r] : ms[r];
             smc[mrow] = mc;
         }
         if (irow != 0xffffu) {
 #pragma unroll
-            for (int al = 0; al < P; ++al) sWi[al * kTileMax + irow] = is[al];
+            for (int r = 0; r < NR; ++r) sWi[r * kTileMax + irow] = is[r];
             sic[irow] = ic;
         }
     }
     __syncthreads();
-    // (B) thread per node: T_a = W_a - x^a - missing + inter, then sum_a T_a e_a(x)
+    // (B) thread per node: T_a = W_a - diagonal - missing + inter, then
+    // alpha_m^[WT] sum_a T_a e_a(x)
     const bool live = threadIdx.x < d.count;
-    double ynext = 0.0;
+    double ynext = 0.0, wnode = 0.0;
     if (live) {
-        const int r = threadIdx.x;
-        const int64_t m = d.first + r;
+        const int r0 = threadIdx.x;
+        const int64_t m = d.first + r0;
         const double x = a.y_in[m];
+        wnode = WT ? a.beta[m] : 1.0;
         double T[P + 1];
-        int deg = sic[r];
+        int deg = sic[r0];
 #pragma unroll
-        for (int al = 0; al < P; ++al) T[al + 1] = sWi[al * kTileMax + r];
-        const uint32_t vt = __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r);
+        for (int r = 0; r < NR; ++r) T[r + A0] = sWi[r * kTileMax + r0];
+        const uint32_t vt = __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r0);
         for (uint32_t c = vt & 0xffffu; c < (vt & 0xffffu) + (vt >> 16); ++c) {
             deg -= smc[c];
 #pragma unroll
-            for (int al = 0; al < P; ++al) T[al + 1] -= sWm[al * kMaxChunks + c];
+            for (int r = 0; r < NR; ++r) T[r + A0] -= sWm[r * kMaxChunks + c];
         }
-        T[0] = (double)deg;
+        if (!WT) T[0] = (double)deg;
         if (comm) {
-            T[0] += W[0] - 1.0;
-            double q = x;
+            double q = wnode;   // the diagonal term beta_m^[WT] x_m^a
 #pragma unroll
-            for (int al = 1; al <= P; ++al) {
+            for (int al = 0; al <= P; ++al) {
                 T[al] += W[al] - q;
                 q *= x;
             }
@@ -355,17 +380,19 @@ __global__ void __launch_bounds__(kThreads) poly_stage_kernel(const PolyParams a
         double coup = 0.0;
 #pragma unroll
         for (int al = 0; al <= P; ++al) coup = fma(T[al], e[al], coup);
+        if (WT) coup *= a.alpha[m];
         const double k = -horner<kMaxP>(a.v, x) + a.k_over_n * coup;
         ynext = rk4_update<MODE>(a, m, k);
     }
     if (MODE == kRhs) return;
-    tile_power_sums_smem<P>(a.part_out, t, live, ynext, sWm);
+    tile_power_sums_smem<P>(a.part_out, t, live, ynext, wnode, sWm);
 }
 
 // Direct method, one CTA per tile: `group` threads per row evaluate the
 // coupling link by link over the row's CSR neighbours (rows padded to 4-entry
 // vectors with the sentinel n): h(x_l - x_m), or g(x_l, x_m) = sum_a e_a(x_m)
-// x_l^a; then the same update and power sums as the CIA.
+// x_l^a, times beta_l and finally alpha_m when the links are weighted; then
+// the same update and power sums as the CIA.
 template <int MODE, bool GEN, int P>
 __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams a) {
     __shared__ double sW[kTileMax];
@@ -388,7 +415,8 @@ __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams 
             for (int k = 0; k < 4; ++k)
                 if (l4[k] < a.n) {
                     const double u = __ldg(a.y_in + l4[k]);
-                    s += GEN ? horner<P>(e, u) : horner<P>(a.c, u - y);
+                    const double gl_ = GEN ? horner<P>(e, u) : horner<P>(a.c, u - y);
+                    s += a.beta ? __ldg(a.beta + l4[k]) * gl_ : gl_;
                 }
         }
         for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
@@ -396,15 +424,17 @@ __global__ void __launch_bounds__(kThreads) poly_direct_kernel(const PolyParams 
     }
     __syncthreads();
     const bool live = threadIdx.x < d.count;
-    double ynext = 0.0;
+    double ynext = 0.0, wnode = 0.0;
     if (live) {
         const int64_t m = d.first + threadIdx.x;
         const double x = a.y_in[m];
-        const double k = -horner<kMaxP>(a.v, x) + a.k_over_n * sW[threadIdx.x];
+        const double coup = a.alpha ? a.alpha[m] * sW[threadIdx.x] : sW[threadIdx.x];
+        const double k = -horner<kMaxP>(a.v, x) + a.k_over_n * coup;
         ynext = rk4_update<MODE>(a, m, k);
+        wnode = a.beta ? a.beta[m] : 1.0;
     }
     if (MODE == kRhs) return;
-    tile_power_sums<P>(a.part_out, t, live, ynext, red);
+    tile_power_sums<P>(a.part_out, t, live, ynext, wnode, red);
 }
 
 // State load: x (original order) -> master (optional) and stage state,
@@ -415,30 +445,32 @@ __global__ void __launch_bounds__(kThreads) poly_load_kernel(const PolyParams a,
     const int t = blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const bool live = threadIdx.x < d.count;
-    double y = 0.0;
+    double y = 0.0, wnode = 0.0;
     if (live) {
         const int64_t m = d.first + threadIdx.x;
         y = x[a.perm[m]];
         if (master) master[m] = y;
         a.y_out[m] = y;
+        wnode = a.beta ? a.beta[m] : 1.0;
     }
-    tile_power_sums<P>(a.part_out, t, live, y, red);
+    tile_power_sums<P>(a.part_out, t, live, y, wnode, red);
 }
 
 size_t window_cap(const cia_plan *pl) { return (size_t)((pl->max_comm + 1) & ~(int64_t)1); }
 
-size_t tables_bytes(int P) { return (size_t)P * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
+// Rows of the window and of the sparse sums: powers 1..P, or 0..P when weighted.
+int rows(const cia_plan *pl) { return pl->poly_p + (pl->poly_weighted ? 1 : 0); }
+
+size_t tables_bytes(int nr) { return (size_t)nr * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
 
 // The powers of the largest community's states fit the shared-memory window
 // (the kernel's static shared memory is under 4 KB).
 bool window_fits(const cia_plan *pl) {
-    const int P = pl->poly_p;
-    return window_cap(pl) * 8 * P + tables_bytes(P) + 4096 <= (size_t)pl->smem_optin;
+    return window_cap(pl) * 8 * rows(pl) + tables_bytes(rows(pl)) + 4096 <= (size_t)pl->smem_optin;
 }
 
 size_t stage_smem(const cia_plan *pl) {
-    const int P = pl->poly_p;
-    return (pl->staging == 2 ? window_cap(pl) * 8 * P : 0) + tables_bytes(P);
+    return (pl->staging == 2 ? window_cap(pl) * 8 * rows(pl) : 0) + tables_bytes(rows(pl));
 }
 
 PolyParams base_params(const cia_plan *pl, int slot) {
@@ -476,6 +508,8 @@ PolyParams base_params(const cia_plan *pl, int slot) {
     a.acc = static_cast<double *>(d.acc);
     a.theta = d.theta;
     a.perm = d.perm;
+    a.alpha = pl->poly_weighted ? d.pl_alpha : nullptr;
+    a.beta = pl->poly_weighted ? d.pl_beta : nullptr;
     return a;
 }
 
@@ -496,11 +530,12 @@ cudaError_t launch(void (*kernel)(PolyParams), const cia_plan *pl, size_t smem, 
 
 template <int MODE, int P>
 cudaError_t launch_degree(const cia_plan *pl, int method, const PolyParams &a, cudaStream_t s) {
-    constexpr int id = 3 * (P - 1) + MODE;   // stage kernels 0..11, direct kernels 12..35
+    constexpr int id = 3 * (P - 1) + MODE;   // stage kernels 0..23, direct kernels 24..47
     if (method == Method::DIRECT)
-        return pl->poly_general ? launch<12 + 2 * id>(poly_direct_kernel<MODE, true, P>, pl, 0, a, s)
-                                : launch<13 + 2 * id>(poly_direct_kernel<MODE, false, P>, pl, 0, a, s);
-    return launch<id>(poly_stage_kernel<MODE, P>, pl, stage_smem(pl), a, s);
+        return pl->poly_general ? launch<24 + 2 * id>(poly_direct_kernel<MODE, true, P>, pl, 0, a, s)
+                                : launch<25 + 2 * id>(poly_direct_kernel<MODE, false, P>, pl, 0, a, s);
+    return pl->poly_weighted ? launch<12 + id>(poly_stage_kernel<MODE, P, true>, pl, stage_smem(pl), a, s)
+                             : launch<id>(poly_stage_kernel<MODE, P, false>, pl, stage_smem(pl), a, s);
 }
 
 template <int MODE>

@@ -328,6 +328,100 @@ def test_general_integrate(cia, oracle_mod, torch_mod):
         assert np.abs(x.cpu().numpy() - ref).max() < 1e-11 * np.abs(ref).max(), method
 
 
+# ------------------------------------------------------------------ rank-one link weights
+
+def difference_as_general(c):
+    from math import comb
+    p = len(c) - 1
+    G = np.zeros((p + 1, p + 1))
+    for a in range(p + 1):
+        for b in range(p + 1 - a):
+            G[a, b] = c[a + b] * comb(a + b, a) * (-1) ** b
+    return G
+
+
+@pytest.mark.parametrize("staging", ["auto", "plain"])
+@pytest.mark.parametrize("form,p", [("difference", 1), ("difference", 3), ("general", 2), ("general", 4)])
+def test_weighted_rhs(cia, oracle_mod, torch_mod, form, p, staging):
+    g = S.sbm_graph([300, 129, 31, 200], 0.85, inter_degree=6.0, seed=40 + p, n_free=25)
+    rng = np.random.default_rng(60 + p)
+    x = rng.uniform(-1.2, 1.2, g.n)
+    al = rng.uniform(0.5, 2.0, g.n)
+    be = rng.normal(size=g.n)
+    be[::7] = 0.0
+    dv = (0.1, -1.0, 0.0, 1.0)
+    if form == "difference":
+        c = rng.normal(size=p + 1)
+        G = difference_as_general(c)
+        plan = make_plan(cia, g, 1.3, c, dv, tile_nodes=128, staging=staging)
+    else:
+        G = rng.normal(size=(p + 1, p + 1))
+        plan = make_general(cia, g, 1.3, G, dv, tile_nodes=128, staging=staging)
+    plan.set_weights(al, be)
+    assert plan.info()["staging"] == (1 if staging == "plain" else 2)
+    ref = oracle_mod.polyw_direct(g.rowptr, g.col, x, 1.3, G, dv, al, be)
+    pot = oracle_mod.polyw_direct(g.rowptr, g.col, x, 0.0, G, dv, al, be)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert coupling_rel_err(got, ref, pot) < FP64_TOL, method
+
+
+def test_weighted_one_sided_and_removed(cia, oracle_mod, torch_mod):
+    """alpha alone, beta alone, then no weights: the unweighted plan's values."""
+    g = S.sbm_graph([150, 90], 0.8, inter_degree=4.0, seed=3, n_free=10)
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=g.n)
+    c, dv = (0.0, 1.0, -0.2), DW_DV
+    G = difference_as_general(c)
+    plan = make_plan(cia, g, 2.0, c, dv)
+    base = gpu_rhs(torch_mod, plan, x, "cia")
+    ones = np.ones(g.n)
+    al, be = rng.uniform(0, 2, g.n), rng.uniform(-1, 1, g.n)
+    pot = oracle_mod.polyw_direct(g.rowptr, g.col, x, 0.0, G, dv, ones, ones)
+    for a_, b_ in ((al, None), (None, be)):
+        plan.set_weights(a_, b_)
+        ref = oracle_mod.polyw_direct(g.rowptr, g.col, x, 2.0, G, dv,
+                                      a_ if a_ is not None else ones, b_ if b_ is not None else ones)
+        assert coupling_rel_err(gpu_rhs(torch_mod, plan, x, "cia"), ref, pot) < FP64_TOL
+    plan.set_weights(None, None)
+    assert np.array_equal(gpu_rhs(torch_mod, plan, x, "cia"), base)
+
+
+def test_weighted_integrate(cia, oracle_mod, torch_mod):
+    """Rank-one weighted Desai-Zwanzig network, 50 RK4 steps, CUDA-graph replay."""
+    g = S.sbm_graph([400, 200, 77], 0.8, inter_degree=5.0, seed=50, n_free=19)
+    rng = np.random.default_rng(13)
+    x0 = rng.normal(size=g.n)
+    al, be = rng.uniform(0.5, 1.5, g.n), rng.uniform(0.0, 2.0, g.n)
+    K, dt, steps = 3.0, 0.01, 50
+    G = difference_as_general((0.0, 1.0))
+    rhs = lambda y: oracle_mod.polyw_direct(g.rowptr, g.col, y, K, G, DW_DV, al, be)
+    ref, _ = oracle_mod.integrate(rhs, x0, dt, steps, wrap=False)
+    plan = make_plan(cia, g, K, (0.0, 1.0), DW_DV)
+    plan.set_weights(al, be)
+    for method in ("cia", "direct"):
+        x = torch_mod.from_numpy(x0.copy()).cuda()
+        plan.integrate(x, dt, steps, method=method)
+        assert np.abs(x.cpu().numpy() - ref).max() < 1e-11 * np.abs(ref).max(), method
+
+
+def test_weights_rejections(cia, torch_mod):
+    g = S.sbm_graph([40, 30], 0.8, inter_degree=2.0, seed=1, n_free=3)
+    kplan = cia.Plan(g.rowptr, g.col, g.labels, np.zeros(g.n), K=1.0)
+    with pytest.raises(cia.CiaError, match="polynomial"):
+        kplan.set_weights(np.ones(g.n), None)
+    plan = make_plan(cia, g, 1.0, (0.0, 1.0), DW_DV)
+    with pytest.raises(cia.CiaError, match="finite"):
+        plan.set_weights(np.full(g.n, np.inf), None)
+    with pytest.raises(ValueError):
+        plan.set_weights(np.ones(g.n + 1), None)
+    x = torch_mod.zeros(g.n, dtype=torch_mod.float64, device="cuda")
+    plan.state_load(x)
+    plan.set_weights(None, np.ones(g.n))
+    with pytest.raises(cia.CiaError, match="load"):
+        plan.advance(0.01, 1)
+
+
 # ------------------------------------------------------------------ errors
 
 def test_plan_rejections(cia, torch_mod):
