@@ -77,6 +77,9 @@ def _load():
         lib.ora_polyw_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P, P, P, P]
         lib.ora_polyw_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, P, ctypes.c_int, P,
                                       P, P, P, P]
+        lib.ora_fourierg_direct.argtypes = [I64, P, P, P, D, ctypes.c_int, D, P, P, P, P, ctypes.c_int, P, P]
+        lib.ora_fourierg_cia.argtypes = [I64, I64, P, P, P, P, P, D, ctypes.c_int, D, P, P, P, P,
+                                         ctypes.c_int, P, P, P]
         _lib = lib
     return _lib
 
@@ -378,6 +381,42 @@ def polyw_cia(sp: Split, x_perm, K, G, dv, alpha_perm, beta_perm) -> np.ndarray:
     lib.ora_polyw_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
                       float(K), G.shape[0] - 1, _p(G), len(dv) - 1, _p(dv), _p(alpha), _p(beta), _p(w),
                       _p(out))
+    return out
+
+
+def _fourier_blocks(C):
+    C = [_square(c) for c in C]
+    if len(C) != 4 or len({c.shape for c in C}) != 1:
+        raise ValueError("C must be four square (p+1) x (p+1) arrays C11, C12, C21, C22")
+    return C
+
+
+def fourierg_direct(rowptr, col, x, K, L, C, dv) -> np.ndarray:
+    """x' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m) with the real 2-D Fourier
+    coupling of eq. FourierRealExpansion: C = (C11, C12, C21, C22), each
+    (p+1) x (p+1), frequencies pi a / L."""
+    lib = _load()
+    x = _f64(x)
+    C11, C12, C21, C22 = _fourier_blocks(C)
+    dv = _f64(dv)
+    out = np.empty_like(x)
+    lib.ora_fourierg_direct(len(x), _p(_i64(rowptr)), _p(_i32(col)), _p(x), float(K), C11.shape[0] - 1,
+                            float(L), _p(C11), _p(C12), _p(C21), _p(C22), len(dv) - 1, _p(dv), _p(out))
+    return out
+
+
+def fourierg_cia(sp: Split, x_perm, K, L, C, dv) -> np.ndarray:
+    """The same by the CIA: the real generalised order parameters r^cos_a, r^sin_a
+    per community (eq. RealOP), the dense term from them, the sparse sum over S."""
+    lib = _load()
+    x = _f64(x_perm)
+    C11, C12, C21, C22 = _fourier_blocks(C)
+    dv = _f64(dv)
+    w = np.zeros(max(1, 2 * sp.M * C11.shape[0]))
+    out = np.empty_like(x)
+    lib.ora_fourierg_cia(sp.n, sp.M, _p(sp.off), _p(sp.s_rowptr), _p(sp.s_col), _p(sp.s_val), _p(x),
+                         float(K), C11.shape[0] - 1, float(L), _p(C11), _p(C12), _p(C21), _p(C22),
+                         len(dv) - 1, _p(dv), _p(w), _p(out))
     return out
 
 

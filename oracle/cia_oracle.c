@@ -504,3 +504,91 @@ void ora_polyw_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_ro
         out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
     }
 }
+
+/* ------------------------------------------------------------------------
+ * General coupling by a real 2-D Fourier series (Sec. "Real Fourier Series",
+ * eq. FourierRealExpansion, eq. RealOP):
+ *   x_m' = -V'(x_m) + (K/N) sum_l a_ml g(x_l, x_m),
+ *   g(u, y) = sum_{a,b=0..p} C11[a][b] cos(a w u) cos(b w y) + C12[a][b] cos(a w u) sin(b w y)
+ *                          + C21[a][b] sin(a w u) cos(b w y) + C22[a][b] sin(a w u) sin(b w y),
+ * w = pi / L, each C row-major with p + 1 columns. */
+static double fourier2_eval(const double *C11, const double *C12, const double *C21, const double *C22,
+                            int p, double w, double u, double y) {
+    double s = 0.0;
+    for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) {
+            const double cu = cos(a * w * u), su = sin(a * w * u);
+            const double cy = cos(b * w * y), sy = sin(b * w * y);
+            const int i = a * (p + 1) + b;
+            s += C11[i] * cu * cy + C12[i] * cu * sy + C21[i] * su * cy + C22[i] * su * sy;
+        }
+    return s;
+}
+
+/* Direct RHS: g link by link. */
+void ora_fourierg_direct(int64_t n, const int64_t *rowptr, const int32_t *col, const double *x, double K,
+                         int p, double L, const double *C11, const double *C12, const double *C21,
+                         const double *C22, int q, const double *dv, double *out) {
+    const double scale = K / (double)n, w = 3.14159265358979323846 / L;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int64_t e = rowptr[m]; e < rowptr[m + 1]; ++e)
+            acc += fourier2_eval(C11, C12, C21, C22, p, w, x[col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + scale * acc;
+    }
+}
+
+/* CIA RHS (permuted state, S with its diagonal -1 entries):
+ * (E1.1) rc[c][a] = (1/N) sum_{l in c} cos(a w x_l), rs[c][a] = (1/N) sum_{l in c} sin(a w x_l),
+ *        a = 0..p                                                  (eq. RealOP)
+ * (E1.2) dense_m = sum_{a,b} C11 rc_a cos(b w x_m) + C12 rc_a sin(b w x_m)
+ *                          + C21 rs_a cos(b w x_m) + C22 rs_a sin(b w x_m)
+ * (E2)   sparse_m = (1/N) sum_l s_ml g(x_l, x_m)
+ *        out_m = -V'(x_m) + K (dense_m + sparse_m).
+ * w: caller scratch of 2 M (p + 1) doubles. */
+void ora_fourierg_cia(int64_t n, int64_t M, const int64_t *off, const int64_t *s_rowptr, const int32_t *s_col,
+                      const int8_t *s_val, const double *x, double K, int p, double L, const double *C11,
+                      const double *C12, const double *C21, const double *C22, int q, const double *dv,
+                      double *wbuf, double *out) {
+    const double invN = 1.0 / (double)n, w = 3.14159265358979323846 / L;
+    double *rc = wbuf, *rs = wbuf + M * (p + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t cc = 0; cc < M; ++cc) {
+        for (int a = 0; a <= p; ++a) {
+            double sc = 0.0, ss = 0.0;
+            for (int64_t l = off[cc]; l < off[cc + 1]; ++l) {
+                sc += cos(a * w * x[l]);
+                ss += sin(a * w * x[l]);
+            }
+            rc[cc * (p + 1) + a] = invN * sc;
+            rs[cc * (p + 1) + a] = invN * ss;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t m = 0; m < n; ++m) {
+        int64_t cc = -1;
+        if (m < off[M]) {
+            int64_t lo = 0, hi = M;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) / 2;
+                if (off[mid] <= m) lo = mid;
+                else hi = mid;
+            }
+            cc = lo;
+        }
+        double dense = 0.0;
+        if (cc >= 0)
+            for (int a = 0; a <= p; ++a)
+                for (int b = 0; b <= p; ++b) {
+                    const int i = a * (p + 1) + b;
+                    const double ca = rc[cc * (p + 1) + a], sa = rs[cc * (p + 1) + a];
+                    const double cy = cos(b * w * x[m]), sy = sin(b * w * x[m]);
+                    dense += C11[i] * ca * cy + C12[i] * ca * sy + C21[i] * sa * cy + C22[i] * sa * sy;
+                }
+        double sparse = 0.0;
+        for (int64_t e = s_rowptr[m]; e < s_rowptr[m + 1]; ++e)
+            sparse += (double)s_val[e] * fourier2_eval(C11, C12, C21, C22, p, w, x[s_col[e]], x[m]);
+        out[m] = -poly_eval(dv, q, x[m]) + K * (dense + invN * sparse);
+    }
+}

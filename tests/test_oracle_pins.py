@@ -555,3 +555,82 @@ def test_rank_one_cia_equals_direct(oracle_mod, seed):
     sp = oracle_mod.split(g.rowptr, g.col, g.labels)
     got = oracle_mod.polyw_cia(sp, x[sp.perm], 1.1, G, dv, al[sp.perm], be[sp.perm])[sp.iperm]
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------ general real 2-D Fourier coupling
+
+def _blocks(p, rng=None):
+    if rng is None:
+        return [np.zeros((p + 1, p + 1)) for _ in range(4)]
+    return [rng.normal(size=(p + 1, p + 1)) for _ in range(4)]
+
+
+def test_fourier_general_sine_of_difference_is_kuramoto(oracle_mod):
+    """sin(w(u - y)) = sin(wu)cos(wy) - cos(wu)sin(wy): C21[1,1] = 1, C12[1,1] = -1
+    gives the Kuramoto coupling of the phases w x (the Kuramoto oracle)."""
+    import synthetic as S
+    g = S.random_labels_graph(60, 0.25, 3, seed=12, free_frac=0.2)
+    rng = np.random.default_rng(31)
+    L = 2.5
+    x = rng.uniform(-L, L, g.n)
+    C = _blocks(1)
+    C[2][1, 1], C[1][1, 1] = 1.0, -1.0
+    got = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 1.7, L, C, [0.0])
+    want = oracle_mod.kuramoto_direct(g.rowptr, g.col, np.pi * x / L, np.zeros(g.n), 1.7)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_fourier_general_constant_and_own_terms(oracle_mod):
+    """C11[0,0] = 1 sums the degree; C12[0,2] = 1 gives deg(m) sin(2 w x_m)."""
+    import synthetic as S
+    g = S.random_labels_graph(40, 0.3, 2, seed=13, free_frac=0.1)
+    x = np.random.default_rng(32).uniform(-3, 3, g.n)
+    deg = np.diff(g.rowptr)
+    C = _blocks(2)
+    C[0][0, 0] = 1.0
+    got = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 2.0, 3.0, C, [0.0])
+    np.testing.assert_allclose(got, 2.0 / g.n * deg, rtol=1e-15, atol=0)
+    C = _blocks(2)
+    C[1][0, 2] = 1.0
+    got = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 2.0, 3.0, C, [0.0])
+    np.testing.assert_allclose(got, 2.0 / g.n * deg * np.sin(2 * np.pi * x / 3.0), rtol=1e-13, atol=1e-16)
+
+
+def test_fourier_general_brute_force_and_periodicity(oracle_mod):
+    """Dense-matrix brute force with numpy's cos/sin; shifting every state by 2L
+    leaves the coupling unchanged (period of the series)."""
+    import synthetic as S
+    g = S.random_labels_graph(30, 0.35, 3, seed=14, free_frac=0.2)
+    A = np.zeros((g.n, g.n))
+    for m in range(g.n):
+        A[m, g.col[g.rowptr[m]:g.rowptr[m + 1]]] = 1.0
+    rng = np.random.default_rng(33)
+    p, L, K = 2, 1.5, 0.9
+    C = _blocks(p, rng)
+    x = rng.uniform(-L, L, g.n)
+    w = np.pi / L
+    U, Y = x[None, :], x[:, None]
+    G = sum(C[0][a, b] * np.cos(a * w * U) * np.cos(b * w * Y) + C[1][a, b] * np.cos(a * w * U) * np.sin(b * w * Y)
+            + C[2][a, b] * np.sin(a * w * U) * np.cos(b * w * Y) + C[3][a, b] * np.sin(a * w * U) * np.sin(b * w * Y)
+            for a in range(p + 1) for b in range(p + 1))
+    want = K / g.n * (A * G).sum(1)
+    got = oracle_mod.fourierg_direct(g.rowptr, g.col, x, K, L, C, [0.0])
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-13)
+    shifted = oracle_mod.fourierg_direct(g.rowptr, g.col, x + 2 * L, K, L, C, [0.0])
+    np.testing.assert_allclose(shifted, got, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_fourier_general_cia_equals_direct(oracle_mod, p):
+    """The real generalised order parameters (eq. RealOP) with the dense formula
+    plus the exact sparse corrections reach the direct sum."""
+    import synthetic as S
+    g = S.random_labels_graph(50, 0.35, 3, seed=70 + p, free_frac=0.2)
+    rng = np.random.default_rng(80 + p)
+    C = _blocks(p, rng)
+    dv = rng.normal(size=3)
+    x = rng.uniform(-2, 2, g.n)
+    ref = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 1.2, 2.0, C, dv)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    got = oracle_mod.fourierg_cia(sp, x[sp.perm], 1.2, 2.0, C, dv)[sp.iperm]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
