@@ -56,7 +56,8 @@ typedef enum {
     CIA_MODEL_KURAMOTO_HO = 1,  /* the same plus a triadic term on complete community hyperedges (App. A.7) */
     CIA_MODEL_CUCKER_SMALE = 2, /* 2-D flocking agents (App. A.6), state (s_x, s_y, v_x, v_y) per node */
     CIA_MODEL_POLYNOMIAL = 3,   /* polynomial difference coupling with a potential (App. A.3, A.5) */
-    CIA_MODEL_POLYNOMIAL_GENERAL = 4 /* general polynomial coupling g(x_l, x_m) with a potential (App. A.3) */
+    CIA_MODEL_POLYNOMIAL_GENERAL = 4, /* general polynomial coupling g(x_l, x_m) with a potential (App. A.3) */
+    CIA_MODEL_FOURIER_GENERAL = 5     /* general real 2-D Fourier coupling g(x_l, x_m) with a potential (App. A.3) */
 } cia_model;
 
 typedef enum {
@@ -116,7 +117,17 @@ typedef struct {
  * (u is the neighbour's state; entries with a or b above p are ignored).  The
  * CIA evaluates the dense term sum_{a,b} poly_g[a][b] W_ca x_m^b (eq. PolyRHS)
  * from the same moments; the links of S are summed with g itself.  poly_c is
- * ignored.  FP64 only; omega must be NULL. */
+ * ignored.  FP64 only; omega must be NULL.
+ * CIA_MODEL_FOURIER_GENERAL (eq. GeneralNetworkFourier with the real series
+ * of eq. FourierRealExpansion, App. A.3): the same with
+ *   g(u, y) = sum_{a,b=0..p} C11[a][b] cos(a w u) cos(b w y) + C12[a][b] cos(a w u) sin(b w y)
+ *                          + C21[a][b] sin(a w u) cos(b w y) + C22[a][b] sin(a w u) sin(b w y),
+ * w = pi / fourier_L, C11 = fourier_c[0], C12 = fourier_c[1], C21 = fourier_c[2],
+ * C22 = fourier_c[3], each row-major with CIA_MAX_HARMONICS + 1 columns;
+ * p in [1, CIA_MAX_HARMONICS] (entries with a or b above p are ignored).  The
+ * CIA keeps the real generalised order parameters sum_{l in c} cos(a w x_l),
+ * sum_{l in c} sin(a w x_l) per community (eq. RealOP); the links of S are
+ * summed with g itself.  FP64 only; omega must be NULL. */
 typedef struct {
     int model;                  /* cia_model */
     int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
@@ -128,6 +139,8 @@ typedef struct {
     double poly_c[CIA_MAX_POLY + 1];   /* polynomial model: coefficients of h, degree p */
     double dV[CIA_MAX_POLY + 1];       /* polynomial models: coefficients of V' */
     double poly_g[(CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)]; /* general polynomial model: g[a][b], row-major */
+    double fourier_L;                  /* general Fourier model: half period, > 0 */
+    double fourier_c[4][(CIA_MAX_HARMONICS + 1) * (CIA_MAX_HARMONICS + 1)]; /* C11, C12, C21, C22 */
 } cia_coupling;
 
 typedef struct {

@@ -51,16 +51,20 @@ class Plan:
     omega None (Desai-Zwanzig: dV = (0, -1, 0, 1), poly_c = (0, 1)).
     model="polynomial_general": the same with g(x_l, x_m) = sum_{a,b} poly_g[a][b] x_l^a x_m^b,
     poly_g a square (p+1) x (p+1) array.
+    model="fourier_general": the same with the real 2-D Fourier series of eq.
+    FourierRealExpansion, fourier_C = (C11, C12, C21, C22) of shape (p+1) x (p+1),
+    frequencies pi a / fourier_L.
     """
 
     def __init__(self, rowptr, col, labels, omega=None, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
                  precision="fp64", build_direct=False, tile_nodes=0, group_size=0,
                  tile_index_bytes=0, staging="auto", model="kuramoto", K2=0.0, sigma=1.0,
-                 beta=0.0, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None, use_graphs=True, _batch=None):
+                 beta=0.0, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None, fourier_L=None, fourier_C=None,
+                 use_graphs=True, _batch=None):
         lib = load()
         self._lib = lib
         self._keep = []
-        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c, dV, poly_g)
+        cp = self._coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c, dV, poly_g, fourier_L, fourier_C)
         opt = _abi.Options(_abi.PRECISION[precision], int(bool(build_direct)), int(tile_nodes),
                            int(group_size), int(tile_index_bytes), _abi.STAGING[staging],
                            0 if use_graphs else 1)
@@ -124,11 +128,12 @@ class Plan:
         return cls(None, None, None, _batch=(list(graphs), list(labels), list(omegas)), **kw)
 
     @staticmethod
-    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None):
+    def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None,
+                  fourier_L=None, fourier_C=None):
         d_sin = list(d_sin)
         d_cos = list(d_cos)
         p = len(d_sin)
-        poly = model in ("polynomial", "polynomial_general")
+        poly = model in ("polynomial", "polynomial_general", "fourier_general")
         if not poly and (len(d_cos) != p or not 1 <= p <= _abi.CIA_MAX_HARMONICS):
             raise ValueError("d_sin and d_cos must have the same length in [1, %d]"
                              % _abi.CIA_MAX_HARMONICS)
@@ -149,7 +154,22 @@ class Plan:
                 raise ValueError("dV takes at most %d coefficients" % S)
             for j, v in enumerate(dV):
                 cp.dV[j] = float(v)
-            if model == "polynomial":
+            if model == "fourier_general":
+                if fourier_L is None or fourier_C is None or len(fourier_C) != 4:
+                    raise ValueError("fourier_general needs fourier_L and fourier_C = (C11, C12, C21, C22)")
+                C = [np.asarray(c, dtype=np.float64) for c in fourier_C]
+                q = C[0].shape[0] - 1
+                if any(c.shape != (q + 1, q + 1) for c in C) or not 1 <= q <= _abi.CIA_MAX_HARMONICS:
+                    raise ValueError("fourier_C must hold four (p+1) x (p+1) arrays, 1 <= p <= %d"
+                                     % _abi.CIA_MAX_HARMONICS)
+                cp.p = q
+                cp.fourier_L = float(fourier_L)
+                SH = _abi.CIA_MAX_HARMONICS + 1
+                for i, c in enumerate(C):
+                    for a_ in range(q + 1):
+                        for b_ in range(q + 1):
+                            cp.fourier_c[i][a_ * SH + b_] = float(c[a_, b_])
+            elif model == "polynomial":
                 poly_c = list(poly_c)
                 if not 1 <= len(poly_c) <= S:
                     raise ValueError("poly_c needs 1..%d coefficients" % S)

@@ -22,7 +22,8 @@ STATUS = {
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
 STAGING = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}
-MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2, "polynomial": 3, "polynomial_general": 4}
+MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2, "polynomial": 3, "polynomial_general": 4,
+         "fourier_general": 5}
 
 
 class CiaError(RuntimeError):
@@ -44,7 +45,9 @@ class Coupling(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
                 ("poly_c", ctypes.c_double * (CIA_MAX_POLY + 1)),
                 ("dV", ctypes.c_double * (CIA_MAX_POLY + 1)),
-                ("poly_g", ctypes.c_double * ((CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)))]
+                ("poly_g", ctypes.c_double * ((CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1))),
+                ("fourier_L", ctypes.c_double),
+                ("fourier_c", (ctypes.c_double * ((CIA_MAX_HARMONICS + 1) * (CIA_MAX_HARMONICS + 1))) * 4)]
 
 
 class Options(ctypes.Structure):

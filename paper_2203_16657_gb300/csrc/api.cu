@@ -90,8 +90,8 @@ cia_status rhs_common(cia_plan *pl, int method, const double *x, double *dxdt, v
     // the slot not holding the resident state is free between calls
     const int slot = pl->state_slot ^ 1;
     if (pl->model == CIA_MODEL_POLYNOMIAL) {
-        CIA_CUDA_TRY(poly_launch_load(pl, x, false, slot, s));
-        CIA_CUDA_TRY(poly_launch_rhs(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA, slot, dxdt, s));
+        CIA_CUDA_TRY(gc_launch_load(pl, x, false, slot, s));
+        CIA_CUDA_TRY(gc_launch_rhs(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA, slot, dxdt, s));
         return CIA_OK;
     }
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
@@ -136,7 +136,7 @@ cia_status stage_launch(cia_plan *pl, int m, int stage, int slot, double dt, cud
     const bool rec = pl->prof_on && pl->prof_used < pl->prof_cap;
     if (rec) CIA_CUDA_TRY(cudaEventRecord(pl->prof_ev[2 * pl->prof_used], s));
     if (pl->model == CIA_MODEL_CUCKER_SMALE) CIA_CUDA_TRY(cs_launch_stage(pl, m, stage, slot, dt, s));
-    else if (pl->model == CIA_MODEL_POLYNOMIAL) CIA_CUDA_TRY(poly_launch_stage(pl, m, stage, slot, dt, s));
+    else if (pl->model == CIA_MODEL_POLYNOMIAL) CIA_CUDA_TRY(gc_launch_stage(pl, m, stage, slot, dt, s));
     else CIA_CUDA_TRY(launch_rk4_stage(pl, m, stage, slot, dt, s));
     if (rec) {
         CIA_CUDA_TRY(cudaEventRecord(pl->prof_ev[2 * pl->prof_used + 1], s));
@@ -217,7 +217,7 @@ cia_status ensure_step_graph(cia_plan *pl, int m, int slot, double dt, double *r
     cudaError_t err = cudaSuccess;
     int sl = slot;
     for (int stage = 1; stage <= 4 && err == cudaSuccess; ++stage) {
-        err = pl->model == CIA_MODEL_POLYNOMIAL ? poly_launch_stage(pl, m, stage, sl, dt, cs)
+        err = pl->model == CIA_MODEL_POLYNOMIAL ? gc_launch_stage(pl, m, stage, sl, dt, cs)
                                                 : launch_rk4_stage(pl, m, stage, sl, dt, cs);
         sl ^= 1;
     }
@@ -260,7 +260,7 @@ extern "C" cia_status cia_state_load(cia_plan_t *pl, const double *x, void *stre
         CIA_CUDA_TRY(cs_launch_load(pl, x, true, 0, (cudaStream_t)stream));
         pl->cs_feat_valid = false;   // features are computed by the first CIA step
     } else if (pl->model == CIA_MODEL_POLYNOMIAL) {
-        CIA_CUDA_TRY(poly_launch_load(pl, x, true, 0, (cudaStream_t)stream));
+        CIA_CUDA_TRY(gc_launch_load(pl, x, true, 0, (cudaStream_t)stream));
     } else {
         CIA_CUDA_TRY(launch_phasors_from_x(pl, x, true, 0, (cudaStream_t)stream));
     }
@@ -411,7 +411,7 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
     clear_error();
     cia_status st = check_device(pl);
     if (st != CIA_OK) return st;
-    if (pl->model != CIA_MODEL_POLYNOMIAL)
+    if (pl->model != CIA_MODEL_POLYNOMIAL || pl->gc_basis != 0)
         return fail(CIA_ERR_UNSUPPORTED, "rank-one link weights are for the polynomial models");
     const int64_t n = pl->n;
     if (alpha || beta) {
@@ -434,7 +434,7 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
     }
     pl->poly_weighted = alpha || beta;
     // the window holds one more row when weighted; the moments change
-    pl->staging = (pl->staging_req == 1 || !poly_window_fits(pl)) ? 1 : 2;
+    pl->staging = (pl->staging_req == 1 || !gc_window_fits(pl)) ? 1 : 2;
     pl->needs_load = true;
     invalidate_graphs(pl);
     return CIA_OK;
@@ -461,7 +461,7 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
     if (st != CIA_OK && st != CIA_ERR_UNSUPPORTED) return st;
     if (!x) return fail(CIA_ERR_INVALID_ARG, "x is NULL");
     if (steps < 1 || !std::isfinite(dt)) return fail(CIA_ERR_INVALID_ARG, "need steps >= 1 and a finite dt");
-    if (pl->model == CIA_MODEL_POLYNOMIAL) return fail(CIA_ERR_UNSUPPORTED, "no tuning candidates for the polynomial model");
+    if (pl->model == CIA_MODEL_POLYNOMIAL) return fail(CIA_ERR_UNSUPPORTED, "no tuning candidates for the polynomial and Fourier couplings");
     struct Cand { int tn, tib, staging; };
     std::vector<Cand> cands;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {

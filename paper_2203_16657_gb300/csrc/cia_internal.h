@@ -10,6 +10,10 @@
 
 #include "cia.h"
 
+// Features per node of the general separable couplings (general_coupling.cu):
+// 1, cos, sin of up to CIA_MAX_HARMONICS harmonics.
+#define CIA_GC_MAX_FEATURES (2 * CIA_MAX_HARMONICS + 1)
+
 namespace cia {
 
 // Thread-local error text behind cia_last_error().
@@ -97,6 +101,7 @@ struct DeviceBuffers {
     double *pl_y[2] = {nullptr, nullptr};     // [n+1] stage states
     double *pl_part[2] = {nullptr, nullptr};  // [T][p+1] sums of (beta) y^k per tile
     double *pl_alpha = nullptr, *pl_beta = nullptr;  // [n] rank-one link weights (permuted)
+    double *gc_f[2] = {nullptr, nullptr};     // Fourier basis: [n][K-1] features of pl_y
     // ensembles of independent networks
     void *tile_kn = nullptr;                  // [T] K / N_i of the tile's instance, compute precision
     int32_t *inst_tiles = nullptr;            // [B][4] community tiles [0,1), free tiles [2,3) of instance i
@@ -180,6 +185,10 @@ struct cia_plan {
     double poly_dv[CIA_MAX_POLY + 1] = {0};
     bool poly_general = false;          // g(x_l, x_m) instead of h(x_l - x_m)
     bool poly_weighted = false;         // rank-one link weights alpha_m beta_l
+    int gc_basis = 0;                   // general couplings: 0 polynomial, 1 real Fourier features
+    int gc_k = 2;                       // features per node incl. the constant
+    double gc_w = 0.0;                  // Fourier basis: pi / L
+    double gc_e[CIA_GC_MAX_FEATURES * CIA_GC_MAX_FEATURES] = {0};  // g = sum E_kj phi_k(u) phi_j(y)
     double poly_g[(CIA_MAX_POLY + 1) * (CIA_MAX_POLY + 1)] = {0};
     bool cs_has_basis = false;          // a basis was set (cia_plan_set_basis)
     bool cs_feat_valid = false;         // features/partials match the resident state
@@ -227,9 +236,9 @@ cudaError_t cs_launch_sample(cia_plan *pl, int slot, int64_t count, uint64_t see
 size_t cs_stage_smem_bytes(const cia_plan *pl);
 
 // Polynomial-coupling launchers (polynomial.cu).
-cudaError_t poly_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
-cudaError_t poly_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
-cudaError_t poly_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
-bool poly_window_fits(const cia_plan *pl);
+cudaError_t gc_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
+cudaError_t gc_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
+cudaError_t gc_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
+bool gc_window_fits(const cia_plan *pl);
 
 }  // namespace cia

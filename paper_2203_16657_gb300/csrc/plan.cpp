@@ -320,34 +320,80 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
         cp->model != CIA_MODEL_CUCKER_SMALE && cp->model != CIA_MODEL_POLYNOMIAL &&
-        cp->model != CIA_MODEL_POLYNOMIAL_GENERAL)
+        cp->model != CIA_MODEL_POLYNOMIAL_GENERAL && cp->model != CIA_MODEL_FOURIER_GENERAL)
         return fail(CIA_ERR_UNSUPPORTED, "unknown model");
-    if (cp->model == CIA_MODEL_POLYNOMIAL || cp->model == CIA_MODEL_POLYNOMIAL_GENERAL) {
+    if (cp->model == CIA_MODEL_POLYNOMIAL || cp->model == CIA_MODEL_POLYNOMIAL_GENERAL ||
+        cp->model == CIA_MODEL_FOURIER_GENERAL) {
         const bool general = cp->model == CIA_MODEL_POLYNOMIAL_GENERAL;
+        const bool fourier = cp->model == CIA_MODEL_FOURIER_GENERAL;
         if (pl->precision != CIA_FP64)
-            return fail(CIA_ERR_UNSUPPORTED, "the polynomial model runs in FP64 (precision CIA_FP64)");
-        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial model");
-        if (cp->p < 0 || cp->p > CIA_MAX_POLY) return fail(CIA_ERR_INVALID_ARG, "p must be in [0, CIA_MAX_POLY]");
+            return fail(CIA_ERR_UNSUPPORTED, "the polynomial and Fourier couplings run in FP64 (precision CIA_FP64)");
+        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial and Fourier couplings");
+        if (!fourier && (cp->p < 0 || cp->p > CIA_MAX_POLY))
+            return fail(CIA_ERR_INVALID_ARG, "p must be in [0, CIA_MAX_POLY]");
+        if (fourier && (cp->p < 1 || cp->p > CIA_MAX_HARMONICS))
+            return fail(CIA_ERR_INVALID_ARG, "p must be in [1, CIA_MAX_HARMONICS]");
         if (!std::isfinite(cp->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
-        constexpr int S = CIA_MAX_POLY + 1;
+        constexpr int S = CIA_MAX_POLY + 1, SH = CIA_MAX_HARMONICS + 1;
         for (int k = 0; k < S; ++k) {
-            if ((!general && !std::isfinite(cp->poly_c[k])) || !std::isfinite(cp->dV[k]))
+            if ((!general && !fourier && !std::isfinite(cp->poly_c[k])) || !std::isfinite(cp->dV[k]))
                 return fail(CIA_ERR_NUMERIC, "a polynomial coefficient is not finite");
             for (int b = 0; general && b < S; ++b)
                 if (!std::isfinite(cp->poly_g[k * S + b]))
                     return fail(CIA_ERR_NUMERIC, "a polynomial coefficient is not finite");
         }
+        if (fourier) {
+            if (!std::isfinite(cp->fourier_L) || !(cp->fourier_L > 0.0))
+                return fail(CIA_ERR_INVALID_ARG, "fourier_L must be positive and finite");
+            for (int q = 0; q < 4; ++q)
+                for (int i = 0; i < SH * SH; ++i)
+                    if (!std::isfinite(cp->fourier_c[q][i]))
+                        return fail(CIA_ERR_NUMERIC, "a Fourier coefficient is not finite");
+        }
         if (pl->tile_nodes > 256)
-            return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be <= 256 for the polynomial model");
-        pl->model = CIA_MODEL_POLYNOMIAL;
+            return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be <= 256 for the polynomial and Fourier couplings");
+        pl->model = CIA_MODEL_POLYNOMIAL;   // one kernel family for the three
         pl->poly_general = general;
+        pl->gc_basis = fourier ? 1 : 0;
         pl->p = 1;
-        pl->poly_p = std::max(cp->p, 1);   // kernels of degree 1..4; coefficients above p are zero
+        pl->poly_p = fourier ? cp->p : std::max(cp->p, 1);   // degree 1..4 (coefficients above p are zero)
+        pl->gc_k = fourier ? 2 * cp->p + 1 : pl->poly_p + 1;
         for (int k = 0; k < S; ++k) {
-            pl->poly_c[k] = !general && k <= cp->p ? cp->poly_c[k] : 0.0;
+            pl->poly_c[k] = !general && !fourier && k <= cp->p ? cp->poly_c[k] : 0.0;
             pl->poly_dv[k] = cp->dV[k];
             for (int b = 0; b < S; ++b)
                 pl->poly_g[k * S + b] = general && k <= cp->p && b <= cp->p ? cp->poly_g[k * S + b] : 0.0;
+        }
+        // g(u, y) = sum_{k,j} E_kj phi_k(u) phi_j(y)
+        constexpr int F = CIA_GC_MAX_FEATURES;
+        std::fill(pl->gc_e, pl->gc_e + F * F, 0.0);
+        if (fourier) {
+            // phi = (1, cos wu, sin wu, cos 2wu, ...): cos(a w u) is feature 2a - 1
+            // (the constant for a = 0), sin(a w u) feature 2a; sin 0 = 0 drops out
+            pl->gc_w = 3.14159265358979323846 / cp->fourier_L;
+            auto ci = [](int a) { return a == 0 ? 0 : 2 * a - 1; };
+            auto si = [](int a) { return 2 * a; };
+            for (int a = 0; a <= cp->p; ++a)
+                for (int b = 0; b <= cp->p; ++b) {
+                    const int i = a * SH + b;
+                    pl->gc_e[ci(a) * F + ci(b)] += cp->fourier_c[0][i];
+                    if (b) pl->gc_e[ci(a) * F + si(b)] += cp->fourier_c[1][i];
+                    if (a) pl->gc_e[si(a) * F + ci(b)] += cp->fourier_c[2][i];
+                    if (a && b) pl->gc_e[si(a) * F + si(b)] += cp->fourier_c[3][i];
+                }
+        } else {
+            // G itself, or h(u - y) = sum_a c_a (u - y)^a regrouped by the power of u:
+            // E_kj = c_{k+j} binom(k+j, k) (-1)^j
+            for (int k = 0; k < S; ++k)
+                for (int j = 0; j < S; ++j) {
+                    if (general) {
+                        pl->gc_e[k * F + j] = pl->poly_g[k * S + j];
+                    } else if (k + j < S) {
+                        double binom = 1.0;
+                        for (int q = 1; q <= k; ++q) binom = binom * (double)(j + q) / (double)q;
+                        pl->gc_e[k * F + j] = pl->poly_c[k + j] * binom * ((j & 1) ? -1.0 : 1.0);
+                    }
+                }
         }
         pl->K = cp->K;
     } else if (cp->model == CIA_MODEL_CUCKER_SMALE) {
@@ -594,6 +640,9 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         if ((s2 = alloc_bytes(pl, &d.acc, n * sizeof(double))) != CIA_OK) return s2;
         for (int b = 0; b < 2; ++b)
             if ((s2 = upload<double>(pl, &d.pl_y[b], nullptr, (size_t)n + 1)) != CIA_OK) return s2;
+        if (pl->gc_basis == 1)
+            for (int b = 0; b < 2; ++b)
+                if ((s2 = upload<double>(pl, &d.gc_f[b], nullptr, (size_t)n * (pl->gc_k - 1))) != CIA_OK) return s2;
     } else if (pl->model != CIA_MODEL_CUCKER_SMALE) {
         if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
         if ((s2 = alloc_bytes(pl, &d.acc, n * rb)) != CIA_OK) return s2;
@@ -746,7 +795,7 @@ static cia_status build_tiles(cia_plan *pl) {
         pl->cs_feat_valid = false;
     } else if (pl->model == CIA_MODEL_POLYNOMIAL) {
         for (int b = 0; b < 2; ++b)
-            if ((s2 = upload<double>(pl, &d.pl_part[b], nullptr, (size_t)T * (pl->poly_p + 1), true)) != CIA_OK)
+            if ((s2 = upload<double>(pl, &d.pl_part[b], nullptr, (size_t)T * pl->gc_k, true)) != CIA_OK)
                 return s2;
     } else {
         for (int b = 0; b < 2; ++b)
@@ -785,7 +834,7 @@ static cia_status build_tiles(cia_plan *pl) {
     if (pl->model == CIA_MODEL_POLYNOMIAL) {
         // its own one-CTA-per-tile kernel: community window in shared memory
         // (auto, window, pipeline) or plain loads (plain, or when it does not fit)
-        pl->staging = (pl->staging == 1 || !poly_window_fits(pl)) ? 1 : 2;
+        pl->staging = (pl->staging == 1 || !gc_window_fits(pl)) ? 1 : 2;
     }
     if (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) {
         UPT(d.tile_desc, tdesc.data(), tdesc.size());
@@ -1040,7 +1089,9 @@ extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *inf
     info->staging = pl->staging;
     info->group_size_direct = pl->group_size_direct;
     info->max_tile_index_bytes = pl->max_tile_idx_bytes;
-    info->model = pl->poly_general ? CIA_MODEL_POLYNOMIAL_GENERAL : pl->model;
+    info->model = pl->gc_basis == 1 ? CIA_MODEL_FOURIER_GENERAL
+                  : pl->poly_general  ? CIA_MODEL_POLYNOMIAL_GENERAL
+                                      : pl->model;
     info->state_dim = pl->state_dim;
     info->instances = pl->B;
     return CIA_OK;

@@ -1,5 +1,6 @@
-"""Parity of the CUDA polynomial-coupling path (moments of x, App. A.3;
-Desai--Zwanzig, App. A.5) with the FP64 oracle, through the C ABI.
+"""Parity of the CUDA general-coupling path (polynomial moments, App. A.3;
+Desai--Zwanzig, App. A.5; rank-one weights; real 2-D Fourier series) with the
+FP64 oracle, through the C ABI.
 
 Tolerances (written here, derived from the arithmetic): the path is FP64
 throughout; the moment expansion cancels terms of size lambda max|x|^p against
@@ -420,6 +421,115 @@ def test_weights_rejections(cia, torch_mod):
     plan.set_weights(None, np.ones(g.n))
     with pytest.raises(cia.CiaError, match="load"):
         plan.advance(0.01, 1)
+
+
+# ------------------------------------------------------------------ general real 2-D Fourier coupling
+
+def make_fourier(cia, g, K, L, C, dv, **kw):
+    return cia.Plan(g.rowptr, g.col, g.labels, None, model="fourier_general", K=K, fourier_L=L,
+                    fourier_C=C, dV=dv, precision="fp64", build_direct=True, **kw)
+
+
+def fourier_err(oracle_mod, g, x, got, ref, L, C, dv):
+    pot = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 0.0, L, C, dv)
+    return coupling_rel_err(got, ref, pot)
+
+
+@pytest.mark.parametrize("staging", ["auto", "plain"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_fourier_rhs_harmonics(cia, oracle_mod, torch_mod, p, staging):
+    g = S.sbm_graph([300, 129, 31, 200], 0.85, inter_degree=6.0, seed=90 + p, n_free=25)
+    rng = np.random.default_rng(300 + p)
+    C = [rng.normal(size=(p + 1, p + 1)) for _ in range(4)]
+    dv = (0.2, -1.0, 0.0, 0.5)
+    L = 2.0
+    x = rng.uniform(-2.5, 2.5, g.n)
+    plan = make_fourier(cia, g, 1.4, L, C, dv, tile_nodes=128, staging=staging)
+    info = plan.info()
+    assert info["model"] == 5 and info["staging"] == (1 if staging == "plain" else 2)
+    ref = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 1.4, L, C, dv)
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        assert fourier_err(oracle_mod, g, x, got, ref, L, C, dv) < FP64_TOL, method
+
+
+def test_fourier_sine_of_difference_matches_kuramoto_plan(cia, torch_mod):
+    """sin(w(u - y)) through the general series equals the FP64 Kuramoto plan
+    on the phases w x."""
+    g = S.sbm_graph([200, 90, 31], 0.85, inter_degree=4.0, seed=14, n_free=7)
+    L = 1.5
+    x = np.random.default_rng(15).uniform(-L, L, g.n)
+    C = [np.zeros((2, 2)) for _ in range(4)]
+    C[2][1, 1], C[1][1, 1] = 1.0, -1.0
+    four = gpu_rhs(torch_mod, make_fourier(cia, g, 2.0, L, C, (0.0,)), x, "cia")
+    kplan = cia.Plan(g.rowptr, g.col, g.labels, np.zeros(g.n), K=2.0, precision="fp64")
+    kur = gpu_rhs(torch_mod, kplan, np.pi * x / L, "cia")
+    assert np.abs(four - kur).max() < 1e-12 * np.abs(kur).max()
+
+
+@pytest.mark.parametrize("case", ["all_free", "single_node", "singletons", "complete"])
+def test_fourier_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
+    if case == "all_free":
+        g = S.random_labels_graph(30, 0.3, 1, seed=1, free_frac=1.0)
+    elif case == "single_node":
+        g = S.Graph(1, np.array([0, 0], np.int64), np.zeros(0, np.int32),
+                    np.array([0], np.int32), np.array([1], np.int64))
+    elif case == "singletons":
+        g = S.random_labels_graph(25, 0.5, 1, seed=5, free_frac=0.0)
+        g.labels = np.arange(g.n, dtype=np.int32)
+    else:
+        g = S.complete_graph_communities([17, 5, 1], seed=6)
+    rng = np.random.default_rng(16)
+    C = [rng.normal(size=(3, 3)) for _ in range(4)]
+    x = rng.uniform(-3, 3, g.n)
+    plan = make_fourier(cia, g, 1.5, 3.0, C, (0.3, -1.0))
+    ref = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 1.5, 3.0, C, (0.3, -1.0))
+    pot = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 0.0, 3.0, C, (0.3, -1.0))
+    for method in ("cia", "direct"):
+        got = gpu_rhs(torch_mod, plan, x, method)
+        if np.abs(ref - pot).max() == 0:
+            assert np.abs(got - ref).max() <= 1e-15 * max(1.0, np.abs(ref).max()), method
+        else:
+            assert coupling_rel_err(got, ref, pot) < FP64_TOL, method
+
+
+def test_fourier_integrate(cia, oracle_mod, torch_mod):
+    """40 RK4 steps of a two-harmonic coupling with a confining potential,
+    CUDA-graph replay and plain launches, against the oracle's RK4."""
+    g = S.sbm_graph([400, 200, 77], 0.8, inter_degree=5.0, seed=51, n_free=19)
+    rng = np.random.default_rng(17)
+    x0 = rng.uniform(-1.5, 1.5, g.n)
+    C = [0.5 * rng.normal(size=(3, 3)) for _ in range(4)]
+    K, L, dt = 2.0, 2.0, 0.01
+    rhs = lambda y: oracle_mod.fourierg_direct(g.rowptr, g.col, y, K, L, C, DW_DV)
+    ref, _ = oracle_mod.integrate(rhs, x0, dt, 40, wrap=False)
+    for graphs in (True, False):
+        plan = make_fourier(cia, g, K, L, C, DW_DV, use_graphs=graphs)
+        for method in ("cia", "direct"):
+            x = torch_mod.from_numpy(x0.copy()).cuda()
+            plan.state_load(x)
+            for _ in range(4):
+                plan.advance(dt, 10, method=method)
+            plan.state_store(x)
+            assert np.abs(x.cpu().numpy() - ref).max() < 1e-11 * np.abs(ref).max(), (graphs, method)
+
+
+def test_fourier_rejections(cia):
+    g = S.sbm_graph([40, 30], 0.8, inter_degree=2.0, seed=1, n_free=3)
+    C = [np.zeros((2, 2)) for _ in range(4)]
+    with pytest.raises(cia.CiaError, match="fourier_L"):
+        make_fourier(cia, g, 1.0, 0.0, C, (0.0,))
+    with pytest.raises(ValueError):
+        make_fourier(cia, g, 1.0, 1.0, [np.zeros((1, 1))] * 4, (0.0,))
+    with pytest.raises(ValueError):
+        make_fourier(cia, g, 1.0, 1.0, C[:3], (0.0,))
+    bad = [c.copy() for c in C]
+    bad[3][1, 1] = np.nan
+    with pytest.raises(cia.CiaError, match="finite"):
+        make_fourier(cia, g, 1.0, 1.0, bad, (0.0,))
+    plan = make_fourier(cia, g, 1.0, 1.0, C, (0.0,))
+    with pytest.raises(cia.CiaError, match="polynomial"):
+        plan.set_weights(np.ones(g.n), None)
 
 
 # ------------------------------------------------------------------ errors
