@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "cia_internal.h"
 
@@ -224,13 +225,22 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
     const int cap = a.win_cap;
     long long *wfix = reinterpret_cast<long long *>(win);   // the window after conversion
     double unit[NR];                                         // 2^E per row
-    // the NR terms of node l: beta_l^[WT] phi_k(x_l)
-    auto terms = [&](int64_t l, double (&q)[NR]) {
-        double f[K];
-        node_features<B, K>(a, l, f);
-        const double wl = WT ? __ldg(a.beta + l) : 1.0;
+    // the NR terms of node l: beta_l^[WT] phi_k(x_l), from its state (powers)
+    // or its stored features
+    const double *yv = a.y_in, *fv = a.f_in, *bv = a.beta;
+    auto terms = [yv, fv, bv](int64_t l, double (&q)[NR]) {
+        if constexpr (B == kPoly) {
+            const double u = __ldg(yv + l);
+            double v = WT ? __ldg(bv + l) : u;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) q[r] = WT ? wl * f[r + A0] : f[r + A0];
+            for (int r = 0; r < NR; ++r) {
+                q[r] = v;
+                if (r + 1 < NR) v *= u;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) q[r] = __ldg(fv + l * (K - 1) + r);
+        }
     };
     // (0) window of features and their largest magnitudes, moments (FP64 over
     // the community's tiles)
@@ -301,29 +311,35 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
         }
         int mc = 0, ic = 0;
         const uint4 *mv = mvec + sd.x + lane;
-        for (uint32_t j = 0; j < sd.y; ++j) {
-            const uint4 q = __ldg(mv + 32 * j);
-            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        // one loop per source of the community's features (the fixed-point
+        // window or global memory), so that neither carries the other's work
+        auto missing = [&](auto windowed) {
+            for (uint32_t j = 0; j < sd.y; ++j) {
+                const uint4 q = __ldg(mv + 32 * j);
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+                for (int e = 0; e < 4; ++e) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int l = (int)(h ? w4[e] >> 16 : w4[e] & 0xffffu);
-                    if (l < lam) {
-                        ++mc;
-                        if (cap) {
+                    for (int h = 0; h < 2; ++h) {
+                        const int l = (int)(h ? w4[e] >> 16 : w4[e] & 0xffffu);
+                        if (l < lam) {
+                            ++mc;
+                            if constexpr (decltype(windowed)::value) {
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) mfix[r] += wfix[r * cap + l];
-                        } else {
-                            double tq[NR];
-                            terms(d.lo + l, tq);
+                                for (int r = 0; r < NR; ++r) mfix[r] += wfix[r * cap + l];
+                            } else {
+                                double tq[NR];
+                                terms(d.lo + l, tq);
 #pragma unroll
-                            for (int r = 0; r < NR; ++r) ms[r] += tq[r];
+                                for (int r = 0; r < NR; ++r) ms[r] += tq[r];
+                            }
                         }
                     }
                 }
             }
-        }
+        };
+        if (cap) missing(std::true_type{});
+        else missing(std::false_type{});
         const int4 *iv = ivec + sd.z + lane;
         for (uint32_t j = 0; j < sd.w; ++j) {
             const int4 q = __ldg(iv + 32 * j);
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
         wnode = WT ? a.beta[m] : 1.0;
         if (comm)
 #pragma unroll
-            for (int k = 0; k < K; ++k) T[k] += W[k] - wnode * ph[k];   // the diagonal term
+            for (int k = 0; k < K; ++k) T[k] += W[k] - (WT ? wnode * ph[k] : ph[k]);   // the diagonal term
         double e[K];
         coefficients<K>(a, ph, e);
         double coup = 0.0;
@@ -392,42 +408,57 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
 // Direct method, one CTA per tile: `group` threads per row evaluate the
 // coupling link by link over the row's CSR neighbours (rows padded to 4-entry
 // vectors with the sentinel n): h(x_l - x_m) for the polynomial difference
-// form, else sum_k e_k(x_m) phi_k(x_l); times beta_l and finally alpha_m when
-// the links are weighted; then the same update and feature sums as the CIA.
-template <int MODE, int B, int K>
+// form (DIFF), else sum_k e_k(x_m) phi_k(x_l); times beta_l and finally
+// alpha_m when the links are weighted; then the same update and feature sums
+// as the CIA.
+template <int MODE, int B, int K, bool DIFF>
 __global__ void __launch_bounds__(kThreads) gc_direct_kernel(const GcParams a) {
-    __shared__ double sW[kMaxK * kThreads];
+    __shared__ double sW[K * kThreads];   // row sums, then the tile's feature sums
     const int t = blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const int G = a.group, gl = threadIdx.x % G, grp = threadIdx.x / G, ngrp = kThreads / G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
     const int4 *col4 = reinterpret_cast<const int4 *>(a.full_col);
+    const double *yv = a.y_in, *bv = a.beta;
+    const int64_t n = a.n;
     for (int r = grp; r < d.count; r += ngrp) {
         const int64_t m = d.first + r;
-        const double y = a.y_in[m];
-        double ph[K], e[K];
-        node_features<B, K>(a, m, ph);
-        coefficients<K>(a, ph, e);
-        double s = 0.0;
-        for (int64_t v = a.full_rowptr[m] / 4 + gl; v < a.full_rowptr[m + 1] / 4; v += G) {
-            const int4 q = __ldg(col4 + v);
-            const int l4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (l4[k] < a.n) {
-                    double gv;
-                    if (B == kPoly && a.diff) {
-                        gv = horner<K - 1>(a.c, __ldg(a.y_in + l4[k]) - y);
-                    } else {
-                        double f[K];
-                        node_features<B, K>(a, l4[k], f);
-                        gv = 0.0;
-#pragma unroll
-                        for (int j = 0; j < K; ++j) gv = fma(e[j], f[j], gv);
-                    }
-                    s += a.beta ? __ldg(a.beta + l4[k]) * gv : gv;
-                }
+        const double y = yv[m];
+        double e[K];
+        if constexpr (!DIFF) {
+            double ph[K];
+            node_features<B, K>(a, m, ph);
+            coefficients<K>(a, ph, e);
         }
+        const int64_t v0 = a.full_rowptr[m] / 4 + gl, v1 = a.full_rowptr[m + 1] / 4;
+        // one loop per weighting, so that the unweighted one carries no weight loads
+        auto row_sum = [&](auto weighted) {
+            double s = 0.0;
+            for (int64_t v = v0; v < v1; v += G) {
+                const int4 q = __ldg(col4 + v);
+                const int l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (l4[k] < n) {
+                        double gv;
+                        if constexpr (DIFF) {
+                            gv = horner<K - 1>(a.c, __ldg(yv + l4[k]) - y);
+                        } else if constexpr (B == kPoly) {
+                            gv = horner<K - 1>(e, __ldg(yv + l4[k]));   // sum_k e_k u^k
+                        } else {
+                            double f[K];
+                            node_features<B, K>(a, l4[k], f);
+                            gv = 0.0;
+#pragma unroll
+                            for (int j = 0; j < K; ++j) gv = fma(e[j], f[j], gv);
+                        }
+                        if constexpr (decltype(weighted)::value) gv *= __ldg(bv + l4[k]);
+                        s += gv;
+                    }
+            }
+            return s;
+        };
+        double s = bv ? row_sum(std::true_type{}) : row_sum(std::false_type{});
         for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (gl == 0) sW[r] = s;
     }
@@ -436,11 +467,11 @@ __global__ void __launch_bounds__(kThreads) gc_direct_kernel(const GcParams a) {
     const int64_t m = d.first + threadIdx.x;
     double ynext = 0.0, wnode = 0.0;
     if (live) {
-        const double x = a.y_in[m];
+        const double x = yv[m];
         const double coup = a.alpha ? a.alpha[m] * sW[threadIdx.x] : sW[threadIdx.x];
         const double kd = -horner<kMaxP>(a.v, x) + a.k_over_n * coup;
         ynext = rk4_update<MODE>(a, m, kd);
-        wnode = a.beta ? a.beta[m] : 1.0;
+        wnode = bv ? bv[m] : 1.0;
     }
     if (MODE == kRhs) return;
     next_features<B, K>(a, t, m, live, ynext, wnode, sW);
@@ -450,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) gc_direct_kernel(const GcParams a) {
 // its features and their tile sums.  One CTA per tile.
 template <int B, int K>
 __global__ void __launch_bounds__(kThreads) gc_load_kernel(const GcParams a, const double *x, double *master) {
-    __shared__ double scratch[kMaxK * kThreads];
+    __shared__ double scratch[K * kThreads];
     const int t = blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const bool live = threadIdx.x < d.count;
@@ -534,7 +565,11 @@ cudaError_t launch(void (*kernel)(GcParams), const cia_plan *pl, size_t smem, co
 template <int MODE, int B, int K>
 cudaError_t launch_shape(const cia_plan *pl, int method, const GcParams &a, cudaStream_t s) {
     constexpr int id = (B * kMaxK + K) * 3 + MODE;   // distinct per (MODE, B, K)
-    if (method == Method::DIRECT) return launch<4 * id>(gc_direct_kernel<MODE, B, K>, pl, 0, a, s);
+    if (method == Method::DIRECT) {
+        if constexpr (B == kPoly)
+            if (a.diff) return launch<4 * id + 3>(gc_direct_kernel<MODE, B, K, true>, pl, 0, a, s);
+        return launch<4 * id>(gc_direct_kernel<MODE, B, K, false>, pl, 0, a, s);
+    }
     if constexpr (B == kPoly)
         if (pl->poly_weighted) return launch<4 * id + 1>(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
     return launch<4 * id + 2>(gc_stage_kernel<MODE, B, K, false>, pl, stage_smem(pl), a, s);
