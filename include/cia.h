@@ -199,6 +199,48 @@ const char *cia_last_error(void);
 
 /* ---- planning: step P1 (Sec. 3.1, App. A.1), offline and untimed --------- */
 
+/* Community detection for step P1 (Sec. "Community Detection (P1)"): labels
+ * that make S sparse, by minimising the Potts Hamiltonian with the
+ * Erdos-Renyi null model (the rber_pots objective the paper recommends)
+ *   H = -sum_{m != l} (a_ml - gamma p) delta(c_m, c_l) + mu M,
+ * p = 2|E| / (N (N - 1)) the link density, M the number of communities and
+ * mu = community_cost an extra charge per community: the paper notes that
+ * the E1 work grows with the number of communities, so that fewer, larger
+ * communities can pay off, more so for a high expansion order.  With
+ * gamma p = 1/2 and mu = 0, H = nnz(S)/2 - |E|: H then counts the entries of
+ * S exactly.  Optimisation: local moving of single nodes to the neighbouring
+ * community with the largest decrease of H, in a seeded random order, then
+ * aggregation of the communities into weighted nodes and again (the Louvain
+ * scheme), then a last local-moving pass over the original nodes, so that
+ * no single-node move lowers H.  Host code (offline, like the rest of P1).
+ * labels: host, g->n entries, written: 0..M-1 in order of first appearance,
+ * -1 for nodes in communities smaller than min_size (no community, Sec. 3.1). */
+typedef struct {
+    double gamma;               /* resolution, > 0; 1 = the paper's choice */
+    double community_cost;      /* mu >= 0, in units of directed entries of a_ml */
+    int min_size;               /* >= 1; smaller communities come back as -1 */
+    int max_levels;             /* aggregation levels, >= 1 */
+    uint64_t seed;              /* visiting order */
+} cia_detect_options;
+
+typedef struct {
+    int64_t communities;        /* labelled communities returned (M) */
+    int64_t unlabelled;         /* nodes returned as -1 */
+    int64_t nnz_missing;        /* -1 entries of S for the returned labels (directed, no diagonal) */
+    int64_t nnz_inter;          /* +1 entries of S for the returned labels (directed) */
+    double hamiltonian;         /* H of the optimised partition (before the min_size relabelling) */
+    int levels;                 /* aggregation levels run */
+    int64_t moves;              /* single-node moves made, all levels */
+} cia_detect_report;
+
+/* Defaults: gamma 1, community_cost 0, min_size 2, max_levels 8, seed 0. */
+void cia_detect_options_default(cia_detect_options *opt);
+
+/* CIA_ERR_INVALID_GRAPH as cia_plan_create; CIA_ERR_INVALID_ARG for bad
+ * options or NULL pointers.  report may be NULL. */
+cia_status cia_detect_communities(const cia_graph *g, const cia_detect_options *opt, int32_t *labels,
+                                  cia_detect_report *report);
+
 /* Build a plan for graph g with the given community labels.
  *
  * community: host, g->n entries; community[i] in [0, M) names the block of

@@ -421,6 +421,44 @@ def fourierg_cia(sp: Split, x_perm, K, L, C, dv) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Community detection objective (Sec. "Community Detection (P1)")
+# --------------------------------------------------------------------------
+
+def potts_hamiltonian(rowptr, col, labels, gamma, mu=0.0) -> float:
+    """H = -sum_{m != l} (a_ml - gamma p) delta(c_m, c_l) + mu M with the
+    Erdos-Renyi null model p = nnz(A) / (N (N - 1)); labels >= 0 name the
+    communities (every label is a community, also of size one)."""
+    rowptr, col = _i64(rowptr), _i32(col)
+    labels = np.asarray(labels, dtype=np.int64)
+    n = len(labels)
+    p = len(col) / (n * (n - 1)) if n > 1 else 0.0
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    e_in = int(np.sum(labels[rows] == labels[col]))
+    _, sizes = np.unique(labels, return_counts=True)
+    pairs = float(np.sum(sizes.astype(np.float64) * (sizes - 1)))
+    return -e_in + gamma * p * pairs + mu * len(sizes)
+
+
+def best_single_move_gain(rowptr, col, labels, gamma, mu=0.0) -> float:
+    """Largest decrease of H over all moves of one node to the community of a
+    neighbour or to a new community of its own, each H evaluated in full by
+    potts_hamiltonian (brute force, small graphs)."""
+    labels = np.asarray(labels, dtype=np.int64).copy()
+    h0 = potts_hamiltonian(rowptr, col, labels, gamma, mu)
+    fresh = labels.max() + 1
+    best = 0.0
+    for m in range(len(labels)):
+        own = labels[m]
+        cands = set(int(labels[l]) for l in col[rowptr[m]:rowptr[m + 1]]) | {int(fresh)}
+        cands.discard(int(own))
+        for c in cands:
+            labels[m] = c
+            best = max(best, h0 - potts_hamiltonian(rowptr, col, labels, gamma, mu))
+        labels[m] = own
+    return best
+
+
+# --------------------------------------------------------------------------
 # Time stepping and observables
 # --------------------------------------------------------------------------
 

@@ -14,7 +14,7 @@ import numpy as np
 from . import _abi
 from ._abi import CiaError, load
 
-__all__ = ["Plan", "Basis", "CiaError", "load", "status_string"]
+__all__ = ["Plan", "Basis", "CiaError", "load", "status_string", "detect_communities"]
 
 
 def status_string(status: int) -> str:
@@ -35,6 +35,24 @@ def _dev_ptr(t, dtype_name: str, n: int) -> ctypes.c_void_p:
     if t.dtype != want or not t.is_contiguous() or t.numel() != n:
         raise ValueError("expected a contiguous %s tensor of %d elements" % (dtype_name, n))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def detect_communities(rowptr, col, *, gamma=1.0, community_cost=0.0, min_size=2, max_levels=8, seed=0):
+    """Community labels for step P1 that make S sparse (include/cia.h,
+    cia_detect_communities): the Potts Hamiltonian with the Erdos-Renyi null
+    model, optimised by local moving and aggregation on the host.  Returns
+    (labels int32 with -1 for communities below min_size, report dict)."""
+    lib = load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(rowptr) - 1
+    g = _abi.Graph(n, rowptr.ctypes.data, col.ctypes.data)
+    opt = _abi.DetectOptions(float(gamma), float(community_cost), int(min_size), int(max_levels), int(seed))
+    labels = np.empty(n, dtype=np.int32)
+    rep = _abi.DetectReport()
+    _abi.check(lib.cia_detect_communities(ctypes.byref(g), ctypes.byref(opt), labels.ctypes.data,
+                                          ctypes.byref(rep)))
+    return labels, {name: getattr(rep, name) for name, _ in _abi.DetectReport._fields_}
 
 
 class Plan:

@@ -69,6 +69,17 @@ class PlanInfo(ctypes.Structure):
                 ("state_dim", ctypes.c_int), ("instances", ctypes.c_int64)]
 
 
+class DetectOptions(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("community_cost", ctypes.c_double),
+                ("min_size", ctypes.c_int), ("max_levels", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class DetectReport(ctypes.Structure):
+    _fields_ = [("communities", ctypes.c_int64), ("unlabelled", ctypes.c_int64),
+                ("nnz_missing", ctypes.c_int64), ("nnz_inter", ctypes.c_int64),
+                ("hamiltonian", ctypes.c_double), ("levels", ctypes.c_int), ("moves", ctypes.c_int64)]
+
+
 class TuneReport(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int), ("tile_nodes", ctypes.c_int),
                 ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int),
@@ -126,6 +137,8 @@ SIGNATURES = {
     "cia_plan_create_batch": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, ctypes.POINTER(Coupling),
                                              ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "cia_plan_retile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cia_detect_options_default": (None, [_P]),
+    "cia_detect_communities": (ctypes.c_int, [_P, _P, _P, _P]),
     "cia_plan_set_weights": (ctypes.c_int, [_P, _P, _P]),
     "cia_plan_autotune": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int64,
                                          ctypes.POINTER(TuneReport), _P]),

@@ -221,6 +221,9 @@ size_t window_smem_bytes(const cia_plan *pl);
 
 // Drop the cached CUDA graph of an RK4 step (api.cu).
 void invalidate_graphs(cia_plan *pl);
+
+// Checks a graph as cia_plan_create does (plan.cpp); sets the error message.
+cia_status validate_graph(const cia_graph *g);
 // Order parameters of every instance of the state in slot `slot`:
 // r_base[counter * B + i], then ++counter (kuramoto.cu).
 cudaError_t launch_order_parameters(cia_plan *pl, int slot, double *r_base, cudaStream_t s);

@@ -46,7 +46,7 @@ static cia_status fail(cia_status s, const std::string &msg) {
 // rows are visited in increasing order, so the entries (j, i) with i < j of
 // row j are met in increasing i; a cursor per row checks they appear exactly
 // in that order, and at the end every entry below the diagonal was matched.
-static cia_status validate_graph(const cia_graph *g) {
+cia_status validate_graph(const cia_graph *g) {
     const int64_t n = g->n;
     if (g->rowptr[0] != 0) return fail(CIA_ERR_INVALID_GRAPH, "rowptr[0] != 0");
     for (int64_t i = 0; i < n; ++i)

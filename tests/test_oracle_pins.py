@@ -634,3 +634,32 @@ def test_fourier_general_cia_equals_direct(oracle_mod, p):
     sp = oracle_mod.split(g.rowptr, g.col, g.labels)
     got = oracle_mod.fourierg_cia(sp, x[sp.perm], 1.2, 2.0, C, dv)[sp.iperm]
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ------------------------------------------------ community detection objective
+
+def test_potts_hamiltonian_counts_s_at_half_density(oracle_mod):
+    """With gamma p = 1/2 and mu = 0, H = nnz(S)/2 - |E|, nnz(S) counted from the
+    oracle's own split of B = D + S (missing without the diagonal, plus inter)."""
+    import synthetic as S
+    for seed in range(3):
+        g = S.random_labels_graph(60, 0.2, 4, seed=90 + seed, free_frac=0.0)
+        n, nnz = g.n, len(g.col)
+        gamma = 0.5 / (nnz / (n * (n - 1)))
+        sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+        nnz_s = int(np.sum(sp.s_val != 0)) - int(np.sum((sp.s_val == -1) & (sp.s_col == np.repeat(
+            np.arange(n), np.diff(sp.s_rowptr)))))   # without the diagonal -1 entries
+        h = oracle_mod.potts_hamiltonian(g.rowptr, g.col, g.labels, gamma)
+        assert abs(h - (nnz_s / 2 - nnz / 2)) < 1e-9
+
+
+def test_potts_hamiltonian_special_partitions(oracle_mod):
+    """Singletons: H = mu N.  One community of a complete graph (p = 1):
+    H = (gamma - 1) N (N - 1) + mu."""
+    import synthetic as S
+    g = S.random_labels_graph(30, 0.3, 2, seed=3, free_frac=0.0)
+    assert oracle_mod.potts_hamiltonian(g.rowptr, g.col, np.arange(g.n), 1.0, 0.7) == pytest.approx(0.7 * g.n)
+    n = 12
+    rowptr, col = complete_csr(n)
+    h = oracle_mod.potts_hamiltonian(rowptr, col, np.zeros(n), 1.3, 2.0)
+    assert h == pytest.approx((1.3 - 1) * n * (n - 1) + 2.0)
