@@ -128,6 +128,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ byte model
 
+def max_over_ranks(torch, dist, world: int, v: float, device) -> float:
+    """The largest value over the ranks (the slowest rank's time); each rank
+    passes its own.  One scalar all-reduce outside every timed region."""
+    if world == 1:
+        return float(v)
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job units per second: every rank processes its own copy of the
+    workload (replicas, weak scaling), the job ends with the slowest rank."""
+    return world * units_per_rank * steps / max_seconds
+
+
 def stage_bytes(info: dict, precision: str) -> float:
     """Algorithmic (compulsory) bytes of one CIA stage launch, averaged over
     the four RK4 stages.
@@ -615,12 +631,8 @@ def main():
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms, prof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "cia", flush, True)
     barrier()
-    total_ms = float(sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * g.n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(torch, dist, world, float(sum(ms)), "cuda")
+    value = job_throughput(g.n, args.steps, world, total_ms / 1e3)
 
     # direct method, same GPU, same steps
     dtotal, dprof = None, None
@@ -636,10 +648,11 @@ def main():
         for _ in range(args.warmup):
             plan.integrate_host(xh, w.dt, 1, r_out=rh)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.integrate_host(xh, w.dt, 1, r_out=rh)
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(torch, dist, world, time.perf_counter() - t0, "cuda")
 
     if rank != 0:
         if world > 1:
@@ -690,7 +703,7 @@ def main():
                                  "direct_rhs_coupling_rel": err.get("direct")},
         "direct": direct,
         "e2e": None if e2e_s is None else {
-            "value": g.n * args.steps / e2e_s, "unit": UNIT,
+            "value": job_throughput(g.n, args.steps, world, e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
