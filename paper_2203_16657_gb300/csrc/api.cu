@@ -57,7 +57,7 @@ cia_status check_plan(cia_plan *pl, int method) {
         return fail(CIA_ERR_UNSUPPORTED, "communities above 65536 nodes are not supported");
     int optin = 0;
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
-    // the polynomial stage kernel reads oversized communities from global memory
+    // the general-coupling stage kernel reads oversized communities from global memory
     if (pl->model == CIA_MODEL_POLYNOMIAL) return CIA_OK;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
         if (method == CIA_METHOD_CIA && !pl->cs_has_basis)
@@ -291,7 +291,7 @@ extern "C" cia_status cia_advance(cia_plan_t *pl, int method, double dt, int64_t
     if (pl->model == CIA_MODEL_CUCKER_SMALE) return cs_advance(pl, method, dt, nsteps, r_out, s);
     const int m = method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA;
     if (pl->model == CIA_MODEL_POLYNOMIAL) {
-        if (r_out) return fail(CIA_ERR_INVALID_ARG, "r_out must be NULL for the polynomial model");
+        if (r_out) return fail(CIA_ERR_INVALID_ARG, "r_out must be NULL for the polynomial and Fourier couplings");
     } else {
         st = ensure_omega_constants(pl, dt, s);
         if (st != CIA_OK) return st;
@@ -422,17 +422,17 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
             w[n + m] = beta ? beta[i] : 1.0;
             if (!std::isfinite(w[m]) || !std::isfinite(w[n + m])) return fail(CIA_ERR_NUMERIC, "a weight is not finite");
         }
-        if (!pl->d.pl_alpha) {
+        if (!pl->d.gc_alpha) {
             void *p = nullptr;
             CIA_CUDA_TRY(cudaMalloc(&p, (size_t)2 * n * sizeof(double)));
             pl->allocations.push_back(p);
             pl->device_bytes += (int64_t)(2 * n * sizeof(double));
-            pl->d.pl_alpha = static_cast<double *>(p);
-            pl->d.pl_beta = pl->d.pl_alpha + n;
+            pl->d.gc_alpha = static_cast<double *>(p);
+            pl->d.gc_beta = pl->d.gc_alpha + n;
         }
-        CIA_CUDA_TRY(cudaMemcpy(pl->d.pl_alpha, w.data(), (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice));
+        CIA_CUDA_TRY(cudaMemcpy(pl->d.gc_alpha, w.data(), (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice));
     }
-    pl->poly_weighted = alpha || beta;
+    pl->gc_weighted = alpha || beta;
     // the window holds one more row when weighted; the moments change
     pl->staging = (pl->staging_req == 1 || !gc_window_fits(pl)) ? 1 : 2;
     pl->needs_load = true;
@@ -461,7 +461,8 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
     if (st != CIA_OK && st != CIA_ERR_UNSUPPORTED) return st;
     if (!x) return fail(CIA_ERR_INVALID_ARG, "x is NULL");
     if (steps < 1 || !std::isfinite(dt)) return fail(CIA_ERR_INVALID_ARG, "need steps >= 1 and a finite dt");
-    if (pl->model == CIA_MODEL_POLYNOMIAL) return fail(CIA_ERR_UNSUPPORTED, "no tuning candidates for the polynomial and Fourier couplings");
+    if (pl->model == CIA_MODEL_POLYNOMIAL)
+        return fail(CIA_ERR_UNSUPPORTED, "no tuning candidates for the polynomial and Fourier couplings");
     struct Cand { int tn, tib, staging; };
     std::vector<Cand> cands;
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {

@@ -97,11 +97,11 @@ struct DeviceBuffers {
     int32_t *cs_check_comm = nullptr;         // their communities
     double *cs_check_out = nullptr;           // [check_count][2] error, reference
     float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
-    // polynomial coupling (FP64 stage states and tile power sums)
-    double *pl_y[2] = {nullptr, nullptr};     // [n+1] stage states
-    double *pl_part[2] = {nullptr, nullptr};  // [T][p+1] sums of (beta) y^k per tile
-    double *pl_alpha = nullptr, *pl_beta = nullptr;  // [n] rank-one link weights (permuted)
-    double *gc_f[2] = {nullptr, nullptr};     // Fourier basis: [n][K-1] features of pl_y
+    // general couplings (FP64 stage states and tile feature sums)
+    double *gc_y[2] = {nullptr, nullptr};     // [n+1] stage states
+    double *gc_part[2] = {nullptr, nullptr};  // [T][K] sums of the (beta-weighted) features per tile
+    double *gc_alpha = nullptr, *gc_beta = nullptr;  // [n] rank-one link weights (permuted)
+    double *gc_f[2] = {nullptr, nullptr};     // Fourier basis: [n][K-1] features of gc_y
     // ensembles of independent networks
     void *tile_kn = nullptr;                  // [T] K / N_i of the tile's instance, compute precision
     int32_t *inst_tiles = nullptr;            // [B][4] community tiles [0,1), free tiles [2,3) of instance i
@@ -178,13 +178,13 @@ struct cia_plan {
     // Cucker--Smale
     int state_dim = 1;                  // FP64 values per node at the boundary
     double cs_sigma = 1.0, cs_beta = 0.0;
-    // polynomial coupling
-    int poly_p = 0;
+    // general couplings (polynomial and Fourier; model CIA_MODEL_POLYNOMIAL internally)
+    int poly_p = 0;                     // polynomial degree (1..4), or harmonics (Fourier)
     int smem_optin = 0;                 // opt-in shared memory per block of the device
-    double poly_c[CIA_MAX_POLY + 1] = {0};
-    double poly_dv[CIA_MAX_POLY + 1] = {0};
+    double poly_c[CIA_MAX_POLY + 1] = {0};  // difference form: h
+    double poly_dv[CIA_MAX_POLY + 1] = {0}; // V'
     bool poly_general = false;          // g(x_l, x_m) instead of h(x_l - x_m)
-    bool poly_weighted = false;         // rank-one link weights alpha_m beta_l
+    bool gc_weighted = false;           // rank-one link weights alpha_m beta_l
     int gc_basis = 0;                   // general couplings: 0 polynomial, 1 real Fourier features
     int gc_k = 2;                       // features per node incl. the constant
     double gc_w = 0.0;                  // Fourier basis: pi / L
@@ -238,7 +238,8 @@ cudaError_t cs_launch_check(cia_plan *pl, int slot, cudaStream_t s);
 cudaError_t cs_launch_sample(cia_plan *pl, int slot, int64_t count, uint64_t seed, float *pairs, cudaStream_t s);
 size_t cs_stage_smem_bytes(const cia_plan *pl);
 
-// Polynomial-coupling launchers (polynomial.cu).
+// General-coupling launchers (general_coupling.cu): the polynomial models and the
+// real 2-D Fourier model, all kept under model CIA_MODEL_POLYNOMIAL internally.
 cudaError_t gc_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
 cudaError_t gc_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
 cudaError_t gc_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);

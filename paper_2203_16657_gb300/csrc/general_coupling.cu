@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) gc_load_kernel(const GcParams a, con
 size_t window_cap(const cia_plan *pl) { return (size_t)((pl->max_comm + 1) & ~(int64_t)1); }
 
 // Rows of the window and of the sparse sums: features 1..K-1, or 0..K-1 when weighted.
-int rows(const cia_plan *pl) { return pl->gc_k - 1 + (pl->poly_weighted ? 1 : 0); }
+int rows(const cia_plan *pl) { return pl->gc_k - 1 + (pl->gc_weighted ? 1 : 0); }
 
 size_t tables_bytes(int nr) { return (size_t)nr * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
 
@@ -533,17 +533,17 @@ GcParams base_params(const cia_plan *pl, int slot) {
     a.comm_tile_begin = d.comm_tile_begin;
     a.full_rowptr = d.full_rowptr;
     a.full_col = d.full_col;
-    a.y_in = d.pl_y[slot];
-    a.y_out = d.pl_y[slot ^ 1];
+    a.y_in = d.gc_y[slot];
+    a.y_out = d.gc_y[slot ^ 1];
     a.f_in = d.gc_f[slot];
     a.f_out = d.gc_f[slot ^ 1];
-    a.part_in = d.pl_part[slot];
-    a.part_out = d.pl_part[slot ^ 1];
+    a.part_in = d.gc_part[slot];
+    a.part_out = d.gc_part[slot ^ 1];
     a.acc = static_cast<double *>(d.acc);
     a.theta = d.theta;
     a.perm = d.perm;
-    a.alpha = pl->poly_weighted ? d.pl_alpha : nullptr;
-    a.beta = pl->poly_weighted ? d.pl_beta : nullptr;
+    a.alpha = pl->gc_weighted ? d.gc_alpha : nullptr;
+    a.beta = pl->gc_weighted ? d.gc_beta : nullptr;
     return a;
 }
 
@@ -571,7 +571,7 @@ cudaError_t launch_shape(const cia_plan *pl, int method, const GcParams &a, cuda
         return launch<4 * id>(gc_direct_kernel<MODE, B, K, false>, pl, 0, a, s);
     }
     if constexpr (B == kPoly)
-        if (pl->poly_weighted) return launch<4 * id + 1>(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
+        if (pl->gc_weighted) return launch<4 * id + 1>(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
     return launch<4 * id + 2>(gc_stage_kernel<MODE, B, K, false>, pl, stage_smem(pl), a, s);
 }
 

@@ -639,7 +639,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         if ((s2 = upload<double>(pl, &d.theta, nullptr, n)) != CIA_OK) return s2;
         if ((s2 = alloc_bytes(pl, &d.acc, n * sizeof(double))) != CIA_OK) return s2;
         for (int b = 0; b < 2; ++b)
-            if ((s2 = upload<double>(pl, &d.pl_y[b], nullptr, (size_t)n + 1)) != CIA_OK) return s2;
+            if ((s2 = upload<double>(pl, &d.gc_y[b], nullptr, (size_t)n + 1)) != CIA_OK) return s2;
         if (pl->gc_basis == 1)
             for (int b = 0; b < 2; ++b)
                 if ((s2 = upload<double>(pl, &d.gc_f[b], nullptr, (size_t)n * (pl->gc_k - 1))) != CIA_OK) return s2;
@@ -795,7 +795,7 @@ static cia_status build_tiles(cia_plan *pl) {
         pl->cs_feat_valid = false;
     } else if (pl->model == CIA_MODEL_POLYNOMIAL) {
         for (int b = 0; b < 2; ++b)
-            if ((s2 = upload<double>(pl, &d.pl_part[b], nullptr, (size_t)T * pl->gc_k, true)) != CIA_OK)
+            if ((s2 = upload<double>(pl, &d.gc_part[b], nullptr, (size_t)T * pl->gc_k, true)) != CIA_OK)
                 return s2;
     } else {
         for (int b = 0; b < 2; ++b)
