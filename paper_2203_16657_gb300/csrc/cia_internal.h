@@ -224,6 +224,11 @@ void invalidate_graphs(cia_plan *pl);
 
 // Checks a graph as cia_plan_create does (plan.cpp); sets the error message.
 cia_status validate_graph(const cia_graph *g);
+
+// Raises `kernel`'s dynamic shared-memory limit on `device` to at least
+// `smem` bytes when that is above the default 48 KB; remembers the largest
+// value set per (kernel, device), so a repeated launch costs one lookup.
+cudaError_t ensure_dynamic_smem(const void *kernel, int device, size_t smem);
 // Order parameters of every instance of the state in slot `slot`:
 // r_base[counter * B + i], then ++counter (kuramoto.cu).
 cudaError_t launch_order_parameters(cia_plan *pl, int slot, double *r_base, cudaStream_t s);

@@ -597,18 +597,11 @@ size_t stage_smem(const cia_plan *pl, bool features) {
 
 template <int MODE>
 cudaError_t launch_stage_t(const cia_plan *pl, const CsParams &a, cudaStream_t s) {
-    static int configured_dev = -1;
-    static size_t configured = 0;
     const size_t smem = stage_smem(pl, MODE == kLoad);
-    if (configured_dev != pl->device || smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(cs_stage_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)std::max(smem, configured));
-        if (e != cudaSuccess) return e;
-        configured = std::max(smem, configured);
-        configured_dev = pl->device;
-    }
+    cudaError_t e = ensure_dynamic_smem((const void *)cs_stage_kernel<MODE>, pl->device, smem);
+    if (e != cudaSuccess) return e;
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cs_stage_kernel<MODE>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cs_stage_kernel<MODE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     bps = std::max(1, std::min(bps, 8));   // at most 8 x 64 tensor-memory columns per SM
     // the feature launch keeps one resident CTA per slot (it loads the weights

@@ -547,32 +547,24 @@ GcParams base_params(const cia_plan *pl, int slot) {
     return a;
 }
 
-// One launch of `kernel`, one tile per CTA; ID tells the instantiations apart
-// so that each kernel keeps its own configured shared-memory limit.
-template <int ID>
-cudaError_t launch(void (*kernel)(GcParams), const cia_plan *pl, size_t smem, const GcParams &a,
-                   cudaStream_t s) {
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+// One launch of `kernel`, one tile per CTA.
+cudaError_t launch(void (*kernel)(GcParams), const cia_plan *pl, size_t smem, const GcParams &a, cudaStream_t s) {
+    cudaError_t e = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
+    if (e != cudaSuccess) return e;
     void *args[] = {const_cast<GcParams *>(&a)};
     return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_tiles), dim3(kThreads), args, smem, s);
 }
 
 template <int MODE, int B, int K>
 cudaError_t launch_shape(const cia_plan *pl, int method, const GcParams &a, cudaStream_t s) {
-    constexpr int id = (B * kMaxK + K) * 3 + MODE;   // distinct per (MODE, B, K)
     if (method == Method::DIRECT) {
         if constexpr (B == kPoly)
-            if (a.diff) return launch<4 * id + 3>(gc_direct_kernel<MODE, B, K, true>, pl, 0, a, s);
-        return launch<4 * id>(gc_direct_kernel<MODE, B, K, false>, pl, 0, a, s);
+            if (a.diff) return launch(gc_direct_kernel<MODE, B, K, true>, pl, 0, a, s);
+        return launch(gc_direct_kernel<MODE, B, K, false>, pl, 0, a, s);
     }
     if constexpr (B == kPoly)
-        if (pl->gc_weighted) return launch<4 * id + 1>(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
-    return launch<4 * id + 2>(gc_stage_kernel<MODE, B, K, false>, pl, stage_smem(pl), a, s);
+        if (pl->gc_weighted) return launch(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
+    return launch(gc_stage_kernel<MODE, B, K, false>, pl, stage_smem(pl), a, s);
 }
 
 template <int MODE>

@@ -1318,13 +1318,10 @@ StageParams<T> base_params(cia_plan *pl, int method) {
 }
 
 template <typename K>
-cudaError_t launch_kernel(K kernel, size_t &configured, int64_t blocks, size_t smem, const void *params,
+cudaError_t launch_kernel(K kernel, const cia_plan *pl, int64_t blocks, size_t smem, const void *params,
                           cudaStream_t s) {
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
+    if (e != cudaSuccess) return e;
     void *args[] = {const_cast<void *>(params)};
     return cudaLaunchKernel((const void *)kernel, dim3((unsigned)blocks), dim3(kThreads), args, smem, s);
 }
@@ -1333,28 +1330,20 @@ template <typename T, int P, int MODE>
 cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream_t s) {
     if (pl->staging == 3) {
         auto kernel = cia_pipeline_kernel<T, P, MODE>;
-        static size_t cfg = 0;
         const size_t smem = pipeline_smem_bytes(pl, pl->ring_stages);
-        if (smem > 48 * 1024 && smem > cfg) {
-            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            cfg = smem;
-        }
+        cudaError_t e = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
+        if (e != cudaSuccess) return e;
         void *args[] = {const_cast<StageParams<T> *>(&a)};
         return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_ctas), dim3(kPipeThreads), args, smem, s);
     }
-    if (pl->staging == 2) {
-        static size_t cfgw = 0;
-        return launch_kernel(cia_window_kernel<T, P, MODE>, cfgw, pl->n_tiles, window_smem_bytes(pl), &a, s);
-    }
-    static size_t cfg = 0;
-    return launch_kernel(cia_stage_kernel<T, P, MODE>, cfg, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
+    if (pl->staging == 2)
+        return launch_kernel(cia_window_kernel<T, P, MODE>, pl, pl->n_tiles, window_smem_bytes(pl), &a, s);
+    return launch_kernel(cia_stage_kernel<T, P, MODE>, pl, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
 }
 
 template <typename T, int P, int MODE>
 cudaError_t launch_direct_t(const cia_plan *pl, const StageParams<T> &a, cudaStream_t s) {
-    static size_t cfg = 0;
-    return launch_kernel(direct_stage_kernel<T, P, MODE>, cfg, pl->n_tiles, stage_smem_bytes(pl, Method::DIRECT),
+    return launch_kernel(direct_stage_kernel<T, P, MODE>, pl, pl->n_tiles, stage_smem_bytes(pl, Method::DIRECT),
                          &a, s);
 }
 
@@ -1365,13 +1354,9 @@ cudaError_t dispatch_stage(cia_plan *pl, int method, const StageParams<T> &a, cu
         // the direct method's triadic term, pair by pair, before the stage
         using C = typename Vec2<T>::type;
         auto kernel = triadic_direct_kernel<T>;
-        static size_t cfg = 0;
         const size_t smem = sizeof(C) * (size_t)std::max<int64_t>(1, pl->max_comm);
-        if (smem > 48 * 1024 && smem > cfg) {
-            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            cfg = smem;
-        }
+        cudaError_t e0 = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
+        if (e0 != cudaSuccess) return e0;
         kernel<<<(unsigned)pl->n_tiles, kThreads, smem, s>>>(pl->d.tile_comm, pl->d.tile_first, pl->d.tile_count,
                                                             pl->d.off, a.ph_in, a.k2_over_n2, (T *)pl->d.tri);
         cudaError_t e = cudaGetLastError();
