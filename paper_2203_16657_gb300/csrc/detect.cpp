@@ -92,7 +92,8 @@ int64_t local_moving(const Level &L, const Objective &ob, std::vector<int64_t> &
                     best_gain = gain;
                 }
             }
-            if (!alone && -stay - ob.mu > best_gain) best = -1;   // a new community of its own
+            // a new community of its own (an empty id exists whenever i is not alone)
+            if (!alone && !empties.empty() && -stay - ob.mu > best_gain) best = -1;
             for (int64_t c : touched) {
                 kto[c] = 0.0;
                 seen[c] = 0;
