@@ -54,8 +54,9 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_SO)
+        # CIA_ORACLE_LIB: a prebuilt copy of the same source (the sanitizer test builds one)
+        path = os.environ.get("CIA_ORACLE_LIB") or build()
+        lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         I64 = ctypes.c_int64
         D = ctypes.c_double
