@@ -157,7 +157,9 @@ typedef struct {
                                    phasors copied (TMA) into shared memory; 3 = persistent
                                    warp-specialised CTAs with TMA copies of each tile's indices
                                    and community phasors.  2 and 3 fall back to 1 when their
-                                   buffers do not fit. */
+                                   buffers do not fit.  Polynomial and Fourier couplings: 1 =
+                                   the community's features from global memory, 0, 2 and 3 = in
+                                   shared memory as 64-bit fixed point (1 when it does not fit). */
     int use_graphs;             /* 0 = auto: cia_advance replays one captured CUDA graph per RK4
                                    step when it advances >= 2 steps (not while profiling);
                                    1 = plain launches only */
@@ -356,7 +358,7 @@ cia_status cia_rhs_direct(cia_plan_t *plan, const double *x, double *dxdt, void 
  * r_out: device, nsteps doubles or NULL; r_out[j] = |(1/N) sum_l e^{i x_l}|
  *   after step j+1 (the Kuramoto order parameter, eq. KuramotoFirstOP);
  *   nsteps x B values for an ensemble (cia_plan_create_batch); must be NULL
- *   for Cucker--Smale.
+ *   for Cucker--Smale and for the polynomial and Fourier couplings.
  * nsteps = 0 only round-trips x through the wrap.
  * Cucker--Smale with method CIA and an error check set (cia_plan_set_check):
  * if a check fails, the remaining steps use the direct method and the call
