@@ -22,15 +22,35 @@
 namespace cia {
 namespace {
 
-// A level of the Louvain hierarchy: weighted nodes (size = original nodes
-// inside) and weighted directed links without self loops (w = links between
-// the two groups of original nodes, counted once per direction).
-struct Level {
+// A level of the Louvain hierarchy seen as weighted nodes (size = original
+// nodes inside) and weighted directed links without self loops (w = links
+// between the two groups of original nodes, counted once per direction): the
+// input graph itself (unit sizes and weights, its int32 columns), or an
+// aggregated level (Owned).
+struct View {
     int64_t n = 0;
-    std::vector<int64_t> rowptr;
-    std::vector<int64_t> col;
-    std::vector<double> w;
-    std::vector<double> size;
+    const int64_t *rowptr = nullptr;
+    const int32_t *col32 = nullptr;   // input graph
+    const int64_t *col64 = nullptr;   // aggregated level
+    const double *w = nullptr;        // null: unit weights
+    const double *size = nullptr;     // null: unit sizes
+    int64_t nbr(int64_t e) const { return col32 ? (int64_t)col32[e] : col64[e]; }
+    double weight(int64_t e) const { return w ? w[e] : 1.0; }
+    double sz(int64_t i) const { return size ? size[i] : 1.0; }
+};
+
+struct Owned {
+    std::vector<int64_t> rowptr, col;
+    std::vector<double> w, size;
+    View view() const {
+        View v;
+        v.n = (int64_t)size.size();
+        v.rowptr = rowptr.data();
+        v.col64 = col.data();
+        v.w = w.data();
+        v.size = size.data();
+        return v;
+    }
 };
 
 struct Objective {
@@ -52,10 +72,10 @@ uint64_t splitmix64(uint64_t &s) {
 // k_iC the link weight from i into C (without i itself), S_C the sizes.  The
 // candidates are the communities of i's neighbours and a new community; the
 // best strictly positive gain wins, the first found among equals.
-int64_t local_moving(const Level &L, const Objective &ob, std::vector<int64_t> &comm, uint64_t &rng) {
+int64_t local_moving(const View &L, const Objective &ob, std::vector<int64_t> &comm, uint64_t &rng) {
     const int64_t n = L.n;
     std::vector<double> csize(n, 0.0);
-    for (int64_t i = 0; i < n; ++i) csize[comm[i]] += L.size[i];
+    for (int64_t i = 0; i < n; ++i) csize[comm[i]] += L.sz(i);
     std::vector<int64_t> empties;
     for (int64_t c = n - 1; c >= 0; --c)
         if (csize[c] == 0.0) empties.push_back(c);
@@ -70,15 +90,15 @@ int64_t local_moving(const Level &L, const Objective &ob, std::vector<int64_t> &
         int64_t moved = 0;
         for (int64_t i : order) {
             const int64_t a = comm[i];
-            const double si = L.size[i];
+            const double si = L.sz(i);
             touched.clear();
             for (int64_t e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e) {
-                const int64_t c = comm[L.col[e]];
+                const int64_t c = comm[L.nbr(e)];
                 if (!seen[c]) {
                     seen[c] = 1;
                     touched.push_back(c);
                 }
-                kto[c] += L.w[e];
+                kto[c] += L.weight(e);
             }
             const bool alone = csize[a] == si;
             const double stay = 2.0 * (kto[a] - ob.gp * si * (csize[a] - si)) - (alone ? ob.mu : 0.0);
@@ -128,30 +148,34 @@ int64_t renumber(std::vector<int64_t> &comm) {
 }
 
 // The communities of L as the nodes of the next level.
-Level aggregate(const Level &L, const std::vector<int64_t> &comm, int64_t M) {
-    Level A;
-    A.n = M;
+Owned aggregate(const View &L, const std::vector<int64_t> &comm, int64_t M) {
+    Owned A;
     A.size.assign(M, 0.0);
-    for (int64_t i = 0; i < L.n; ++i) A.size[comm[i]] += L.size[i];
+    for (int64_t i = 0; i < L.n; ++i) A.size[comm[i]] += L.sz(i);
     std::vector<std::vector<int64_t>> members(M);
     for (int64_t i = 0; i < L.n; ++i) members[comm[i]].push_back(i);
     A.rowptr.assign(M + 1, 0);
     std::vector<double> acc(M, 0.0);
+    std::vector<char> seen(M, 0);
     std::vector<int64_t> touched;
     for (int64_t c = 0; c < M; ++c) {
         touched.clear();
         for (int64_t i : members[c])
             for (int64_t e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e) {
-                const int64_t d = comm[L.col[e]];
+                const int64_t d = comm[L.nbr(e)];
                 if (d == c) continue;   // internal links do not move
-                if (acc[d] == 0.0) touched.push_back(d);
-                acc[d] += L.w[e];
+                if (!seen[d]) {
+                    seen[d] = 1;
+                    touched.push_back(d);
+                }
+                acc[d] += L.weight(e);
             }
         std::sort(touched.begin(), touched.end());
         for (int64_t d : touched) {
             A.col.push_back(d);
             A.w.push_back(acc[d]);
             acc[d] = 0.0;
+            seen[d] = 0;
         }
         A.rowptr[c + 1] = (int64_t)A.col.size();
     }
@@ -192,17 +216,16 @@ extern "C" cia_status cia_detect_communities(const cia_graph *g, const cia_detec
     const int64_t nnz = g->rowptr[n];
     const Objective ob{opt->gamma * (n > 1 ? (double)nnz / ((double)n * (double)(n - 1)) : 0.0), opt->community_cost};
 
-    Level base;
+    View base;
     base.n = n;
-    base.rowptr.assign(g->rowptr, g->rowptr + n + 1);
-    base.col.assign(g->col, g->col + nnz);
-    base.w.assign(nnz, 1.0);
-    base.size.assign(n, 1.0);
+    base.rowptr = g->rowptr;
+    base.col32 = g->col;
 
     uint64_t rng = opt->seed;
     std::vector<int64_t> node_comm(n);            // community of every original node
     std::iota(node_comm.begin(), node_comm.end(), 0);
-    Level L = base;
+    Owned agg;   // the current aggregated level
+    View L = base;
     int levels = 0;
     int64_t moves = 0;
     for (; levels < opt->max_levels; ++levels) {
@@ -214,7 +237,8 @@ extern "C" cia_status cia_detect_communities(const cia_graph *g, const cia_detec
         const int64_t M = renumber(comm);
         for (auto &c : node_comm) c = comm[c];
         if (M == L.n) break;
-        L = aggregate(L, comm, M);
+        agg = aggregate(L, comm, M);
+        L = agg.view();
     }
     // a last pass over the original nodes: a local minimum under single moves
     moves += local_moving(base, ob, node_comm, rng);
