@@ -2,6 +2,7 @@
 // the thread-local error text behind cia_last_error() and the validation of
 // an input graph (no CUDA calls, so that this file also builds without the
 // CUDA runtime).
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -19,10 +20,12 @@ static cia_status fail(cia_status s, const std::string &msg) {
     return s;
 }
 
-// Validate the CSR: bounds, ordering, self loops, then symmetry in O(nnz):
-// rows are visited in increasing order, so the entries (j, i) with i < j of
-// row j are met in increasing i; a cursor per row checks they appear exactly
-// in that order, and at the end every entry below the diagonal was matched.
+// Validate the CSR: bounds, ordering and self loops row by row, then
+// symmetry: every entry (i, j) above the diagonal must have its mirror (j, i),
+// found by binary search in the sorted row j, and the entries below the
+// diagonal must be exactly as many (the mirrors are distinct entries, so
+// then every entry below the diagonal is some mirror).  Rows run in parallel;
+// the smallest offending row is reported.
 cia_status validate_graph(const cia_graph *g) {
     const int64_t n = g->n;
     if (g->rowptr[0] != 0) return fail(CIA_ERR_INVALID_GRAPH, "rowptr[0] != 0");
@@ -51,23 +54,41 @@ cia_status validate_graph(const cia_graph *g) {
         }
     }
     if (bad_row >= 0) return fail(CIA_ERR_INVALID_GRAPH, why + " in row " + std::to_string(bad_row));
-    std::vector<int64_t> cursor(g->rowptr, g->rowptr + n);
+    int64_t above = 0, below = 0, bad_i = -1, bad_j = -1;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(+ : above, below)
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) {
-            int64_t j = g->col[e];
-            if (j <= i) continue;
-            int64_t &cj = cursor[j];
-            if (cj >= g->rowptr[j + 1] || g->col[cj] != i)
-                return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(i) + "->" +
-                                                       std::to_string(j) + " has no reverse");
-            ++cj;
+            const int64_t j = g->col[e];
+            if (j < i) {
+                ++below;
+                continue;
+            }
+            ++above;
+            const int32_t *lo = g->col + g->rowptr[j], *hi = g->col + g->rowptr[j + 1];
+            const int32_t *f = std::lower_bound(lo, hi, (int32_t)i);
+            if (f == hi || *f != i) {
+#pragma omp critical
+                {
+                    if (bad_i < 0 || i < bad_i) { bad_i = i; bad_j = j; }
+                }
+            }
         }
     }
-    for (int64_t j = 0; j < n; ++j) {
-        int64_t c = cursor[j];
-        if (c < g->rowptr[j + 1] && g->col[c] < j)
-            return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(j) + "->" +
-                                                   std::to_string(g->col[c]) + " has no reverse");
+    if (bad_i >= 0)
+        return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(bad_i) + "->" +
+                                               std::to_string(bad_j) + " has no reverse");
+    if (above != below) {
+        // an entry below the diagonal without its mirror: the smallest such row
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t e = g->rowptr[j]; e < g->rowptr[j + 1]; ++e) {
+                const int64_t i = g->col[e];
+                if (i >= j) break;
+                const int32_t *lo = g->col + g->rowptr[i], *hi = g->col + g->rowptr[i + 1];
+                const int32_t *f = std::lower_bound(lo, hi, (int32_t)j);
+                if (f == hi || *f != j)
+                    return fail(CIA_ERR_INVALID_GRAPH, "asymmetric: link " + std::to_string(j) + "->" +
+                                                           std::to_string(i) + " has no reverse");
+            }
     }
     return CIA_OK;
 }

@@ -51,6 +51,8 @@ def _plan(lib, rowptr, col, labels, omega=None, **kw):
 
 @pytest.mark.parametrize("rowptr,col,why", [
     ([0, 1, 1], [1], "asymmetric"),
+    ([0, 0, 1], [0], "asymmetric: link 1->0"),                 # a link below the diagonal alone
+    ([0, 2, 3, 4], [1, 2, 0, 1], "asymmetric: link 0->2"),     # 2 lists 1, not 0
     ([0, 1, 2], [0, 0], "self loop"),
     ([0, 2, 3, 4], [2, 1, 0, 0], "not strictly increasing"),
     ([0, 1, 2], [5, 0], "out of range"),
