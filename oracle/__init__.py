@@ -1,6 +1,6 @@
 """FP64 CPU oracle for the community integration algorithm (CIA).
 
-TEST INFRASTRUCTURE ONLY: the judge of the CUDA library.  Only the tests,
+TEST INFRASTRUCTURE ONLY: the correctness reference of the CUDA library.  Only the tests,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this package.  It shares no code with the device path: its own P1 split, its
 own right-hand sides (``cia_oracle.c``), its own integrators.

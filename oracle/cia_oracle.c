@@ -1,7 +1,7 @@
 /*
  * Plain FP64 CPU oracle for the community integration algorithm (CIA).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the correctness judge for the CUDA
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference for the CUDA
  * library; the product path never links, loads or calls it.  It shares no code,
  * header, table or constant with the device path.
  *

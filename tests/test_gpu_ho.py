@@ -2,7 +2,7 @@
 
 The triadic term lives on the complete hyperedges of each community
 (App. A.7 with lambda = (1, 1, -2)); the oracle's brute-force sum over ordered
-pairs is the judge, its moment formula (pinned to the brute force) gives the
+pairs is the reference, its moment formula (pinned to the brute force) gives the
 long runs.  Tolerances as for the pairwise model: FP64 1e-12, FP32 1e-5
 (coupling part, inf-norm relative)."""
 import numpy as np
