@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the small FP64 and the higher-order Kuramoto workloads")
     ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-coupling workloads")
-    ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly"], default=None,
+    ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly", "p1"], default=None,
                     help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
 
@@ -486,6 +486,30 @@ def poly_leg(args, torch, cia, flush) -> dict:
     return out
 
 
+# ------------------------------------------------------------------ step P1 (host, offline)
+
+def p1_leg(args) -> dict:
+    """Community detection for step P1 on the headline graph (host code of
+    libcia, untimed in the hot path): wall time, the entries of S it leaves
+    against the planted labels, and whether the planted partition is found."""
+    import paper_2203_16657_gb300 as cia
+    import synthetic as S
+    from oracle import split
+    w = S.kuramoto_lognormal(scale=args.scale)
+    g = w.graph
+    t0 = time.perf_counter()
+    labels, rep = cia.detect_communities(g.rowptr, g.col, seed=1)
+    secs = time.perf_counter() - t0
+    sp = split(g.rowptr, g.col, g.labels)
+    rows = np.repeat(np.arange(g.n), np.diff(sp.s_rowptr))
+    planted = int(np.sum(sp.s_val != 0)) - int(np.sum((sp.s_val == -1) & (sp.s_col == rows)))
+    found = len(set(zip(labels.tolist(), g.labels.tolist()))) == len(set(g.labels.tolist())) == rep["communities"]
+    return {"workload": WORKLOAD, "n": g.n, "nnz_graph": int(len(g.col)), "seconds": secs,
+            "local_moving_threads": 1, "communities": rep["communities"],
+            "nnz_s_detected": rep["nnz_missing"] + rep["nnz_inter"], "nnz_s_planted": planted,
+            "planted_partition_recovered": bool(found), "report": rep}
+
+
 # ------------------------------------------------------------------ small FP64 and higher-order workloads
 
 def _time_method(torch, plan, x0, dt, steps, warmup, method, flush) -> float:
@@ -593,6 +617,12 @@ def main():
             return 0
         w = S.kuramoto_lognormal(scale=args.scale)
         reference_arm(args, w)
+        return 0
+
+    if args.only == "p1":
+        # host-only leg: no GPU work
+        if rank == 0:
+            print(json.dumps({"leg": "p1", **p1_leg(args)}), flush=True)
         return 0
 
     import torch
