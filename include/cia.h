@@ -130,7 +130,8 @@ typedef struct {
  * summed with g itself.  FP64 only; omega must be NULL. */
 typedef struct {
     int model;                  /* cia_model */
-    int p;                      /* number of harmonics, 1..CIA_MAX_HARMONICS */
+    int p;                      /* Kuramoto and Fourier models: harmonics, 1..CIA_MAX_HARMONICS;
+                                   polynomial models: degree, 0..CIA_MAX_POLY */
     double d_sin[CIA_MAX_HARMONICS];
     double d_cos[CIA_MAX_HARMONICS];
     double K;                   /* coupling constant multiplying (1/N) sum */
