@@ -262,6 +262,62 @@ def test_cs_cia_exact_for_constant_weight(oracle_mod):
     np.testing.assert_allclose(c[sp.iperm], d, rtol=0, atol=1e-13)
 
 
+def _separable_weight(dx, dy, L):
+    """g(d) = 1 + cos(pi d_x / L) + 0.5 cos(2 pi d_y / L): non-constant and, by
+    cos(a - b) = cos a cos b + sin a sin b, exactly phi(s_l) . phi(s_m) for the
+    five features of _separable_features."""
+    return 1.0 + np.cos(np.pi * dx / L) + 0.5 * np.cos(2 * np.pi * dy / L)
+
+
+def _separable_features(s, L):
+    a, b = np.pi * s[:, 0] / L, 2 * np.pi * s[:, 1] / L
+    h = math.sqrt(0.5)
+    return np.stack([np.ones(len(s)), np.cos(a), np.sin(a), h * np.cos(b), h * np.sin(b)], axis=1)
+
+
+@pytest.mark.parametrize("beta,seed", [(0.0, 21), (0.4, 22), (0.4, 23)])
+def test_cs_cia_non_constant_separable_weight_brute_force(oracle_mod, beta, seed):
+    """Eqs. Cucker_Smale_orderParams and Cucker_Smale_fast_RHS with an exactly
+    separable, non-constant weight g on the community blocks D and the exact
+    weight eta on the links of S (-1 missing, +1 inter).  The expected value is
+    the definition summed pair by pair over a dense adjacency:
+
+        v_m' = (1/N) [ sum_{l in c(m)} g(s_l - s_m)(v_l - v_m)
+                       - sum_{l in c(m), l != m, a_ml = 0} eta (v_l - v_m)
+                       + sum_{l not in c(m), a_ml = 1} eta (v_l - v_m) ].
+
+    Every feature value differs between nodes and between features, so a
+    transposed feature index, node m's feature row used for l (or the other way
+    round), or another community's U/H row changes the result."""
+    g = S.random_labels_graph(44, 0.45, 4, seed=seed, free_frac=0.15)
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    rng = np.random.default_rng(seed)
+    L = 10.0
+    x = np.concatenate([rng.uniform(0, 10, (g.n, 2)), rng.normal(size=(g.n, 2))], axis=1)
+    K, sigma = 1.3, 1.0
+    n = g.n
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, g.col[g.rowptr[i]:g.rowptr[i + 1]]] = 1.0
+    lab = np.asarray(g.labels)
+    same = (lab[:, None] == lab[None, :]) & (lab[:, None] >= 0)
+    want = np.zeros((n, 4))
+    for m in range(n):
+        dv = x[:, 2:] - x[m, 2:]
+        dx, dy = x[:, 0] - x[m, 0], x[:, 1] - x[m, 1]
+        eta = K * (sigma * sigma + dx * dx + dy * dy) ** (-beta)
+        w = np.where(same[m], _separable_weight(dx, dy, L), 0.0)
+        w -= np.where(same[m] & (A[m] == 0) & (np.arange(n) != m), eta, 0.0)
+        w += np.where(~same[m] & (A[m] == 1), eta, 0.0)
+        want[m, :2] = x[m, 2:]
+        want[m, 2:] = (w[:, None] * dv).sum(axis=0) / n
+    feat = _separable_features(x[:, :2], L)
+    assert np.ptp(feat, axis=0)[1:].min() > 0.5            # non-constant in every feature
+    got = oracle_mod.cs_cia(sp, x[sp.perm], feat[sp.perm], K, sigma, beta)[sp.iperm]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    assert np.abs(want[:, 2:]).max() > 0.05
+
+
 # ---------------------------------------------------------------- learned basis
 
 def _params(rng, H=8, R=4):
