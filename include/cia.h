@@ -427,7 +427,10 @@ cia_status cia_selftest_bounded_wait(cia_plan_t *plan, int64_t limit_ns, void *s
  * loop where cudaMalloc, which may synchronise the device, is not allowed).
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (phasors and community observables) is one fixed 5 MiB array in device
- * memory, held by every GPU that loads this library until the process exits.
+ * memory.  A device reserves that array when the library's module is loaded
+ * there -- at the latest at the first call on that device (under CUDA's
+ * default lazy module loading), earlier if modules are loaded eagerly -- and
+ * keeps it until the process exits.
  * The paper has no counterpart of this entry point.
  *
  * Everything is in PERMUTED node order (communities contiguous, unlabelled
@@ -438,9 +441,12 @@ cia_status cia_selftest_bounded_wait(cia_plan_t *plan, int64_t limit_ns, void *s
  *     the column arrays may be NULL when they have no entries;
  *   x, omega, dxdt: device, n doubles (omega may be NULL = 0);
  *   coupling: host, CIA_MODEL_KURAMOTO with p harmonics.
- * Limit: p * (n + M) <= 327680, otherwise CIA_ERR_INVALID_ARG and nothing runs.
- * The first call on a device resolves the scratch array's device address
- * (with that device current); make that first call before any stream capture.
+ * Limit: p * (n + M) <= 327680 (n and M each at most 327680), otherwise
+ * CIA_ERR_INVALID_ARG and nothing runs.
+ * The first call on a device (and the first after a device reset, which gives
+ * the device a new context) resolves the scratch array's device address with
+ * that device current, which may load the module; make that first call
+ * before any stream capture.
  * All calls share the scratch array: calls that can overlap on the GPU (e.g.
  * on unordered streams) race with each other. */
 cia_status cia_rhs_kuramoto_static(int64_t n, int64_t M, const int64_t *offsets,

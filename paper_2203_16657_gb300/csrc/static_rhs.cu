@@ -7,12 +7,15 @@
 // provides cia_rhs_kuramoto_static: the FP64 Kuramoto CIA right-hand side on
 // caller-provided device arrays, whose only scratch memory -- the phasors
 // e^{i k x_m} of the state and the community observables Z_{c,k} -- lives in
-// one file-scope __device__ array of fixed size.  Every GPU that loads the
-// library holds that array (kScratchBytes) until the process exits.
+// one file-scope __device__ array of fixed size.  A device holds that array
+// (5 MiB) from the moment this module is loaded there -- at the latest at the
+// first call on that device, earlier if modules are loaded eagerly -- until
+// the process exits.
 //
 // The array is shared by all calls: it keeps the last call's contents, every
 // element a call reads is written earlier in the same call, and calls whose
 // work overlaps on the GPU (different streams, no ordering) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,9 +38,41 @@ static __device__ __align__(256) double2 g_static_scratch[kScratchEntries];
 
 // Device address of g_static_scratch on each device, resolved once per device
 // (with that device current) by cudaGetSymbolAddress: in host code the symbol
-// itself is only a host-side stand-in, not a device address.
+// itself is only a host-side stand-in, not a device address.  The address is
+// valid for one context: after a device reset the runtime creates a new
+// primary context, reloads the module and the array may move, so the address
+// is kept together with the unique id of the context it was resolved in and
+// resolved again when the current context's id differs.
 double2 *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 std::mutex g_scratch_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if none is current),
+// through the driver entry points the runtime hands out (no libcuda link).
+cudaError_t current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    *id = 0;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 constexpr int kBlock = 256;
 
@@ -162,22 +197,29 @@ extern "C" cia_status cia_rhs_kuramoto_static(int64_t n, int64_t M, const int64_
     const int p = coupling->p;
     if (p < 1 || p > CIA_MAX_HARMONICS) return fail(CIA_ERR_INVALID_ARG, "p must be in [1, CIA_MAX_HARMONICS]");
     if (!std::isfinite(coupling->K)) return fail(CIA_ERR_NUMERIC, "K is not finite");
-    if ((int64_t)p * (n + M) > kScratchEntries)
+    // n and M are bounded first so that p * (n + M) cannot overflow
+    if (n > kScratchEntries || M > kScratchEntries || (int64_t)p * (n + M) > kScratchEntries)
         return fail(CIA_ERR_INVALID_ARG,
-                    "p * (n + M) = " + std::to_string((int64_t)p * (n + M)) +
-                        " exceeds the static scratch capacity of " + std::to_string(kScratchEntries) +
-                        " complex entries; use cia_plan_create + cia_rhs");
+                    "p * (n + M) with n = " + std::to_string(n) + ", M = " + std::to_string(M) +
+                        ", p = " + std::to_string(p) + " exceeds the static scratch capacity of " +
+                        std::to_string(kScratchEntries) + " complex entries; use cia_plan_create + cia_rhs");
     int dev = -1;
     CIA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(CIA_ERR_UNSUPPORTED, "device index out of range");
     double2 *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
+        unsigned long long ctx = 0;
+        CIA_CUDA_TRY(current_context_id(&ctx));
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
+            // cudaGetSymbolAddress makes the device's primary context current if
+            // none is, and loads this module in it (no allocation by this code)
             void *addr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+            CIA_CUDA_TRY(current_context_id(&ctx));
             g_scratch_addr[dev] = static_cast<double2 *>(addr);
+            g_scratch_ctx[dev] = ctx;
         }
         scratch = g_scratch_addr[dev];
     }
