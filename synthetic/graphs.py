@@ -190,6 +190,86 @@ def sbm_graph(sizes, p_in: float, *, seed: int, p_out: float | None = None,
     return Graph(n=n, rowptr=rowptr, col=col, labels=labels, sizes=sizes)
 
 
+def _native():
+    """The row-parallel generator (hash_sbm.c), compiled once with gcc."""
+    global _NATIVE
+    if _NATIVE is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "hash_sbm.c")
+        out_dir = os.path.join(here, "_build")
+        so = os.path.join(out_dir, "libhash_sbm.so")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            os.makedirs(out_dir, exist_ok=True)
+            tmp = so + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, src])
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        P, I64, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64
+        lib.syn_pair_hash.restype = U64
+        lib.syn_pair_hash.argtypes = [U64, U64]
+        lib.syn_hash_sbm_rowptr.restype = I64
+        lib.syn_hash_sbm_rowptr.argtypes = [I64, I64, P, U64, U64, ctypes.c_int, P, P]
+        lib.syn_hash_sbm_fill.restype = None
+        lib.syn_hash_sbm_fill.argtypes = [I64, I64, P, U64, U64, ctypes.c_int, P, P, P, P]
+        _NATIVE = lib
+    return _NATIVE
+
+
+_NATIVE = None
+
+
+def pair_threshold(p_in: float) -> tuple[int, int]:
+    """(thr, all): a pair is linked iff its hash is below thr = floor(p_in * 2^64)
+    (exact: a double times a power of two), or always when all = 1 (p_in = 1)."""
+    if not 0.0 <= p_in <= 1.0:
+        raise ValueError("p_in must be in [0, 1]")
+    return (0, 1) if p_in == 1.0 else (int(p_in * 2.0 ** 64), 0)
+
+
+def hash_sbm_graph(sizes, p_in: float, *, seed: int, inter_degree: float = 0.0,
+                   n_free: int = 0) -> Graph:
+    """Planted-partition graph whose intra-community links are decided pair by
+    pair by a counter-based hash (hash_sbm.c): each pair of one community is
+    linked with probability p_in, independently; n*inter_degree/2 distinct
+    uniformly random inter-community pairs are linked as in sbm_graph; n_free
+    extra nodes (label -1) have inter links only.  Node ids are in block order
+    (not shuffled) and the rows are generated in parallel, so communities of
+    10^4 to 10^5 nodes and ensembles of thousands of networks are built in
+    seconds.
+    """
+    import ctypes
+    lib = _native()
+    rng = rng_for(seed)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    m = len(sizes)
+    n = int(sizes.sum()) + int(n_free)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    comm = np.full(n, -1, dtype=np.int64)
+    comm[:off[-1]] = np.repeat(np.arange(m, dtype=np.int64), sizes)
+    if inter_degree > 0:
+        i, j = _inter_pairs_degree(comm, inter_degree, rng)
+        ik = np.concatenate([i * n + j, j * n + i])
+        ik.sort()
+    else:
+        ik = np.zeros(0, np.int64)
+    irow = ik // max(n, 1)
+    inter_rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(irow, minlength=n), out=inter_rowptr[1:])
+    inter_col = np.ascontiguousarray((ik % max(n, 1)).astype(np.int32))
+    thr, full = pair_threshold(p_in)
+    hseed = int(rng.integers(0, 2 ** 63, dtype=np.int64))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    nnz = lib.syn_hash_sbm_rowptr(n, m, ptr(off), hseed, thr, full, ptr(inter_rowptr), ptr(rowptr))
+    col = np.empty(nnz, dtype=np.int32)
+    lib.syn_hash_sbm_fill(n, m, ptr(off), hseed, thr, full, ptr(inter_rowptr), ptr(inter_col), ptr(rowptr),
+                          ptr(col))
+    return Graph(n=n, rowptr=rowptr, col=col, labels=comm.astype(np.int32), sizes=sizes)
+
+
 def complete_graph_communities(sizes, *, seed: int, shuffle: bool = True) -> Graph:
     """Disjoint complete graphs (p_in = 1, no inter-community links)."""
     return sbm_graph(sizes, 1.0, seed=seed, inter_degree=0.0, shuffle=shuffle)

@@ -19,8 +19,10 @@ Workloads (sizes, distributions and integrator settings):
 * ``kuramoto_ensemble``: independent Kuramoto networks, per instance
   N_i ~ U{256..16384}, M_i ~ U{2..32} communities of equal size (+-1),
   p_in ~ U[0.7, 1.0], integer inter degree ~ U{2..10}, omega ~ N(0,1),
-  theta0 ~ U[0, 2pi), K=4, RK4 dt=0.01, 500 steps, FP32 (4096 instances at
-  full size; tests and the measurement take the first few).
+  theta0 ~ U[0, 2pi), K=4, RK4 dt=0.01, 500 steps, FP32, 4096 instances.
+  Its graphs come from the row-parallel hash generator (node ids in block
+  order), so that all 4096 (about 34 M nodes and 33 G directed links) are
+  generated in seconds, one instance at a time.
 
 ``scale`` shrinks the node count and community sizes for tests; the structure
 (p_in, degree, distributions) is unchanged.
@@ -32,7 +34,7 @@ import functools
 
 import numpy as np
 
-from .graphs import Graph, equal_sizes, lognormal_sizes, rng_for, sbm_graph
+from .graphs import Graph, equal_sizes, hash_sbm_graph, lognormal_sizes, rng_for, sbm_graph
 
 SEED_BASE = 2203166570
 
@@ -138,23 +140,39 @@ class EnsembleWorkload:
     precision: str
 
 
-def kuramoto_ensemble(instances: int = 4096, n_range=(256, 16384), steps: int = 500) -> EnsembleWorkload:
-    """The first `instances` networks of the seeded ensemble (instance i has
-    the same graph whatever `instances` is); n_range bounds N_i for tests."""
-    seed = SEED_BASE + 4
-    out = []
-    for i in range(instances):
-        rng = rng_for(seed + 7919 * (i + 1))
-        n = int(rng.integers(n_range[0], n_range[1] + 1))
-        m = int(rng.integers(2, 33))
-        m = min(m, n // 2)
-        p_in = float(rng.uniform(0.7, 1.0))
-        deg = int(rng.integers(2, 11))
-        g = sbm_graph(equal_sizes(n, m), p_in, inter_degree=float(deg), seed=seed + 7919 * (i + 1) + 1)
-        omega = as_fp32_values(rng.normal(0.0, 1.0, size=g.n))
-        theta0 = as_fp32_values(_phases(rng, g.n))
-        out.append(KuramotoWorkload("kuramoto_ensemble[%d]" % i, g, theta0, omega, 4.0,
-                                    np.array([1.0]), np.array([0.0]), 0.01, steps, "fp32"))
+ENSEMBLE_SEED = SEED_BASE + 4
+
+
+def ensemble_instance_shape(i: int, n_range=(256, 16384)) -> tuple[int, int, float, int]:
+    """(N_i, M_i, p_in, inter degree) of ensemble instance i, without building it."""
+    rng = rng_for(ENSEMBLE_SEED + 7919 * (i + 1))
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    m = min(int(rng.integers(2, 33)), n // 2)
+    p_in = float(rng.uniform(0.7, 1.0))
+    deg = int(rng.integers(2, 11))
+    return n, m, p_in, deg
+
+
+def ensemble_instance(i: int, n_range=(256, 16384), steps: int = 500) -> KuramotoWorkload:
+    """Instance i of the seeded ensemble (the same network whatever else is built)."""
+    seed = ENSEMBLE_SEED + 7919 * (i + 1)
+    rng = rng_for(seed)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    m = min(int(rng.integers(2, 33)), n // 2)
+    p_in = float(rng.uniform(0.7, 1.0))
+    deg = int(rng.integers(2, 11))
+    g = hash_sbm_graph(equal_sizes(n, m), p_in, inter_degree=float(deg), seed=seed + 1)
+    omega = as_fp32_values(rng.normal(0.0, 1.0, size=g.n))
+    theta0 = as_fp32_values(_phases(rng, g.n))
+    return KuramotoWorkload("kuramoto_ensemble[%d]" % i, g, theta0, omega, 4.0,
+                            np.array([1.0]), np.array([0.0]), 0.01, steps, "fp32")
+
+
+def kuramoto_ensemble(instances: int = 4096, n_range=(256, 16384), steps: int = 500,
+                      first: int = 0) -> EnsembleWorkload:
+    """Instances first .. first + instances - 1 of the seeded ensemble; n_range
+    bounds N_i for tests."""
+    out = [ensemble_instance(i, n_range, steps) for i in range(first, first + instances)]
     return EnsembleWorkload("kuramoto_ensemble", out, 4.0, 0.01, steps, "fp32")
 
 

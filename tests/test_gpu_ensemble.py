@@ -194,6 +194,28 @@ def test_autotune_picks_a_working_tiling(P, oracle_mod):
         o += n
 
 
+def test_largest_ensemble_instances(P, oracle_mod):
+    """The instances of the full ensemble with the largest communities (N_i
+    above 15000 in M_i = 2 communities of about 8000 nodes), batched with a
+    small one: every node's FP32 right-hand side against the oracle."""
+    import torch
+    import synthetic as S
+    big = [i for i in range(4096)
+           if S.ensemble_instance_shape(i)[1] == 2 and S.ensemble_instance_shape(i)[0] >= 15000][:3]
+    assert len(big) == 3
+    inst = [S.ensemble_instance(i) for i in [0] + big]
+    assert max(w.graph.sizes.max() for w in inst) >= 7500
+    plan = _batch_plan(P, inst)
+    x = torch.from_numpy(_concat([w.theta0 for w in inst])).cuda()
+    out = plan.rhs(x).cpu().numpy()
+    o = 0
+    for w in inst:
+        n = w.graph.n
+        ref = oracle_mod.kuramoto_direct(w.graph.rowptr, w.graph.col, w.theta0, w.omega, 4.0)
+        assert coupling_rel_err(out[o:o + n], ref, w.omega) <= 1e-5, w.name
+        o += n
+
+
 def test_bench_sized_ensemble_sampled(P, oracle_mod):
     """The 32 instances the measurement uses (full per-instance size
     distribution): CIA right-hand side of every instance against the oracle."""

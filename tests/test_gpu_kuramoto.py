@@ -166,6 +166,43 @@ def test_rhs_fp32_lognormal_reduced(cia, oracle_mod, torch_mod, staging):
         assert coupling_rel_err(gpu_rhs(torch_mod, plan, w.theta0, method), ref, w.omega) < FP32_TOL
 
 
+def test_rhs_fp32_lognormal_full_size(cia, oracle_mod, torch_mod):
+    """The full N = 262144 lognormal workload (256 communities, p_in 0.95,
+    inter degree 8) in the launch configuration the measurement times: FP32
+    CIA right-hand side against the FP64 oracle's direct sum, element-wise
+    on the coupling part."""
+    w = S.cached("kuramoto_lognormal")
+    g = w.graph
+    plan = make_plan(cia, g, w.omega, w.K, precision="fp32")
+    assert plan.info()["staging"] == 2                 # the community-window kernel
+    ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
+    got = gpu_rhs(torch_mod, plan, w.theta0, "cia")
+    assert coupling_rel_err(got, ref, w.omega) < FP32_TOL
+    assert coupling_rel_err(gpu_rhs(torch_mod, plan, w.theta0, "direct"), ref, w.omega) < FP32_TOL
+
+
+@pytest.mark.parametrize("lam,staging", [(20000, 2), (50000, 1)])
+def test_rhs_fp32_large_communities(cia, oracle_mod, torch_mod, lam, staging):
+    """Communities above 10^4 nodes in FP32 (p_in 0.95, inter degree 8, a few
+    unlabelled nodes): the community observable of lam unit phasors summed by
+    32-term warp trees in FP32 and in FP64 above them must keep the coupling
+    part within the FP32 bar.  lam = 20000 still takes the shared-memory window
+    (160 KB); lam = 50000 does not fit it, so the whole plan takes the
+    plain-load kernel."""
+    g = S.hash_sbm_graph([lam, 1500, 37], 0.95, seed=70 + lam // 10000, inter_degree=8.0, n_free=13)
+    rng = np.random.default_rng(lam)
+    th = S.as_fp32_values(rng.uniform(-np.pi, np.pi, g.n))
+    th[:lam] = S.as_fp32_values(0.3 * rng.standard_normal(lam))   # partly synchronised: |Z| ~ lam
+    om = S.as_fp32_values(0.5 * rng.standard_cauchy(g.n))
+    plan = cia.Plan(g.rowptr, g.col, g.labels, om, K=2.0, precision="fp32")
+    assert plan.info()["staging"] == staging
+    ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 2.0)
+    got = gpu_rhs(torch_mod, plan, th, "cia")
+    assert coupling_rel_err(got, ref, om) < FP32_TOL
+    # the nodes of the large community alone (their coupling is the largest)
+    assert coupling_rel_err(got[:lam], ref[:lam], om[:lam]) < FP32_TOL
+
+
 # ------------------------------------------------------------------ integration
 
 def test_integrate_fp64_small_sbm(cia, oracle_mod, torch_mod):
