@@ -157,8 +157,13 @@ typedef struct {
                                    one CTA per tile; 2 = one CTA per tile with the community's
                                    phasors copied (TMA) into shared memory; 3 = persistent
                                    warp-specialised CTAs with TMA copies of each tile's indices
-                                   and community phasors.  2 and 3 fall back to 1 when their
-                                   buffers do not fit.  Polynomial and Fourier couplings: 1 =
+                                   and community phasors; 4 = persistent CTAs, each tile's
+                                   community phasors and indices copied (TMA) into one
+                                   shared-memory buffer of at most tile_index_bytes (the window
+                                   of a large community leaves less room for indices, so its
+                                   tiles are shorter), the next tile's copy overlapping the
+                                   current tile's node phase.  2, 3 and 4 fall back to 1 when
+                                   their buffers do not fit.  Polynomial and Fourier couplings: 1 =
                                    the community's features from global memory, 0, 2 and 3 = in
                                    shared memory as 64-bit fixed point (1 when it does not fit). */
     int use_graphs;             /* 0 = auto: cia_advance replays one captured CUDA graph per RK4
@@ -183,7 +188,7 @@ typedef struct {
     int group_size;
     int tile_nodes;
     int missing_index_bytes;    /* 2 (16-bit community-local index) or 4 */
-    int staging;                /* the kernel in use: 1, 2 or 3 as in cia_options */
+    int staging;                /* the kernel in use: 1, 2, 3 or 4 as in cia_options */
     int group_size_direct;      /* threads per row of the direct method */
     int64_t max_tile_index_bytes; /* largest sparse-index footprint of a tile */
     int model;                  /* cia_model */
@@ -275,6 +280,24 @@ cia_status cia_plan_create(const cia_graph *g, const int32_t *community, const d
 cia_status cia_plan_create_batch(int64_t B, const cia_graph *graphs, const int32_t *const *communities,
                                  const double *const *omegas, const cia_coupling *coupling,
                                  const cia_options *opt, cia_plan_t **out);
+
+/* The same ensemble plan built one instance at a time, so that the caller
+ * never holds every instance's graph at once (an ensemble of thousands of
+ * networks can have tens of billions of CSR entries).  cia_plan_batch_begin
+ * takes the coupling (CIA_MODEL_KURAMOTO) and options (build_direct must be
+ * 0: CIA_ERR_UNSUPPORTED otherwise; plan a sample of instances with
+ * cia_plan_create_batch for the direct method); cia_plan_batch_add validates
+ * and splits one instance (step P1, Sec. 3.1) -- g, community and omega
+ * (nullable) as for cia_plan_create, copied, so the caller may free them when
+ * it returns; every community of an added instance must have at most 65535
+ * nodes (CIA_ERR_UNSUPPORTED).  cia_plan_batch_finish lays the instances out
+ * on the device exactly as cia_plan_create_batch would for the same
+ * instances in the same order; the plan can then be used like any other.  A
+ * failed add leaves the plan as it was; a failed finish leaves a plan that
+ * only cia_plan_destroy accepts. */
+cia_status cia_plan_batch_begin(const cia_coupling *coupling, const cia_options *opt, cia_plan_t **out);
+cia_status cia_plan_batch_add(cia_plan_t *plan, const cia_graph *g, const int32_t *community, const double *omega);
+cia_status cia_plan_batch_finish(cia_plan_t *plan);
 
 /* Rank-one link weights for the polynomial models (Sec. "Rank One Coupling",
  * eq. rank1system, on the plan's graph): every link's coupling is scaled by

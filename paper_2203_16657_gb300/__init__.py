@@ -145,6 +145,47 @@ class Plan:
             omegas = [None] * len(graphs)
         return cls(None, None, None, _batch=(list(graphs), list(labels), list(omegas)), **kw)
 
+    @classmethod
+    def streamed(cls, instances, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,), precision="fp32", tile_nodes=0,
+                 tile_index_bytes=0, staging="auto", use_graphs=True):
+        """An ensemble planned one instance at a time (include/cia.h,
+        cia_plan_batch_begin/add/finish): `instances` yields (rowptr, col,
+        labels, omega) per instance, omega may be None; each instance's arrays
+        can be dropped once the next one is requested."""
+        lib = load()
+        cp = cls._coupling("kuramoto", d_sin, d_cos, K, 0.0, 1.0, 0.0)
+        opt = _abi.Options(_abi.PRECISION[precision], 0, int(tile_nodes), 0, int(tile_index_bytes),
+                           _abi.STAGING[staging], 0 if use_graphs else 1)
+        handle = ctypes.c_void_p()
+        _abi.check(lib.cia_plan_batch_begin(ctypes.byref(cp), ctypes.byref(opt), ctypes.byref(handle)))
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._keep = []
+        self._h = handle
+        n = 0
+        for rowptr, col, labels, omega in instances:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            lb = np.ascontiguousarray(labels, dtype=np.int32)
+            if len(lb) != len(rp) - 1:
+                raise ValueError("labels must have n entries")
+            om = None
+            if omega is not None:
+                om = np.ascontiguousarray(omega, dtype=np.float64)
+                if len(om) != len(rp) - 1:
+                    raise ValueError("omega must have n entries")
+            g = _abi.Graph(len(rp) - 1, rp.ctypes.data, cl.ctypes.data)
+            _abi.check(lib.cia_plan_batch_add(handle, ctypes.byref(g), lb.ctypes.data,
+                                              om.ctypes.data if om is not None else None))
+            n += len(rp) - 1
+        _abi.check(lib.cia_plan_batch_finish(handle))
+        self.n = n
+        self.precision = precision
+        self.dim = 1
+        self.size = n
+        self.instances = self.info()["instances"]
+        return self
+
     @staticmethod
     def _coupling(model, d_sin, d_cos, K, K2, sigma, beta, poly_c=(0.0, 1.0), dV=(0.0,), poly_g=None,
                   fourier_L=None, fourier_C=None):

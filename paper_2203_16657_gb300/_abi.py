@@ -21,7 +21,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "fp32": 1}
 METHOD = {"cia": 0, "direct": 1}
-STAGING = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3}
+STAGING = {"auto": 0, "plain": 1, "window": 2, "pipeline": 3, "stream": 4}
 MODEL = {"kuramoto": 0, "kuramoto_ho": 1, "cucker_smale": 2, "polynomial": 3, "polynomial_general": 4,
          "fourier_general": 5}
 
@@ -136,6 +136,9 @@ SIGNATURES = {
     "cia_plan_destroy": (ctypes.c_int, [_P]),
     "cia_plan_create_batch": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, ctypes.POINTER(Coupling),
                                              ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "cia_plan_batch_begin": (ctypes.c_int, [ctypes.POINTER(Coupling), ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "cia_plan_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(Graph), _P, _P]),
+    "cia_plan_batch_finish": (ctypes.c_int, [_P]),
     "cia_plan_retile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "cia_detect_options_default": (None, [_P]),
     "cia_detect_communities": (ctypes.c_int, [_P, _P, _P, _P]),

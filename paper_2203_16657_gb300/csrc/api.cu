@@ -69,6 +69,7 @@ cia_status check_plan(cia_plan *pl, int method) {
     }
     const size_t need = (method == CIA_METHOD_CIA && pl->staging == 3)   ? pipeline_smem_bytes(pl, pl->ring_stages)
                         : (method == CIA_METHOD_CIA && pl->staging == 2) ? window_smem_bytes(pl)
+                        : (method == CIA_METHOD_CIA && pl->staging == 4) ? stream_smem_bytes(pl)
                         : stage_smem_bytes(pl, method == CIA_METHOD_DIRECT ? Method::DIRECT : Method::CIA);
     if (method == CIA_METHOD_DIRECT && pl->triadic &&
         (size_t)(pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->max_comm > (size_t)optin - 1024)

@@ -27,6 +27,13 @@ cia_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::cia::cuda_fail(_e, #expr);          \
     } while (0)
 
+// Padding entries of the missing-link vectors are lambda_c .. lambda_c +
+// kPadSlots - 1 (each a distinct shared-memory bank group, so that padding
+// never conflicts with a live gather); kernels that stage the community in
+// shared memory keep kPadSlots zero entries after it, the others skip any
+// index >= lambda_c.
+constexpr int kPadSlots = 16;
+
 // Descriptor of one work tile (64 bytes, read by every CIA kernel).
 struct alignas(16) TileDesc {
     int32_t comm, first, count, nsl;      // community (-1: unlabelled), first node, nodes, slices
@@ -52,7 +59,7 @@ struct DeviceBuffers {
     int32_t *comm_tile_begin = nullptr; // [M+1] tiles of community c: [begin[c], begin[c+1])
     // S, split in its two signs, as sliced ELL: a slice is 32 rows of a tile
     // (one per lane), rows ordered by decreasing list length; missing lists
-    // hold 16-bit community-local indices (sentinel lambda_c), inter lists
+    // hold 16-bit community-local indices (padding lambda_c .. lambda_c + 15), inter lists
     // 32-bit permuted ids (sentinel n); vector j of lane r sits at
     // slice_offset + 32 j + r.  Each tile is one contiguous blob:
     //   [slice descriptors: nsl x uint4 (miss offset, miss vectors, inter offset, inter vectors)]
@@ -109,11 +116,14 @@ struct DeviceBuffers {
     int64_t *r_counter = nullptr;             // step index of the next order-parameter row
 };
 
+struct BatchStaging;   // instances of a streamed ensemble plan before cia_plan_batch_finish
+
 // The split of S kept on the host after planning (re-tiling reuses it).
 struct HostSplit {
     std::vector<int32_t> comm_of;              // [n] community of permuted node m, -1 if none
     std::vector<int64_t> miss_cnt, miss_off;   // per row: missing links, offsets into miss_local
-    std::vector<int32_t> miss_local;           // community-local indices, ascending per row
+    std::vector<uint16_t> miss_local;          // community-local indices, ascending per row (only
+                                               // when every community has at most 65535 nodes)
     std::vector<int64_t> inter_cnt, inter_off; // per row: inter links, offsets into inter_col
     std::vector<int32_t> inter_col;            // permuted ids, ascending per row
 };
@@ -141,6 +151,7 @@ struct cia_plan {
     int64_t ph_stride = 0;              // phasor entries per harmonic: n + 1 rounded up to even
     int tile_index_bytes = 24576;
     int64_t max_tile_idx_bytes = 0;     // largest index footprint of one tile (bytes)
+    int64_t max_tile_buf = 0;           // largest window + blob of one tile (persistent per-tile kernel)
     int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0, max_cta_runs = 0;
     int n_ctas = 0;                     // persistent grid of the pipelined CIA kernel (one per SM)
     int ring_stages = 0;                // tile buffers of its TMA ring
@@ -167,6 +178,7 @@ struct cia_plan {
     int64_t B = 1;
     std::vector<int64_t> inst_off;      // [B+1] node offsets (original ids)
     std::vector<int64_t> inst_comm_off; // [B+1] community offsets
+    cia::BatchStaging *batch_stage = nullptr;   // streamed ensemble plan being built
     // CUDA graph of one RK4 step (cached by method, dt, slot and order-parameter output)
     cudaGraphExec_t graph_exec = nullptr;
     int graph_method = -1, graph_slot = -1;
@@ -217,6 +229,8 @@ cudaError_t launch_rk4_stage(cia_plan *pl, int method, int stage, int ph_in_slot
 cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
 size_t stage_smem_bytes(const cia_plan *pl, int method);
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
+size_t stream_smem_bytes(const cia_plan *pl);
+int64_t stream_tile_buf_bytes(const cia_plan *pl, int64_t lam, int64_t blob_bytes);
 size_t window_smem_bytes(const cia_plan *pl);
 
 // Drop the cached CUDA graph of an RK4 step (api.cu).

@@ -35,6 +35,9 @@ constexpr int kWarps = kThreads / 32;
 #ifndef CIA_WINDOW_MIN_BLOCKS
 #define CIA_WINDOW_MIN_BLOCKS 4    // resident CTAs per SM the window kernel's registers are sized for
 #endif
+#ifndef CIA_STREAM_MIN_BLOCKS
+#define CIA_STREAM_MIN_BLOCKS 4    // resident CTAs per SM the persistent per-tile kernel is sized for
+#endif
 #ifndef CIA_WINDOW_VECTORS
 #define CIA_WINDOW_VECTORS 2       // missing-index vectors of a chunk loaded before any is used (<= 8)
 #endif
@@ -97,9 +100,10 @@ __host__ __device__ constexpr size_t zrun_bytes(int64_t runs, int p, size_t comp
     return ((size_t)runs * (size_t)p * complex_bytes + 127) & ~(size_t)127;
 }
 
-// Shared-memory phasor entries per harmonic for TMA staging: lambda_max + 1
-// plus up to one entry on each side from rounding the window to 16 bytes.
-int64_t tma_ph_region(const cia_plan *pl) { return (pl->max_comm + 4) & ~(int64_t)1; }
+// Shared-memory phasor entries per harmonic for TMA staging: lambda_max, the
+// kPadSlots zero entries after it, and up to one entry before it and one
+// after from rounding the window to 16 bytes.
+int64_t tma_ph_region(const cia_plan *pl) { return (pl->max_comm + kPadSlots + 3) & ~(int64_t)1; }
 
 template <typename T>
 struct StageParams {
@@ -140,6 +144,8 @@ struct StageParams {
     double dt;
     int first_stage;
     // TMA staging
+    int64_t n_tiles;           // tiles of the plan (persistent kernels)
+    int tile_buf;              // persistent per-tile kernel: bytes of its window + blob buffer
     int ph_region;             // shared-memory phasor entries per harmonic
     int idx_cap;               // shared-memory index buffer bytes
     int *err_flag;             // set when a bounded wait gives up
@@ -449,7 +455,10 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
         if (dense) mbar_wait_bounded(&wbar, 0, kWaitLimitNs);
         return;
     }
-    if (dense && threadIdx.x < P) win[(size_t)threadIdx.x * a.ph_region + d.shift + d.lam] = mk2(T(0), T(0));
+    // the padding entries lambda .. lambda + kPadSlots - 1 read zero phasors
+    if (dense && threadIdx.x < P * kPadSlots)
+        win[(size_t)(threadIdx.x / kPadSlots) * a.ph_region + d.shift + d.lam + threadIdx.x % kPadSlots] =
+            mk2(T(0), T(0));
     __syncthreads();
 
     for (int s = warp; s < d.nsl; s += kWarps) {
@@ -592,6 +601,265 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     }
     if (MODE == kRhs) return;
     block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
+}
+
+// ---- persistent CIA stage, per-tile staging (staging 4) ---------------------
+//
+// Every CTA walks a fixed sequence of tiles: in round j, CTA c takes the
+// tile of launch rank j G + c (j even) or j G + G - 1 - c (j odd), G the
+// grid -- the costliest-first launch order dealt out in a snake, so that no
+// CTA's total work exceeds another's by more than one tile.  Per tile, one
+// mbarrier phase covers bulk (TMA) copies of the community's phasor window
+// (every harmonic) and of the tile's whole index blob into one shared-memory
+// buffer; Phase A then reads indices and missing-link phasors from shared
+// memory and only the inter-community phasors from global memory.  The
+// copies of the next tile are issued as soon as Phase A of the current one
+// has released the buffer (its descriptor arrives by cp.async during Phase
+// A), and its observable and node inputs are loaded while they fly, so the
+// per-tile setup overlaps Phase B of the current tile.
+template <typename T>
+__device__ __forceinline__ uint32_t stream_window_bytes(const TileDesc &d) {
+    // per harmonic: shift + lambda phasors and the kPadSlots zero entries, 16-byte rounded
+    using C = typename Vec2<T>::type;
+    return d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam + kPadSlots) * sizeof(C) + 15) & ~(size_t)15) : 0u;
+}
+
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(kThreads, CIA_STREAM_MIN_BLOCKS) cia_stream_kernel(const StageParams<T> a) {
+    using C = typename Vec2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ C zc[P];
+    __shared__ double red[kWarps][2 * P];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) TileDesc sd[2];       // this round's tile and the next round's
+    __shared__ int s_tile[2];                      // their tile ids (-1: none)
+
+    unsigned char *buf = smem_raw;                                              // window | blob
+    C *sWm = reinterpret_cast<C *>(smem_raw + a.tile_buf);                      // [P][kMaxChunks]
+    C *sWi = sWm + P * kMaxChunks;                                              // [P][tile_nodes]
+    const int64_t stride = a.ph_stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    auto rank_of = [&](int j) -> int64_t {
+        return (int64_t)j * G + ((j & 1) ? G - 1 - (int)blockIdx.x : (int)blockIdx.x);
+    };
+    auto tile_at = [&](int j) -> int { return rank_of(j) < a.n_tiles ? a.tile_order[rank_of(j)] : -1; };
+    // copies of one tile's window and blob, one mbarrier phase (thread 0)
+    auto issue = [&](const TileDesc &d) {
+        const uint32_t wreg = stream_window_bytes<T>(d);
+        const uint32_t wbytes = d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam) * sizeof(C) + 15) & ~(size_t)15) : 0u;
+        mbar_arrive_expect_tx(&bar, wbytes * P + d.blob_bytes);
+        if (wbytes)
+            for (int k = 0; k < P; ++k)
+                bulk_g2s(buf + (size_t)k * wreg, a.ph_in + k * stride + (d.lo - d.shift), wbytes, &bar);
+        if (d.blob_bytes) bulk_g2s(buf + (size_t)P * wreg, a.blob + d.blob_off, d.blob_bytes, &bar);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        const int t0 = tile_at(0), t1 = tile_at(1);
+        s_tile[0] = t0;
+        s_tile[1] = t1;
+        if (t0 >= 0) {
+            sd[0] = a.tile_desc[t0];
+            issue(sd[0]);
+        }
+    }
+    __syncthreads();
+    int t = s_tile[0];
+    if (t < 0) return;
+
+    // node inputs of the current tile (registers) and its observable (warp 0)
+    const int r = threadIdx.x;
+    double theta_m = 0.0, wdt64_m = 0.0;
+    T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
+    int32_t perm_m = 0;
+    auto load_inputs = [&](const TileDesc &d) {
+        if (r < d.count) {
+            const int64_t m = d.first + r;
+            if (MODE == kRhs) {
+                omega_m = a.omega[m];
+                perm_m = a.perm[m];
+            } else {
+                theta_m = a.theta[m];
+                if (!a.first_stage) acc_m = a.acc[m];
+                if (MODE == kStage) wdt_m = a.wdt_next[m];
+                else wdt64_m = a.wdt64[m];
+            }
+        }
+    };
+    load_inputs(sd[0]);
+    if (sd[0].comm >= 0) community_observable<T, P>(a, sd[0].comm, zc);
+
+    for (int j = 0;; ++j) {
+        const int cur = j & 1, nxt = cur ^ 1;
+        const int tn = s_tile[nxt];
+        const TileDesc &d = sd[cur];
+        const bool dense = d.comm >= 0;
+        bool ok = mbar_wait_bounded(&bar, (uint32_t)(j & 1), kWaitLimitNs);
+        if (!ok && threadIdx.x == 0) atomicExch(a.err_flag, 1);
+        if (__syncthreads_or(!ok)) {
+            // the copies may still land: wait for them once more before the
+            // CTA's shared memory is released
+            mbar_wait_bounded(&bar, (uint32_t)(j & 1), kWaitLimitNs);
+            return;
+        }
+        const uint32_t wreg = stream_window_bytes<T>(d);
+        const int wstride = (int)(wreg / sizeof(C));                 // entries between harmonics
+        const C *cw = reinterpret_cast<const C *>(buf) + d.shift;   // cw[k * wstride + l]
+        // the padding entries lambda .. lambda + kPadSlots - 1 read zero phasors
+        if (dense && threadIdx.x < P * kPadSlots)
+            reinterpret_cast<C *>(buf)[(threadIdx.x / kPadSlots) * wstride + d.shift + d.lam +
+                                       threadIdx.x % kPadSlots] = mk2(T(0), T(0));
+        __syncthreads();
+        const unsigned char *b = buf + (size_t)P * wreg;
+        const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
+        const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
+        const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
+        const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
+        const bool live = r < d.count;
+        const int64_t m = d.first + r;
+        const int lo = (int)d.lo, first = d.first;
+        const uint32_t vt = live ? reinterpret_cast<const uint32_t *>(b + d.vtab_off)[r] : 0u;
+        C um[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            um[k] = !live ? mk2(T(0), T(0)) : dense ? cw[k * wstride + (first + r - lo)] : __ldg(a.ph_in + k * stride + m);
+        // the next round's descriptor (async, into the other slot) and tile id
+        if (warp == 0 && lane < 4 && tn >= 0)
+            cp_async16(reinterpret_cast<uint4 *>(&sd[nxt]) + lane, reinterpret_cast<const uint4 *>(a.tile_desc + tn) + lane);
+        const int t2 = threadIdx.x == 0 ? tile_at(j + 2) : -1;
+
+        // Phase A: warp per slice, lane per row
+        for (int sl = warp; sl < d.nsl; sl += kWarps) {
+            const uint4 sdv = sdesc[sl];
+            const uint32_t rows = srows[sl * 32 + lane];
+            const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+            C macc[P], iacc[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) macc[k] = iacc[k] = mk2(T(0), T(0));
+            const int4 *iv = ivec + sdv.z + lane;
+            const uint4 *mv = mvec + sdv.x + lane;
+            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;   // inter vectors gathered ahead
+            for (uint32_t j0 = 0; j0 < sdv.w || j0 == 0; j0 += kPre) {
+                C pre[kPre][4][P];
+#pragma unroll
+                for (uint32_t q = 0; q < kPre; ++q) {
+                    if (j0 + q < sdv.w) {
+                        const int4 iq = iv[32 * (j0 + q)];
+                        const int l4[4] = {iq.x, iq.y, iq.z, iq.w};
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                            for (int k = 0; k < P; ++k) pre[q][hh][k] = __ldg(a.ph_in + k * stride + l4[hh]);
+                    }
+                }
+                if (j0 == 0) {
+                    // missing links from the shared-memory window while the gathers fly
+#pragma unroll 2
+                    for (uint32_t jj = 0; jj < sdv.y; ++jj) {
+                        const uint4 mq = mv[32 * jj];
+                        const uint32_t w4[4] = {mq.x, mq.y, mq.z, mq.w};
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh) {
+                            const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
+#pragma unroll
+                            for (int k = 0; k < P; ++k)
+                                macc[k] = add2(macc[k], add2(cw[k * wstride + l0], cw[k * wstride + l1]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < kPre; ++q) {
+                    if (j0 + q < sdv.w) {
+#pragma unroll
+                        for (int k = 0; k < P; ++k)
+                            iacc[k] = add2(iacc[k], add2(add2(pre[q][0][k], pre[q][1][k]), add2(pre[q][2][k], pre[q][3][k])));
+                    }
+                }
+            }
+            if (mrow != 0xffffu) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) sWm[k * kMaxChunks + mrow] = mk2(-macc[k].x, -macc[k].y);
+            }
+            if (irow != 0xffffu) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) sWi[k * a.tile_nodes + irow] = iacc[k];
+            }
+        }
+        if (warp == 0 && lane < 4) cp_async_wait_all();
+        __syncthreads();   // Phase A done: window and blob free, sums complete, next descriptor landed
+        if (threadIdx.x == 0) {
+            if (tn >= 0) {
+                fence_proxy_async_smem();
+                issue(sd[nxt]);
+            }
+            s_tile[cur] = t2;
+        }
+
+        // Phase B, thread per node
+        T sre[P], sim[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
+        if (live) {
+            T coup = T(0);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const C u = um[k];
+                C w = sWi[k * a.tile_nodes + r];
+                for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
+                    const C v = sWm[k * kMaxChunks + c];
+                    w.x += v.x;
+                    w.y += v.y;
+                }
+                T zr = w.x, zi = w.y;
+                if (dense) {
+                    // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
+                    zr += zc[k].x - u.x;
+                    zi += zc[k].y - u.y;
+                }
+                const T re = zr * u.x + zi * u.y;
+                const T im = zi * u.x - zr * u.y;
+                coup += a.d_sin[k] * im + a.d_cos[k] * re;
+            }
+            coup *= a.tile_kn ? a.tile_kn[t] : a.k_over_n;
+            if (P >= 2 && dense && a.k2_over_n2 != T(0))
+                coup += a.k2_over_n2 * triadic_from_moments<T>(zc[0].x, zc[0].y, zc[P >= 2 ? 1 : 0].x,
+                                                               zc[P >= 2 ? 1 : 0].y, um[0].x, um[0].y,
+                                                               um[P >= 2 ? 1 : 0].x, um[P >= 2 ? 1 : 0].y);
+            if (a.tri) coup += a.tri[m];
+            if (MODE == kRhs) {
+                a.rhs_out[perm_m] = (double)omega_m + (double)coup;
+            } else {
+                const T accv = acc_m + a.b_s * coup;
+                T y;
+                if (MODE == kStage) {
+                    a.acc[m] = accv;
+                    y = (T)theta_m + wdt_m + a.c_next_dt * coup;
+                } else {
+                    // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
+                    const double th = wrap_pi(theta_m + wdt64_m + a.dt * (double)accv);
+                    a.theta[m] = th;
+                    y = (T)th;
+                }
+                C u[P];
+                phasors<T, P>(y, u);
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    a.ph_out[k * stride + m] = u[k];
+                    sre[k] = u[k].x;
+                    sim[k] = u[k].y;
+                }
+            }
+        }
+        if (MODE != kRhs) block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
+        else __syncthreads();   // zc is read above before warp 0 replaces it
+        if (tn < 0) break;
+        // the next tile's node inputs and observable, while its copies fly
+        load_inputs(sd[nxt]);
+        if (sd[nxt].comm >= 0) community_observable<T, P>(a, sd[nxt].comm, zc);
+        t = tn;
+    }
 }
 
 // ---- persistent, warp-specialised CIA stage (the main path) ----------------
@@ -802,10 +1070,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                 fail = s_prod_abort || !mbar_wait_bounded(&full_bar[s], k & 1, kWaitLimitNs);
                 if (!fail && dense) {
                     fail = !mbar_wait_bounded(&pfull_bar[h.pbuf], (h.run >> 1) & 1, kWaitLimitNs);
-                    // the slot after the community is where padding entries point: zero it
+                    // the slots after the community are where padding entries point: zero them
                     if (!fail)
                         for (int kk = 0; kk < P; ++kk)
-                            pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam] = mk2(T(0), T(0));
+                            for (int j = 0; j < kPadSlots; ++j)
+                                pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam + j] = mk2(T(0), T(0));
                 }
                 if (!fail && u >= 1) fail = !mbar_wait_bounded(&swempty_bar[b], (u - 1) & 1, kWaitLimitNs);
                 if (fail) {
@@ -1305,6 +1574,8 @@ StageParams<T> base_params(cia_plan *pl, int method) {
     a.acc = (T *)pl->d.acc;
     a.theta = pl->d.theta;
     a.wdt64 = pl->d.wdt_full64;
+    a.n_tiles = pl->n_tiles;
+    a.tile_buf = (int)((pl->max_tile_buf + 127) & ~(int64_t)127);
     a.ph_region = (int)tma_ph_region(pl);
     a.idx_cap = (int)((pl->max_tile_idx_bytes + 15) & ~(int64_t)15);
     a.err_flag = pl->d.err_flag;
@@ -1338,6 +1609,17 @@ cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream
     }
     if (pl->staging == 2)
         return launch_kernel(cia_window_kernel<T, P, MODE>, pl, pl->n_tiles, window_smem_bytes(pl), &a, s);
+    if (pl->staging == 4) {
+        auto kernel = cia_stream_kernel<T, P, MODE>;
+        const size_t smem = stream_smem_bytes(pl);
+        cudaError_t e = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kernel, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(pl->n_tiles, (int64_t)std::max(per_sm, 1) * pl->n_sms));
+        return launch_kernel(kernel, pl, grid, smem, &a, s);
+    }
     return launch_kernel(cia_stage_kernel<T, P, MODE>, pl, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
 }
 
@@ -1435,6 +1717,23 @@ size_t stage_smem_bytes(const cia_plan *pl, int method) {
 size_t window_smem_bytes(const cia_plan *pl) {
     const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
     return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes);
+}
+
+// Dynamic shared memory of the persistent per-tile kernel: the largest tile's
+// window (every harmonic) and index blob, then chunk sums and inter sums.
+size_t stream_smem_bytes(const cia_plan *pl) {
+    const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
+    return (size_t)((pl->max_tile_buf + 127) & ~(int64_t)127) + cb * (size_t)(kMaxChunks + pl->tile_nodes);
+}
+
+// Bytes of the per-tile buffer of the persistent per-tile kernel for a tile
+// of a community of lam nodes (lam = 0: free nodes) with a blob of the given
+// size; the window rounding is the device's with the larger shift.
+int64_t stream_tile_buf_bytes(const cia_plan *pl, int64_t lam, int64_t blob_bytes) {
+    const int64_t cb = pl->precision == CIA_FP64 ? 16 : 8;
+    const int64_t shift = pl->precision == CIA_FP64 ? 0 : 1;
+    const int64_t wreg = lam > 0 ? ((shift + lam + kPadSlots) * cb + 15) & ~(int64_t)15 : 0;
+    return (int64_t)pl->p * wreg + blob_bytes;
 }
 
 // Dynamic shared memory of the pipelined CIA kernel: a ring of tile buffers

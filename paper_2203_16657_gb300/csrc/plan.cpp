@@ -77,7 +77,30 @@ static int64_t instance_of_node(const cia_plan *pl, int64_t id) {
     return (int64_t)(std::upper_bound(pl->inst_off.begin(), pl->inst_off.end(), id) - pl->inst_off.begin()) - 1;
 }
 
+// One instance of a streamed ensemble plan, split, kept until the plan is
+// finished: rows in the instance's permuted order (its labelled nodes, then
+// its free ones).
+struct StagedInstance {
+    int64_t n = 0, n_lab = 0, M = 0, nnz = 0, max_comm = 0;
+    std::vector<int32_t> perm;       // [n] permuted -> original id within the instance
+    std::vector<int64_t> off;        // [M + 1] community offsets within the instance
+    std::vector<int64_t> miss_cnt;   // [n_lab] missing links per labelled row
+    std::vector<uint16_t> miss;      // community-local indices, rows in order
+    std::vector<int64_t> inter_cnt;  // [n] inter links per row
+    std::vector<int64_t> inter;      // targets: >= 0 the ensemble's permuted id of a labelled
+                                     // node; < 0: -1 - (index among all free nodes so far)
+    std::vector<double> omega;       // [n] natural frequencies, permuted (empty: zero)
+};
+
+struct BatchStaging {
+    cia_options opt{};
+    std::vector<StagedInstance> inst;
+    int64_t lab_total = 0, free_total = 0, comm_total = 0, n_total = 0;
+};
+
 static void free_all(cia_plan *pl) {
+    delete pl->batch_stage;
+    pl->batch_stage = nullptr;
     invalidate_graphs(pl);
     if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
     pl->capture_stream = nullptr;
@@ -118,54 +141,223 @@ static const int64_t kChunk = 64;
 // Most chunks per tile (shared-memory partial sums of one consumer group).
 static const int64_t kMaxChunks = 512;
 
-// Scratch of schedule_missing (one per planning thread).
+// Scratch of the missing-link scheduler (one per planning thread).
 struct MissScheduler {
-    std::vector<int32_t> bucket[32][16];   // remaining entries of each lane by bank pair
+    std::vector<int32_t> bucket[32][16];   // greedy: remaining entries of each lane by bank group
+    std::vector<int32_t> lane_at;          // colouring: [lane][colour] entry, -1 = free
+    std::vector<int32_t> grp_at;           // colouring: [bank group][colour] lane, -1 = free
+    std::vector<int32_t> path;             // colouring: (lane, group, colour) triples of a swap path
+    std::vector<int32_t> later;            // colouring: (lane, entry) pairs whose bank group is full
+    std::vector<uint16_t> out;             // [position][32] scheduled entries of one slice
 };
 
-// Fill the missing-link vectors of one slice (32 lanes, nvm vectors of 8
-// entries each).  Lane l sums the entries ent[l][0..len[l]); their order is
-// free, so it is chosen such that at every entry position the live lanes of
-// each group of G lanes use distinct shared-memory bank groups (community-
-// local index mod G) whenever their remaining entries allow -- the gathers of
-// one step are then free of bank conflicts.  G = 16 for 8-byte elements (a
-// warp's 8-byte loads are served per half-warp), G = 8 for 16-byte elements
-// (per quarter-warp).  Lanes with fewer remaining entries pick first, each
-// taking an unused bank group from its largest bucket.
-static void schedule_missing(const int32_t *const ent[32], const int64_t len[32], int64_t nvm,
-                             uint16_t sentinel, uint16_t *out, MissScheduler &sc, int G) {
-    int remaining[32];
-    for (int lane = 0; lane < 32; ++lane) {
-        for (auto &b : sc.bucket[lane]) b.clear();
-        for (int64_t e = 0; e < len[lane]; ++e) sc.bucket[lane][ent[lane][e] & (G - 1)].push_back(ent[lane][e]);
-        remaining[lane] = (int)len[lane];
+// Extra 8-entry vectors per slice that the conflict-free schedule may add
+// beyond the longest lane's list (padding entries read the zero slots).
+#ifndef CIA_SCHED_EXTRA_VECTORS
+#define CIA_SCHED_EXTRA_VECTORS 1
+#endif
+
+// Set of colours (positions) < 128.
+struct ColourSet {
+    uint64_t w[2] = {0, 0};
+    void fill(int64_t n) {
+        w[0] = n >= 64 ? ~0ull : ((1ull << n) - 1);
+        w[1] = n >= 128 ? ~0ull : n > 64 ? ((1ull << (n - 64)) - 1) : 0ull;
     }
-    for (int64_t pos = 0; pos < 8 * nvm; ++pos) {
-        const int64_t j = pos / 8, h = pos % 8;
-        for (int grp = 0; grp < 32 / G; ++grp) {
-            int order[16];
-            for (int q = 0; q < G; ++q) order[q] = G * grp + q;
-            std::stable_sort(order, order + G, [&](int x, int y) { return remaining[x] < remaining[y]; });
-            unsigned used = 0;
-            for (int q = 0; q < G; ++q) {
-                const int lane = order[q];
-                uint16_t v = sentinel;
-                if (remaining[lane] > 0) {
-                    int best = -1;
-                    for (int pass = 0; pass < 2 && best < 0; ++pass)
-                        for (int c = 0; c < G; ++c) {
-                            if (sc.bucket[lane][c].empty() || (pass == 0 && (used >> c & 1u))) continue;
-                            if (best < 0 || sc.bucket[lane][c].size() > sc.bucket[lane][best].size()) best = c;
-                        }
-                    v = (uint16_t)sc.bucket[lane][best].back();
-                    sc.bucket[lane][best].pop_back();
-                    --remaining[lane];
-                    used |= 1u << best;
+    bool has(int64_t c) const { return (w[c >> 6] >> (c & 63)) & 1ull; }
+    void set(int64_t c) { w[c >> 6] |= 1ull << (c & 63); }
+    void clear(int64_t c) { w[c >> 6] &= ~(1ull << (c & 63)); }
+    int64_t first() const { return w[0] ? __builtin_ctzll(w[0]) : w[1] ? 64 + __builtin_ctzll(w[1]) : -1; }
+};
+
+// Greedy order of one group of G lanes (fallback): at each position the
+// lanes with fewer remaining entries pick first, each taking an unused bank
+// group from its largest bucket.
+static void greedy_group(const uint16_t *const ent[], const int64_t len[], int G, int64_t ncol, int32_t *lane_at,
+                         MissScheduler &sc) {
+    int remaining[16];
+    for (int u = 0; u < G; ++u) {
+        for (auto &bk : sc.bucket[u]) bk.clear();
+        for (int64_t e = 0; e < len[u]; ++e) sc.bucket[u][ent[u][e] & (G - 1)].push_back(ent[u][e]);
+        remaining[u] = (int)len[u];
+    }
+    for (int64_t p = 0; p < ncol; ++p) {
+        int order[16];
+        for (int q = 0; q < G; ++q) order[q] = q;
+        std::stable_sort(order, order + G, [&](int x, int y) { return remaining[x] < remaining[y]; });
+        unsigned used = 0;
+        for (int q = 0; q < G; ++q) {
+            const int u = order[q];
+            lane_at[(size_t)u * ncol + p] = -1;
+            if (remaining[u] == 0) continue;
+            int best = -1;
+            for (int pass = 0; pass < 2 && best < 0; ++pass)
+                for (int c = 0; c < G; ++c) {
+                    if (sc.bucket[u][c].empty() || (pass == 0 && (used >> c & 1u))) continue;
+                    if (best < 0 || sc.bucket[u][c].size() > sc.bucket[u][best].size()) best = c;
                 }
-                out[8 * (32 * j + lane) + h] = v;
+            lane_at[(size_t)u * ncol + p] = sc.bucket[u][best].back();
+            sc.bucket[u][best].pop_back();
+            --remaining[u];
+            used |= 1u << best;
+        }
+    }
+}
+
+// Edge colouring of one group of G lanes (see schedule_slice); false if a
+// swap path ran longer than the graph allows (the caller then falls back).
+static bool colour_group(const uint16_t *const ent[], const int64_t len[], int G, int64_t ncol, MissScheduler &sc) {
+    int32_t *LA = sc.lane_at.data();   // [u * ncol + c]
+    int32_t *GA = sc.grp_at.data();    // [g * ncol + c]
+    std::fill(LA, LA + (size_t)G * ncol, -1);
+    std::fill(GA, GA + (size_t)G * ncol, -1);
+    ColourSet lane_free[16], grp_free[16];
+    for (int v = 0; v < G; ++v) {
+        lane_free[v].fill(ncol);
+        grp_free[v].fill(ncol);
+    }
+    sc.later.clear();
+    const int64_t max_steps = 2 * (int64_t)G * ncol + 2;
+    for (int u = 0; u < G; ++u) {
+        for (int64_t k = 0; k < len[u]; ++k) {
+            const int32_t e = ent[u][k];
+            const int g = e & (G - 1);
+            const int64_t ca = lane_free[u].first();   // exists: len <= ncol
+            const int64_t cb = grp_free[g].first();
+            if (cb < 0) {                              // bank group full: placed after the colouring
+                sc.later.insert(sc.later.end(), {u, e});
+                continue;
+            }
+            int64_t c = ca;
+            if (!grp_free[g].has(ca)) {
+                if (lane_free[u].has(cb)) {
+                    c = cb;
+                } else {
+                    // swap ca <-> cb along the alternating path from g that starts with ca
+                    sc.path.clear();
+                    int node = g;
+                    bool at_group = true;
+                    int64_t col = ca;
+                    for (int64_t step = 0;; ++step) {
+                        if (step > max_steps) return false;
+                        if (at_group) {
+                            const int32_t lu = GA[(size_t)node * ncol + col];
+                            if (lu < 0) break;
+                            sc.path.insert(sc.path.end(), {lu, node, (int32_t)col});
+                            node = lu;
+                        } else {
+                            const int32_t ee = LA[(size_t)node * ncol + col];
+                            if (ee < 0) break;
+                            sc.path.insert(sc.path.end(), {node, ee & (G - 1), (int32_t)col});
+                            node = ee & (G - 1);
+                        }
+                        at_group = !at_group;
+                        col = col == ca ? cb : ca;
+                    }
+                    const size_t np = sc.path.size() / 3;
+                    std::vector<int32_t> moved(np);
+                    for (size_t i = 0; i < np; ++i) {
+                        const int32_t lu = sc.path[3 * i], gg = sc.path[3 * i + 1], cc = sc.path[3 * i + 2];
+                        moved[i] = LA[(size_t)lu * ncol + cc];
+                        LA[(size_t)lu * ncol + cc] = -1;
+                        GA[(size_t)gg * ncol + cc] = -1;
+                    }
+                    for (size_t i = 0; i < np; ++i) {
+                        const int32_t lu = sc.path[3 * i], gg = sc.path[3 * i + 1], cc = sc.path[3 * i + 2];
+                        const int64_t nc = cc == ca ? cb : ca;
+                        LA[(size_t)lu * ncol + nc] = moved[i];
+                        GA[(size_t)gg * ncol + nc] = lu;
+                    }
+                    for (size_t i = 0; i < np; ++i) {
+                        const int32_t lu = sc.path[3 * i], gg = sc.path[3 * i + 1];
+                        for (const int64_t cc : {ca, cb}) {
+                            if (LA[(size_t)lu * ncol + cc] < 0) lane_free[lu].set(cc); else lane_free[lu].clear(cc);
+                            if (GA[(size_t)gg * ncol + cc] < 0) grp_free[gg].set(cc); else grp_free[gg].clear(cc);
+                        }
+                    }
+                }
+            }
+            LA[(size_t)u * ncol + c] = e;
+            GA[(size_t)g * ncol + c] = u;
+            lane_free[u].clear(c);
+            grp_free[g].clear(c);
+        }
+    }
+    // entries of full bank groups: any free position of their lane (a conflict)
+    for (size_t i = 0; i < sc.later.size(); i += 2) {
+        const int u = sc.later[i];
+        const int64_t c = lane_free[u].first();
+        LA[(size_t)u * ncol + c] = sc.later[i + 1];
+        lane_free[u].clear(c);
+    }
+    return true;
+}
+
+// Order the missing-link entries of one slice (32 lanes, lane l sums
+// ent[l][0..len[l])) into positions: at position p every lane reads one
+// entry (or a padding entry), and the kernels issue one shared-memory gather
+// per position for the whole warp.  A warp's 8-byte loads are served per
+// half-warp (G = 16 lanes, 16 bank groups of 8 bytes: the community-local
+// index mod 16), 16-byte loads per quarter-warp (G = 8); a position is free
+// of bank conflicts when the live lanes of each group of G lanes use distinct
+// bank groups.  For each group of G lanes this is an edge colouring of the
+// bipartite multigraph lanes x bank groups (one edge per entry, colours =
+// positions): with as many colours as the largest degree (the longest list,
+// or the most entries of the G lanes in one bank group) a colouring exists
+// (Koenig's theorem); it is built edge by edge, swapping the two colours
+// along an alternating path when no colour is free at both ends.  Positions
+// are capped at the longest list rounded up to 8 plus CIA_SCHED_EXTRA_VECTORS
+// vectors; entries of a bank group that then has no free position are placed
+// last, at free positions of their lanes (conflicts).  Padding entries take
+// distinct unused bank groups: sentinel + j, j in [0, G), all of them zero
+// slots after the community window, when `spread` allows (else the sentinel
+// itself).  Returns the number of positions (a multiple of 8);
+// sc.out[p * 32 + lane].
+static int64_t schedule_slice(const uint16_t *const ent[32], const int64_t len[32], int G, uint16_t sentinel,
+                              bool spread, MissScheduler &sc) {
+    int64_t maxlen = 0;
+    for (int lane = 0; lane < 32; ++lane) maxlen = std::max(maxlen, len[lane]);
+    const int64_t npos_min = (maxlen + 7) / 8 * 8;
+    int64_t delta = maxlen;
+    for (int q = 0; q < 32 / G; ++q) {
+        int64_t load[16] = {0};
+        for (int u = 0; u < G; ++u)
+            for (int64_t e = 0; e < len[q * G + u]; ++e) ++load[ent[q * G + u][e] & (G - 1)];
+        for (int g = 0; g < G; ++g) delta = std::max(delta, load[g]);
+    }
+    const int64_t ncol = std::min<int64_t>(std::min<int64_t>((delta + 7) / 8 * 8, npos_min + 8 * CIA_SCHED_EXTRA_VECTORS), 128);
+    sc.out.assign((size_t)ncol * 32, sentinel);
+    if (ncol == 0) return 0;
+    sc.lane_at.resize((size_t)G * ncol);
+    sc.grp_at.resize((size_t)G * ncol);
+    for (int q = 0; q < 32 / G; ++q) {
+        if (!colour_group(ent + q * G, len + q * G, G, ncol, sc))
+            greedy_group(ent + q * G, len + q * G, G, ncol, sc.lane_at.data(), sc);
+        const int32_t *LA = sc.lane_at.data();
+        // padding entries: distinct bank groups unused at their position
+        for (int64_t p = 0; p < ncol; ++p) {
+            unsigned used = 0;
+            for (int u = 0; u < G; ++u)
+                if (LA[(size_t)u * ncol + p] >= 0) used |= 1u << (LA[(size_t)u * ncol + p] & (G - 1));
+            int g = 0;
+            for (int u = 0; u < G; ++u) {
+                const int32_t e = LA[(size_t)u * ncol + p];
+                uint16_t v;
+                if (e >= 0) {
+                    v = (uint16_t)e;
+                } else if (spread) {
+                    while (g < G && (used >> g & 1u)) ++g;
+                    const int gg = g < G ? g : (sentinel & (G - 1));
+                    v = (uint16_t)(sentinel + ((gg - sentinel) & (G - 1)));
+                    if (g < G) used |= 1u << g;
+                } else {
+                    v = sentinel;
+                }
+                sc.out[(size_t)p * 32 + q * G + u] = v;
             }
         }
     }
+    return ncol;
 }
 
 // One tile's blob (see cia::DeviceBuffers): slice descriptors, row maps, the
@@ -178,9 +370,9 @@ struct TileBlob {
 
 static int64_t chunks_of(int64_t entries) { return std::max<int64_t>(1, (entries + kChunk - 1) / kChunk); }
 
-static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inter_sent, int bank_lanes,
-                            const std::vector<int64_t> &miss_cnt, const std::vector<int64_t> &miss_off,
-                            const std::vector<int32_t> &miss_local, const std::vector<int64_t> &inter_cnt,
+static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, bool spread, int32_t inter_sent,
+                            int bank_lanes, const std::vector<int64_t> &miss_cnt, const std::vector<int64_t> &miss_off,
+                            const std::vector<uint16_t> &miss_local, const std::vector<int64_t> &inter_cnt,
                             const std::vector<int64_t> &inter_off, const std::vector<int32_t> &inter_col,
                             TileBlob &tb, MissScheduler &sc) {
     // chunks: row r's missing list in v_r nearly equal contiguous pieces,
@@ -205,10 +397,21 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inte
     std::stable_sort(mo.begin(), mo.end(), [&](int32_t x, int32_t y) { return ch[x].len > ch[y].len; });
     std::stable_sort(io.begin(), io.end(), [&](int32_t x, int32_t y) { return inter_cnt[f + x] > inter_cnt[f + y]; });
     const int64_t nsm = (V + 31) / 32, nsi = (cnt + 31) / 32, nsl = std::max(nsm, nsi);
+    // schedule every slice's missing entries first: the schedule fixes its vector count
     std::vector<int64_t> nvm(nsl, 0), nvi(nsl, 0);
+    std::vector<std::vector<uint16_t>> sched(nsl);
     int64_t mv = 0, iv = 0;
     for (int64_t s = 0; s < nsl; ++s) {
-        if (s < nsm) nvm[s] = (ch[mo[32 * s]].len + 7) / 8;
+        const uint16_t *ent[32];
+        int64_t len[32];
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t ms = 32 * s + lane;
+            const Chunk *c = ms < V ? &ch[mo[ms]] : nullptr;
+            ent[lane] = c ? miss_local.data() + miss_off[f + c->row] + c->e0 : nullptr;
+            len[lane] = c ? c->len : 0;
+        }
+        nvm[s] = s < nsm ? schedule_slice(ent, len, bank_lanes, msent, spread, sc) / 8 : 0;
+        sched[s].swap(sc.out);
         if (s < nsi) nvi[s] = (inter_cnt[f + io[32 * s]] + 3) / 4;
         mv += 32 * nvm[s];
         iv += 32 * nvi[s];
@@ -229,36 +432,29 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, int32_t inte
         desc[4 * s + 1] = (uint32_t)nvm[s];
         desc[4 * s + 2] = (uint32_t)iv;
         desc[4 * s + 3] = (uint32_t)nvi[s];
-        const int32_t *ent[32];
-        int64_t len[32];
         for (int lane = 0; lane < 32; ++lane) {
             const int64_t ms = 32 * s + lane;
             const bool mlive = ms < V, ilive = ms < cnt;
-            const Chunk *c = mlive ? &ch[mo[ms]] : nullptr;
-            ent[lane] = mlive ? miss_local.data() + miss_off[f + c->row] + c->e0 : nullptr;
-            len[lane] = mlive ? c->len : 0;
             const int32_t ir = ilive ? io[ms] : -1;
-            rows[32 * s + lane] = (uint32_t)(mlive ? c->vidx : 0xffff) | ((uint32_t)(ilive ? ir : 0xffff) << 16);
+            rows[32 * s + lane] = (uint32_t)(mlive ? ch[mo[ms]].vidx : 0xffff) | ((uint32_t)(ilive ? ir : 0xffff) << 16);
             for (int64_t j = 0; j < nvi[s]; ++j)
                 for (int h = 0; h < 4; ++h) {
                     const int64_t e = 4 * j + h;
                     const bool has = ilive && e < inter_cnt[f + ir];
                     ivec[4 * (iv + 32 * j + lane) + h] = has ? inter_col[inter_off[f + ir] + e] : inter_sent;
                 }
+            // position p of the schedule is entry h = p % 8 of vector j = p / 8
+            for (int64_t p = 0; p < 8 * nvm[s]; ++p)
+                mvec[8 * (mv + 32 * (p / 8) + lane) + (p % 8)] = sched[s][(size_t)p * 32 + lane];
         }
-        schedule_missing(ent, len, nvm[s], msent, mvec + 8 * mv, sc, bank_lanes);
         mv += 32 * nvm[s];
         iv += 32 * nvi[s];
     }
 }
 
-// Phase 1 of planning: options, model, validation, kappa and the split of S
-// into the host lists kept by the plan (pl->hs), the direct method's CSR and
-// every device buffer that does not depend on the tiling.
-static cia_status build_split(const cia_graph *g, const int32_t *community, const double *omega,
-                              const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
-    const int64_t n = g->n;
-    // ---- options and model
+// Options and model of a plan (no graph yet); has_omega: natural
+// frequencies are given.
+static cia_status configure(const cia_coupling *cp, const cia_options *opt, bool has_omega, cia_plan *pl) {
     pl->precision = opt ? opt->precision : CIA_FP64;
     if (pl->precision != CIA_FP64 && pl->precision != CIA_FP32)
         return fail(CIA_ERR_INVALID_ARG, "unknown precision");
@@ -270,7 +466,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     if (pl->tile_index_bytes < 256 || pl->tile_index_bytes % 16)
         return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
     pl->staging = opt ? opt->staging : 0;
-    if (pl->staging < 0 || pl->staging > 3) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2 or 3");
+    if (pl->staging < 0 || pl->staging > 4) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2, 3 or 4");
     pl->use_graphs = opt ? opt->use_graphs : 0;
     if (pl->use_graphs != 0 && pl->use_graphs != 1) return fail(CIA_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (cp->model != CIA_MODEL_KURAMOTO && cp->model != CIA_MODEL_KURAMOTO_HO &&
@@ -283,7 +479,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         const bool fourier = cp->model == CIA_MODEL_FOURIER_GENERAL;
         if (pl->precision != CIA_FP64)
             return fail(CIA_ERR_UNSUPPORTED, "the polynomial and Fourier couplings run in FP64 (precision CIA_FP64)");
-        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial and Fourier couplings");
+        if (has_omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the polynomial and Fourier couplings");
         if (!fourier && (cp->p < 0 || cp->p > CIA_MAX_POLY))
             return fail(CIA_ERR_INVALID_ARG, "p must be in [0, CIA_MAX_POLY]");
         if (fourier && (cp->p < 1 || cp->p > CIA_MAX_HARMONICS))
@@ -354,7 +550,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     } else if (cp->model == CIA_MODEL_CUCKER_SMALE) {
         if (pl->precision != CIA_FP32)
             return fail(CIA_ERR_UNSUPPORTED, "the Cucker-Smale model runs in FP32 (precision CIA_FP32)");
-        if (omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the Cucker-Smale model");
+        if (has_omega) return fail(CIA_ERR_INVALID_ARG, "omega must be NULL for the Cucker-Smale model");
         if (!std::isfinite(cp->K) || !std::isfinite(cp->sigma) || !std::isfinite(cp->beta))
             return fail(CIA_ERR_NUMERIC, "K, sigma or beta is not finite");
         if (!(cp->sigma > 0.0)) return fail(CIA_ERR_INVALID_ARG, "sigma must be positive");
@@ -388,11 +584,14 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     }
     for (int k = cp->p; k < CIA_MAX_HARMONICS; ++k) pl->d_sin[k] = pl->d_cos[k] = 0.0;
     }
-    if (omega)
-        for (int64_t i = 0; i < n; ++i)
-            if (!std::isfinite(omega[i]))
-                return fail(CIA_ERR_NUMERIC, "omega[" + std::to_string(i) + "] is not finite");
+    return CIA_OK;
+}
 
+// Validation of A, kappa and the split of S into the host lists kept by the
+// plan (pl->hs) and, with the direct method, its padded permuted CSR.
+static cia_status split_graph(const cia_graph *g, const int32_t *community, cia_plan *pl,
+                              std::vector<int64_t> &full_rp, std::vector<int32_t> &full_col) {
+    const int64_t n = g->n;
     // ---- validate A
     cia_status st = validate_graph(g);
     if (st != CIA_OK) return st;
@@ -450,12 +649,11 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         inter_cnt[m] = deg - inside;
     }
     auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
-    auto pad8 = [](int64_t x) { return (x + 7) & ~(int64_t)7; };
     hs.miss_off.assign(n + 1, 0);
     hs.inter_off.assign(n + 1, 0);
     auto &miss_off = hs.miss_off;
     auto &inter_off = hs.inter_off;
-    std::vector<int64_t> full_rp;
+    full_rp.clear();
     for (int64_t m = 0; m < n; ++m) {
         miss_off[m + 1] = miss_off[m] + miss_cnt[m];
         inter_off[m + 1] = inter_off[m] + inter_cnt[m];
@@ -472,11 +670,11 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
 
     // ---- pass 2: the lists themselves (missing as community-local indices),
     // ascending within each row
-    hs.miss_local.assign(miss_off[n], 0);
+    hs.miss_local.assign(pl->miss_idx_bytes == 2 ? miss_off[n] : 0, 0);
     hs.inter_col.assign(inter_off[n], 0);
     auto &miss_local = hs.miss_local;
     auto &inter_col = hs.inter_col;
-    std::vector<int32_t> full_col(pl->has_direct ? full_rp[n] : 0);
+    full_col.assign(pl->has_direct ? full_rp[n] : 0, 0);
 #pragma omp parallel
     {
         std::vector<unsigned char> mark(pl->max_comm + 1, 0);
@@ -506,7 +704,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
                         }
                         mark[u] = 0;
                     } else if (lo + u != m) {
-                        miss_local[w++] = (int32_t)u;
+                        if (pl->miss_idx_bytes == 2) miss_local[w++] = (uint16_t)u;
                     }
                 }
             }
@@ -517,6 +715,15 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
         }
     }
 
+    return CIA_OK;
+}
+
+// Every device buffer of a plan that does not depend on the tiling, after
+// its split; omega_perm: natural frequencies in permuted order (NULL: zero).
+static cia_status upload_split(cia_plan *pl, const cia_options *opt, const double *omega_perm,
+                               const std::vector<int64_t> &full_rp, const std::vector<int32_t> &full_col) {
+    const int64_t n = pl->n, M = pl->M;
+    const auto &comm_of = pl->hs.comm_of;
     // ---- default threads per row of the direct method (16-byte vectors;
     // about two vectors per thread)
     const int gs = opt ? opt->group_size : 0;
@@ -548,7 +755,7 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     {
         std::vector<unsigned char> om(n * rb, 0);
         for (int64_t m = 0; m < n; ++m) {
-            double w = omega ? omega[pl->perm[m]] : 0.0;
+            double w = omega_perm ? omega_perm[m] : 0.0;
             if (rb == sizeof(double)) std::memcpy(&om[m * rb], &w, rb);
             else {
                 float wf = (float)w;
@@ -612,6 +819,29 @@ static cia_status build_split(const cia_graph *g, const int32_t *community, cons
     return CIA_OK;
 }
 
+// Phase 1 of planning: options, model, validation, kappa and the split of S
+// into the host lists kept by the plan (pl->hs), the direct method's CSR and
+// every device buffer that does not depend on the tiling.
+static cia_status build_split(const cia_graph *g, const int32_t *community, const double *omega,
+                              const cia_coupling *cp, const cia_options *opt, cia_plan *pl) {
+    cia_status st = configure(cp, opt, omega != nullptr, pl);
+    if (st != CIA_OK) return st;
+    const int64_t n = g->n;
+    if (omega)
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(omega[i]))
+                return fail(CIA_ERR_NUMERIC, "omega[" + std::to_string(i) + "] is not finite");
+    std::vector<int64_t> full_rp;
+    std::vector<int32_t> full_col;
+    if ((st = split_graph(g, community, pl, full_rp, full_col)) != CIA_OK) return st;
+    std::vector<double> om;
+    if (omega) {
+        om.resize(n);
+        for (int64_t m = 0; m < n; ++m) om[m] = omega[pl->perm[m]];
+    }
+    return upload_split(pl, opt, omega ? om.data() : nullptr, full_rp, full_col);
+}
+
 // Phase 2 of planning: cut the communities into work tiles, build the
 // sliced-ELL blobs and every device buffer whose size depends on the tiling.
 // Runs again (after freeing the previous tiling) when the tiling changes.
@@ -638,15 +868,23 @@ static cia_status build_tiles(cia_plan *pl) {
     // rows or when the rows' sparse indices (padded to 16-byte vectors) would
     // exceed tile_index_bytes; a single longer row forms a tile of its own
     std::vector<int32_t> tile_comm, tile_first, tile_count, comm_tile_begin(M + 1, 0);
+    // the persistent per-tile kernel (staging 4) holds a tile's community
+    // window and its blob in one shared-memory buffer of tile_index_bytes: the
+    // window of a large community leaves less room for the tile's indices
+    const bool budget_window = pl->staging_req == 4;
     auto cut = [&](int32_t c, int64_t b, int64_t e) {
+        int64_t limit = pl->tile_index_bytes;
+        if (budget_window)
+            limit = std::max<int64_t>(2048, limit - stream_tile_buf_bytes(pl, c >= 0 ? pl->off[c + 1] - pl->off[c] : 0, 0));
         int64_t s = b;
         while (s < e) {
             int64_t rows = 0, bytes = 0, r = s;
             int64_t chunks = 0;
             while (r < e && rows < pl->tile_nodes) {
-                int64_t rb = pad8(miss_cnt[r]) * 2 + pad4(inter_cnt[r]) * 4;
+                // index vectors, plus (staging 4) the row's share of the blob's tables
+                int64_t rb = pad8(miss_cnt[r]) * 2 + pad4(inter_cnt[r]) * 4 + (budget_window ? 9 : 0);
                 int64_t rc = chunks_of(miss_cnt[r]);
-                if (rows > 0 && (bytes + rb > pl->tile_index_bytes || chunks + rc > kMaxChunks)) break;
+                if (rows > 0 && (bytes + rb > limit || chunks + rc > kMaxChunks)) break;
                 bytes += rb;
                 chunks += rc;
                 ++rows;
@@ -691,10 +929,16 @@ static cia_status build_tiles(cia_plan *pl) {
 #pragma omp for schedule(dynamic, 8)
             for (int64_t t = 0; t < T; ++t) {
                 const int32_t c = tile_comm[t];
-                const uint16_t msent = c >= 0 ? (uint16_t)(pl->off[c + 1] - pl->off[c]) : 0;
-                // the Cucker--Smale kernels gather 16-byte states, the Kuramoto ones 8-byte phasors
-                const int bank_lanes = pl->model == CIA_MODEL_CUCKER_SMALE ? 8 : 16;
-                build_tile_blob(tile_first[t], tile_count[t], msent, (int32_t)n, bank_lanes, miss_cnt, miss_off, miss_local,
+                const int64_t lam = c >= 0 ? pl->off[c + 1] - pl->off[c] : 0;
+                const uint16_t msent = (uint16_t)lam;
+                // bank groups of the gathered element: 16-byte elements (Cucker--Smale
+                // states, FP64 phasors) are served per quarter-warp, 8-byte ones per half-warp
+                const bool wide = pl->model == CIA_MODEL_CUCKER_SMALE ||
+                                  (pl->model != CIA_MODEL_POLYNOMIAL && pl->precision == CIA_FP64);
+                const int bank_lanes = wide ? 8 : 16;
+                // padding entries lambda .. lambda + 15 (zero slots after the window)
+                const bool spread = lam + kPadSlots - 1 <= 65535;
+                build_tile_blob(tile_first[t], tile_count[t], msent, spread, (int32_t)n, bank_lanes, miss_cnt, miss_off, miss_local,
                                 inter_cnt, inter_off, inter_col, tbs[t], sched);
             }
         }
@@ -722,9 +966,14 @@ static cia_status build_tiles(cia_plan *pl) {
             d.shift = (int32_t)(d.lo - (d.lo & ~(per16 - 1)));
             d.vtab_off = tbs[t].vtab_off;
         }
+        pl->max_tile_buf = 0;
         for (int64_t t = 0; t < T; ++t) {
             tile_bytes[t] = (int64_t)tbs[t].bytes.size();
             pl->max_tile_idx_bytes = std::max<int64_t>(pl->max_tile_idx_bytes, tile_bytes[t]);
+            pl->max_tile_buf = std::max<int64_t>(
+                pl->max_tile_buf,
+                stream_tile_buf_bytes(pl, tile_comm[t] >= 0 ? pl->off[tile_comm[t] + 1] - pl->off[tile_comm[t]] : 0,
+                                      tile_bytes[t]));
             pl->n_slices += tbs[t].nsl;
         }
         pl->blob_bytes = blob_off[T];
@@ -810,6 +1059,11 @@ static cia_status build_tiles(cia_plan *pl) {
         int optin = 0;
         CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
         if (window_smem_bytes(pl) > (size_t)optin - 1024) pl->staging = 1;
+    }
+    if (pl->staging == 4) {
+        int optin = 0;
+        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+        if (stream_smem_bytes(pl) > (size_t)optin - 1024) pl->staging = 1;
     }
     if (pl->staging == 3) {
         // contiguous tile ranges, one per SM, balanced by the bytes each tile
@@ -990,6 +1244,197 @@ extern "C" cia_status cia_plan_create_batch(int64_t B, const cia_graph *graphs, 
     return CIA_OK;
 }
 
+// ---- streamed ensemble plans ------------------------------------------------
+
+extern "C" cia_status cia_plan_batch_begin(const cia_coupling *coupling, const cia_options *opt, cia_plan_t **out) {
+    clear_error();
+    if (!out) return fail(CIA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!coupling) return fail(CIA_ERR_INVALID_ARG, "coupling is NULL");
+    if (coupling->model != CIA_MODEL_KURAMOTO) return fail(CIA_ERR_UNSUPPORTED, "ensembles support the Kuramoto model only");
+    if (opt && opt->build_direct)
+        return fail(CIA_ERR_UNSUPPORTED, "a streamed ensemble plan has no direct method: plan a sample of the "
+                                         "instances with cia_plan_create_batch for it");
+    cia_plan *pl = new (std::nothrow) cia_plan();
+    if (!pl) return fail(CIA_ERR_OOM, "host allocation of the plan failed");
+    cia_status st = CIA_OK;
+    try {
+        st = configure(coupling, opt, true, pl);
+        if (st == CIA_OK) {
+            pl->batch_stage = new BatchStaging();
+            if (opt) pl->batch_stage->opt = *opt;
+            pl->B = 0;
+            pl->inst_off.assign(1, 0);
+            pl->inst_comm_off.assign(1, 0);
+        }
+    } catch (const std::bad_alloc &) {
+        st = fail(CIA_ERR_OOM, "host allocation failed while planning");
+    }
+    if (st != CIA_OK) {
+        free_all(pl);
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_batch_add(cia_plan_t *pl, const cia_graph *g, const int32_t *community,
+                                         const double *omega) {
+    clear_error();
+    if (!pl || !pl->batch_stage) return fail(CIA_ERR_INVALID_ARG, "not a streamed ensemble plan being built");
+    BatchStaging &bs = *pl->batch_stage;
+    const int64_t i = (int64_t)bs.inst.size();
+    const std::string who = "instance " + std::to_string(i) + ": ";
+    if (!g || g->n < 1 || !g->rowptr || (!g->col && g->rowptr[g->n] > 0) || !community)
+        return fail(CIA_ERR_INVALID_ARG, who + "empty graph or NULL array");
+    if (bs.n_total + g->n > (int64_t)INT32_MAX - 1)
+        return fail(CIA_ERR_INVALID_ARG, who + "the ensemble has too many nodes");
+    if (omega)
+        for (int64_t v = 0; v < g->n; ++v)
+            if (!std::isfinite(omega[v]))
+                return fail(CIA_ERR_NUMERIC, who + "omega[" + std::to_string(v) + "] is not finite");
+    try {
+        // split the instance on its own (the direct method's CSR is not built)
+        cia_plan tmp;
+        tmp.has_direct = 0;
+        std::vector<int64_t> rp;
+        std::vector<int32_t> col;
+        cia_status st = split_graph(g, community, &tmp, rp, col);
+        if (st != CIA_OK) return fail(st, who + cia_last_error());
+        if (tmp.max_comm > 65535)
+            return fail(CIA_ERR_UNSUPPORTED, who + "a community above 65535 nodes has no CIA layout");
+        StagedInstance si;
+        si.n = g->n;
+        si.M = tmp.M;
+        si.n_lab = tmp.off[tmp.M];
+        si.nnz = tmp.nnz_graph;
+        si.max_comm = tmp.max_comm;
+        si.perm = std::move(tmp.perm);
+        si.off = std::move(tmp.off);
+        si.miss_cnt.assign(tmp.hs.miss_cnt.begin(), tmp.hs.miss_cnt.begin() + si.n_lab);
+        si.miss = std::move(tmp.hs.miss_local);
+        si.inter_cnt = std::move(tmp.hs.inter_cnt);
+        // the ensemble's permuted order: every instance's labelled nodes, then
+        // every instance's free nodes, both in instance order
+        const auto &ic = tmp.hs.inter_col;
+        si.inter.resize(ic.size());
+        for (size_t e = 0; e < ic.size(); ++e) {
+            const int64_t q = ic[e];
+            si.inter[e] = q < si.n_lab ? bs.lab_total + q : -1 - (bs.free_total + (q - si.n_lab));
+        }
+        if (omega) {
+            si.omega.resize(si.n);
+            for (int64_t m = 0; m < si.n; ++m) si.omega[m] = omega[si.perm[m]];
+        }
+        bs.lab_total += si.n_lab;
+        bs.free_total += si.n - si.n_lab;
+        bs.comm_total += si.M;
+        bs.n_total += si.n;
+        pl->inst_off.push_back(bs.n_total);
+        pl->inst_comm_off.push_back(bs.comm_total);
+        bs.inst.push_back(std::move(si));
+    } catch (const std::bad_alloc &) {
+        return fail(CIA_ERR_OOM, who + "host allocation failed while planning");
+    }
+    pl->B = (int64_t)bs.inst.size();
+    return CIA_OK;
+}
+
+extern "C" cia_status cia_plan_batch_finish(cia_plan_t *pl) {
+    clear_error();
+    if (!pl || !pl->batch_stage) return fail(CIA_ERR_INVALID_ARG, "not a streamed ensemble plan being built");
+    BatchStaging &bs = *pl->batch_stage;
+    const int64_t B = (int64_t)bs.inst.size();
+    if (B < 1) return fail(CIA_ERR_INVALID_ARG, "no instance was added");
+    cia_status st = CIA_OK;
+    try {
+        const int64_t n = bs.n_total, M = bs.comm_total, L = bs.lab_total;
+        pl->n = n;
+        pl->M = M;
+        pl->n_free = bs.free_total;
+        pl->ph_stride = (n + 2) & ~(int64_t)1;
+        pl->miss_idx_bytes = 2;
+        pl->max_comm = 0;
+        pl->nnz_graph = 0;
+        auto &hs = pl->hs;
+        pl->perm.assign(n, 0);
+        pl->off.assign(M + 1, 0);
+        hs.comm_of.assign(n, -1);
+        hs.miss_cnt.assign(n, 0);
+        hs.inter_cnt.assign(n, 0);
+        std::vector<double> om(n, 0.0);
+        bool any_omega = false;
+        // row of the ensemble for row m of instance i
+        std::vector<int64_t> lab_base(B), free_base(B);
+        for (int64_t i = 0, lb = 0, fb = L; i < B; ++i) {
+            lab_base[i] = lb;
+            free_base[i] = fb;
+            lb += bs.inst[i].n_lab;
+            fb += bs.inst[i].n - bs.inst[i].n_lab;
+        }
+#pragma omp parallel for schedule(dynamic, 1) reduction(|| : any_omega)
+        for (int64_t i = 0; i < B; ++i) {
+            const StagedInstance &si = bs.inst[i];
+            const int64_t o = pl->inst_off[i], c0 = pl->inst_comm_off[i];
+            for (int64_t m = 0; m < si.n; ++m) {
+                const int64_t r = m < si.n_lab ? lab_base[i] + m : free_base[i] + (m - si.n_lab);
+                pl->perm[r] = (int32_t)(o + si.perm[m]);
+                hs.inter_cnt[r] = si.inter_cnt[m];
+                if (!si.omega.empty()) om[r] = si.omega[m];
+            }
+            for (int64_t c = 0; c < si.M; ++c) {
+                pl->off[c0 + c] = lab_base[i] + si.off[c];
+                for (int64_t m = si.off[c]; m < si.off[c + 1]; ++m) hs.comm_of[lab_base[i] + m] = (int32_t)(c0 + c);
+            }
+            for (int64_t m = 0; m < si.n_lab; ++m) hs.miss_cnt[lab_base[i] + m] = si.miss_cnt[m];
+            any_omega = any_omega || !si.omega.empty();
+        }
+        pl->off[M] = L;
+        hs.miss_off.assign(n + 1, 0);
+        hs.inter_off.assign(n + 1, 0);
+        for (int64_t m = 0; m < n; ++m) {
+            hs.miss_off[m + 1] = hs.miss_off[m] + hs.miss_cnt[m];
+            hs.inter_off[m + 1] = hs.inter_off[m] + hs.inter_cnt[m];
+        }
+        pl->nnz_missing = hs.miss_off[n];
+        pl->nnz_inter = hs.inter_off[n];
+        // the lists, instance by instance, releasing each staged copy
+        hs.miss_local.resize(pl->nnz_missing);
+        hs.inter_col.resize(pl->nnz_inter);
+        for (int64_t i = 0; i < B; ++i) {
+            StagedInstance &si = bs.inst[i];
+            std::copy(si.miss.begin(), si.miss.end(), hs.miss_local.begin() + hs.miss_off[lab_base[i]]);
+            // labelled rows' inter links, then free rows'
+            int64_t split = 0;
+            for (int64_t m = 0; m < si.n_lab; ++m) split += si.inter_cnt[m];
+            auto decode = [&](int64_t v) { return (int32_t)(v >= 0 ? v : L + (-1 - v)); };
+            int32_t *dl = hs.inter_col.data() + hs.inter_off[lab_base[i]];
+            for (int64_t e = 0; e < split; ++e) dl[e] = decode(si.inter[e]);
+            if (si.n > si.n_lab) {
+                int32_t *df = hs.inter_col.data() + hs.inter_off[free_base[i]];
+                for (int64_t e = split; e < (int64_t)si.inter.size(); ++e) df[e - split] = decode(si.inter[e]);
+            }
+            pl->max_comm = std::max(pl->max_comm, si.max_comm);
+            pl->nnz_graph += si.nnz;
+            si = StagedInstance();
+        }
+        const cia_options opt = bs.opt;
+        delete pl->batch_stage;
+        pl->batch_stage = nullptr;
+        std::vector<int64_t> no_rp;
+        std::vector<int32_t> no_col;
+        st = upload_split(pl, &opt, any_omega ? om.data() : nullptr, no_rp, no_col);
+        if (st == CIA_OK) {
+            pl->staging_req = pl->staging;
+            st = build_tiles(pl);
+        }
+    } catch (const std::bad_alloc &) {
+        st = fail(CIA_ERR_OOM, "host allocation failed while planning");
+    }
+    return st;
+}
+
 extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_index_bytes, int staging) {
     clear_error();
     if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
@@ -999,7 +1444,7 @@ extern "C" cia_status cia_plan_retile(cia_plan_t *pl, int tile_nodes, int tile_i
         return fail(CIA_ERR_INVALID_ARG, "tile_nodes must be a multiple of 32 in [32, 1024] (<= 128 for Cucker-Smale)");
     const int tib = tile_index_bytes ? tile_index_bytes : 65536;
     if (tib < 256 || tib % 16) return fail(CIA_ERR_INVALID_ARG, "tile_index_bytes must be a multiple of 16, at least 256");
-    if (staging < 0 || staging > 3) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2 or 3");
+    if (staging < 0 || staging > 4) return fail(CIA_ERR_INVALID_ARG, "staging must be 0, 1, 2, 3 or 4");
     int dev = -1;
     CIA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != pl->device) return fail(CIA_ERR_INVALID_ARG, "plan belongs to another device");
@@ -1094,7 +1539,7 @@ extern "C" cia_status cia_plan_get_split(const cia_plan_t *pl, int64_t *miss_row
                     for (uint32_t j = 0; j < nvm; ++j)
                         for (int h = 0; h < 8; ++h) {
                             const uint16_t v = sm[8 * (moff + 32 * j + lane) + h];
-                            if (v != d.lam) mrow[d.first + chunk_row[mr]].push_back((int32_t)(d.lo + v));
+                            if (v < d.lam) mrow[d.first + chunk_row[mr]].push_back((int32_t)(d.lo + v));   // >= lam: padding
                         }
                 if (ir != 0xffffu)
                     for (uint32_t j = 0; j < nvi; ++j)

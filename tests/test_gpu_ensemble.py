@@ -149,7 +149,8 @@ def test_ensemble_of_one_equals_single_plan(P):
 
 
 @pytest.mark.parametrize("tile_nodes,tib,staging", [(64, 4096, "plain"), (256, 16384, "pipeline"),
-                                                   (128, 49152, "auto"), (256, 8192, "window")])
+                                                   (128, 49152, "auto"), (256, 8192, "window"),
+                                                   (256, 24576, "stream"), (128, 8192, "stream")])
 def test_retile_keeps_results(P, oracle_mod, tile_nodes, tib, staging):
     import torch
     e = _small(4)
@@ -231,3 +232,30 @@ def test_bench_sized_ensemble_sampled(P, oracle_mod):
         ref = oracle_mod.kuramoto_direct(w.graph.rowptr, w.graph.col, w.theta0, w.omega, 4.0)
         assert coupling_rel_err(out[o:o + n], ref, w.omega) <= 1e-5, w.name
         o += n
+
+
+def test_streamed_plan_equals_batch_plan(P):
+    """An ensemble planned instance by instance (cia_plan_batch_begin/add/
+    finish) has the one-call plan's layout: the same permutation, split of S
+    and tiling, and an integration with order parameters bit for bit equal."""
+    import torch
+    inst = [(w.graph, w.omega, w.theta0) for w in _small(5).instances] + _with_free_nodes(3)
+    a = P.Plan.batch([(g.rowptr, g.col) for g, _, _ in inst], [g.labels for g, _, _ in inst],
+                     [om for _, om, _ in inst], K=4.0, precision="fp32")
+    b = P.Plan.streamed(((g.rowptr, g.col, g.labels, om) for g, om, _ in inst), K=4.0, precision="fp32")
+    ia, ib = a.info(), b.info()
+    for key in ("n", "M", "n_free", "nnz_graph", "nnz_missing", "nnz_inter", "n_tiles", "instances", "staging"):
+        assert ia[key] == ib[key], key
+    pa, oa = a.permutation()
+    pb, ob = b.permutation()
+    assert np.array_equal(pa, pb) and np.array_equal(oa, ob)
+    for x, y in zip(a.split(), b.split()):
+        assert np.array_equal(x, y)
+    x0 = torch.from_numpy(_concat([th for _, _, th in inst])).cuda()
+    xa, xb = x0.clone(), x0.clone()
+    ra = torch.zeros(8 * len(inst), dtype=torch.float64, device="cuda")
+    rb = torch.zeros_like(ra)
+    a.integrate(xa, 0.01, 8, r_out=ra)
+    b.integrate(xb, 0.01, 8, r_out=rb)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(ra, rb)

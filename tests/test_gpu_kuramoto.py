@@ -87,7 +87,7 @@ def test_rhs_fp64_small_sbm(cia, oracle_mod, torch_mod, method):
     assert coupling_rel_err(got, ref, w.omega) < FP64_TOL
 
 
-@pytest.mark.parametrize("staging", ["pipeline", "window"])
+@pytest.mark.parametrize("staging", ["pipeline", "window", "stream"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_rhs_harmonics(cia, oracle_mod, torch_mod, p, precision, staging):
@@ -103,7 +103,7 @@ def test_rhs_harmonics(cia, oracle_mod, torch_mod, p, precision, staging):
         assert coupling_rel_err(gpu_rhs(torch_mod, plan, th, method), ref, om) < tol, method
 
 
-@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline"])
+@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline", "stream"])
 @pytest.mark.parametrize("group_size", [4, 8, 16, 32])
 @pytest.mark.parametrize("tile_nodes,tile_index_bytes", [(32, 0), (96, 0), (1024, 0), (256, 256),
                                                          (1024, 4096)])
@@ -118,7 +118,7 @@ def test_rhs_launch_shapes(cia, oracle_mod, torch_mod, group_size, tile_nodes, t
     plan = make_plan(cia, g, om, 3.0, tile_nodes=tile_nodes, group_size=group_size,
                      tile_index_bytes=tile_index_bytes, staging=staging)
     # the pipelined TMA kernel and the window kernel take tiles of at most 256 rows
-    want = {"auto": 2, "plain": 1, "window": 2, "pipeline": 3}[staging]
+    want = {"auto": 2, "plain": 1, "window": 2, "pipeline": 3, "stream": 4}[staging]
     assert plan.info()["staging"] == (want if tile_nodes <= 256 else 1)
     ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, th, om, 3.0)
     for method in ("cia", "direct"):
@@ -156,7 +156,7 @@ def test_rhs_degenerate_graphs(cia, oracle_mod, torch_mod, case):
             assert coupling_rel_err(got, ref, om) < FP64_TOL
 
 
-@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline"])
+@pytest.mark.parametrize("staging", ["auto", "plain", "window", "pipeline", "stream"])
 def test_rhs_fp32_lognormal_reduced(cia, oracle_mod, torch_mod, staging):
     w = S.kuramoto_lognormal(scale=1 / 16)
     g = w.graph
@@ -174,11 +174,39 @@ def test_rhs_fp32_lognormal_full_size(cia, oracle_mod, torch_mod):
     w = S.cached("kuramoto_lognormal")
     g = w.graph
     plan = make_plan(cia, g, w.omega, w.K, precision="fp32")
-    assert plan.info()["staging"] == 2                 # the community-window kernel
     ref = oracle_mod.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)
-    got = gpu_rhs(torch_mod, plan, w.theta0, "cia")
-    assert coupling_rel_err(got, ref, w.omega) < FP32_TOL
     assert coupling_rel_err(gpu_rhs(torch_mod, plan, w.theta0, "direct"), ref, w.omega) < FP32_TOL
+    # every CIA kernel, the persistent ones with several tiles per CTA
+    for staging, tib, want in [("window", 0, 2), ("stream", 49152, 4), ("stream", 24576, 4),
+                               ("pipeline", 32768, 3)]:
+        plan.retile(0, tib, staging)
+        assert plan.info()["staging"] == want
+        got = gpu_rhs(torch_mod, plan, w.theta0, "cia")
+        assert coupling_rel_err(got, ref, w.omega) < FP32_TOL, staging
+
+
+def test_stream_kernel_many_rounds_integrate(cia, oracle_mod, torch_mod):
+    """The persistent per-tile kernel with far more tiles than resident CTAs
+    (every CTA runs several rounds: descriptors fetched ahead, the copy
+    barrier's phases reused), through all four RK4 stage modes: 20 steps of
+    r(t) and the final phases against the oracle's RK4 of its CIA."""
+    w = S.kuramoto_lognormal(scale=1 / 8, steps=20)
+    g = w.graph
+    plan = make_plan(cia, g, w.omega, w.K, precision="fp32", tile_nodes=32, tile_index_bytes=8192,
+                     staging="stream")
+    assert plan.info()["staging"] == 4 and plan.info()["n_tiles"] > 4 * 152
+    sp = oracle_mod.split(g.rowptr, g.col, g.labels)
+    omp = w.omega[sp.perm]
+    rhs = lambda x: oracle_mod.kuramoto_cia(sp, x, omp, w.K)
+    ref, r_ref = oracle_mod.integrate(rhs, w.theta0[sp.perm], w.dt, w.steps, wrap=True,
+                                      observe=oracle_mod.order_parameter)
+    x = torch_mod.from_numpy(w.theta0.copy()).cuda()
+    r = torch_mod.zeros(w.steps, dtype=torch_mod.float64, device="cuda")
+    plan.integrate(x, w.dt, w.steps, r_out=r)
+    plan.sync()
+    assert np.abs(r.cpu().numpy() - np.array(r_ref)).max() < 1e-5
+    got = x.cpu().numpy()[sp.perm]
+    assert np.abs(oracle_mod.angle_diff(got, ref)).max() < 1e-4
 
 
 @pytest.mark.parametrize("lam,staging", [(20000, 2), (50000, 1)])
