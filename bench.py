@@ -53,7 +53,7 @@ def parse():
                     help="skip the Cucker-Smale (learned basis) secondary workload")
     ap.add_argument("--cs-pairs", type=int, default=10_000_000, help="training pairs of the CS basis")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble secondary workload")
-    ap.add_argument("--ens-instances", type=int, default=32,
+    ap.add_argument("--ens-instances", type=int, default=4096,
                     help="instances of the seeded 4096-network ensemble to run")
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the small FP64 and the higher-order Kuramoto workloads")
@@ -136,6 +136,21 @@ def max_over_ranks(torch, dist, world: int, v: float, device) -> float:
     t = torch.tensor([float(v)], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_instances(sizes, world: int, rank: int) -> list:
+    """The instances of an ensemble that rank `rank` of `world` runs: instances
+    are independent, so they are dealt out whole, largest first, each to the
+    rank with the fewest nodes so far (ties to the lowest rank); every rank
+    computes the same assignment from the sizes alone, with no exchange."""
+    load = [0] * world
+    mine = []
+    for i in sorted(range(len(sizes)), key=lambda j: (-int(sizes[j]), j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += int(sizes[i])
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
 
 
 def job_throughput(units_per_rank: float, steps: int, world: int, max_seconds: float) -> float:
@@ -349,62 +364,120 @@ def cs_leg(args, torch, cia, flush) -> dict:
 
 # ------------------------------------------------------------------ batched ensemble (secondary line)
 
-ENS_WORKLOAD = ("kuramoto_ensemble: the first {B} of 4096 seeded independent Kuramoto networks, "
+ENS_WORKLOAD = ("kuramoto_ensemble: {B} seeded independent Kuramoto networks (4096 in the full ensemble), "
                 "N_i~U{{256..16384}}, M_i~U{{2..32}} equal communities, p_in~U[0.7,1], inter degree "
-                "U{{2..10}}, omega~N(0,1), K=4, RK4 dt=0.01, FP32 + FP64 time accumulation; one "
-                "launch per RK4 stage for all instances, r(t) per instance")
+                "U{{2..10}}, omega~N(0,1), K=4, RK4 dt=0.01, FP32 + FP64 time accumulation; planned one "
+                "instance at a time (cia_plan_batch_*), one launch per RK4 stage for all instances, "
+                "r(t) per instance")
 
 
-def ensemble_leg(args, torch, cia, flush) -> dict:
-    """All instances in one plan: autotuned tiling, per-step device time with
-    the L2 flushed between steps, the same steps replayed from one CUDA graph
-    per step (L2 warm), and the RHS error of every instance against the FP64
-    oracle."""
+def ensemble_bytes(info: dict) -> float:
+    """Algorithmic bytes of one CIA stage launch of an ensemble (the same
+    per-node, per-missing-link and per-inter-link model as stage_bytes)."""
+    return stage_bytes(info, "fp32")
+
+
+def ensemble_leg(args, torch, cia, flush, world: int = 1, rank: int = 0, dist=None) -> dict:
+    """The ensemble planned instance by instance (generated, added and
+    dropped one at a time): per-step device time with the L2 flushed between
+    steps, graph replay with per-instance order parameters, the RHS error of
+    sampled instances against the FP64 oracle; the tiling is autotuned on the
+    first 64 instances, whose plan also times the direct method.  Under
+    torchrun each rank runs its shard of the instances (shard_instances: no
+    collective on the data path) and the job's time is the slowest rank's."""
     import oracle
     import synthetic as S
     oracle.set_num_threads(host_cores())
-    e = S.kuramoto_ensemble(args.ens_instances)
-    inst = e.instances
-    B = len(inst)
-    plan = cia.Plan.batch([(w.graph.rowptr, w.graph.col) for w in inst], [w.graph.labels for w in inst],
-                          [w.omega for w in inst], K=e.K, precision="fp32")
-    x0np = np.concatenate([w.theta0 for w in inst])
-    x0 = torch.from_numpy(x0np.copy()).cuda()
-    tune = plan.autotune(x0, e.dt, steps=5)
+    B = args.ens_instances
+    dt, K = 0.01, 4.0
+    # the tiling, autotuned on a sample plan that also runs the direct method
+    ns = min(B, 64)
+    sample = [S.ensemble_instance(i) for i in range(ns)]
+    splan = cia.Plan.batch([(w.graph.rowptr, w.graph.col) for w in sample], [w.graph.labels for w in sample],
+                           [w.omega for w in sample], K=K, precision="fp32", build_direct=True)
+    sx = torch.from_numpy(np.concatenate([w.theta0 for w in sample])).cuda()
+    tune = splan.autotune(sx, dt, steps=3)
+    sinfo = splan.info()
+    s_steps = 5
+    sms, _ = timed_steps(torch, splan, sx, dt, s_steps, 2, "cia", flush, False)
+    dms, _ = timed_steps(torch, splan, sx, dt, s_steps, 1, "direct", flush, False)
+    s_cia, s_dir = float(sum(sms)) / s_steps, float(sum(dms)) / s_steps
+    sample_block = {
+        "instances": ns, "n": sinfo["n"], "nnz_graph": sinfo["nnz_graph"],
+        "cia": {"value": sinfo["n"] / (s_cia / 1e3), "unit": UNIT, "ms_per_step": s_cia},
+        "direct": {"value": sinfo["n"] / (s_dir / 1e3), "unit": UNIT, "ms_per_step": s_dir,
+                   "bytes_per_stage": direct_stage_bytes(sinfo, "fp32")},
+        "speedup_cia_over_direct": s_dir / max(s_cia, 1e-12)}
+    del splan, sx
+    # this rank's instances of the full ensemble, one instance at a time
+    ids = shard_instances([S.ensemble_instance_shape(i)[0] for i in range(B)], world, rank) if world > 1 \
+        else list(range(B))
+    keep = sorted({ids[0], ids[len(ids) // 3], ids[(2 * len(ids)) // 3], ids[-1]} | ({447} if 447 in ids else set()))
+    kept, theta = {}, []
+    t0 = time.perf_counter()
+
+    def instances():
+        for i in ids:
+            w = S.ensemble_instance(i)
+            theta.append(w.theta0)
+            if i in keep:
+                kept[i] = w
+            yield w.graph.rowptr, w.graph.col, w.graph.labels, w.omega
+
+    plan = cia.Plan.streamed(instances(), K=K, precision="fp32", tile_nodes=tune["tile_nodes"],
+                             tile_index_bytes=tune["tile_index_bytes"],
+                             staging={1: "plain", 2: "window", 3: "pipeline", 4: "stream"}[tune["staging"]])
+    plan_s = time.perf_counter() - t0
     info = plan.info()
     n = info["n"]
+    offs = dict(zip(ids, np.concatenate([[0], np.cumsum([len(th) for th in theta])])[:-1]))
+    x0 = torch.from_numpy(np.concatenate(theta)).cuda()
+    del theta
     out = plan.rhs(x0).cpu().numpy()
-    err, o = 0.0, 0
-    for w in inst:
-        m = w.graph.n
-        ref = oracle.kuramoto_direct(w.graph.rowptr, w.graph.col, w.theta0, w.omega, e.K)
-        err = max(err, coupling_rel_err(out[o:o + m], ref, w.omega))
-        o += m
-    steps = max(3, args.steps // 2)
-    ms, prof = timed_steps(torch, plan, x0, e.dt, steps, args.warmup, "cia", flush, True)
-    total = float(sum(ms))
+    err = 0.0
+    for i, w in kept.items():
+        ref = oracle.kuramoto_direct(w.graph.rowptr, w.graph.col, w.theta0, w.omega, K)
+        err = max(err, coupling_rel_err(out[offs[i]:offs[i] + w.graph.n], ref, w.omega))
+    del out
+    steps = max(3, min(args.steps // 2, 20))
+    ms, prof = timed_steps(torch, plan, x0, dt, steps, min(args.warmup, 3), "cia", flush, True)
+    total = max_over_ranks(torch, dist, world, float(sum(ms)), "cuda")
+    n_job = n
+    if world > 1:
+        t = torch.tensor([float(n)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        n_job = int(t.item())
+    Bl = len(ids)
     # graph replay: all steps in one advance call, order parameters per instance
-    r = torch.zeros(steps * B, dtype=torch.float64, device="cuda")
+    r = torch.zeros(steps * Bl, dtype=torch.float64, device="cuda")
     plan.state_load(x0)
-    plan.advance(e.dt, args.warmup, r_out=torch.zeros(args.warmup * B, dtype=torch.float64, device="cuda"))
+    plan.advance(dt, 2, r_out=torch.zeros(2 * Bl, dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    plan.advance(e.dt, steps, r_out=r)
+    plan.advance(dt, steps, r_out=r)
     b.record()
     torch.cuda.synchronize()
-    gms = a.elapsed_time(b)
+    gms = max_over_ranks(torch, dist, world, a.elapsed_time(b), "cuda")
+    rr = r.view(steps, Bl).cpu().numpy()
     stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
-    sb = stage_bytes(info, "fp32")
+    sb = ensemble_bytes(info)
     return {
-        "workload": ENS_WORKLOAD.format(B=B), "instances": B, "n": n, "nnz_graph": info["nnz_graph"],
-        "nnz_missing": info["nnz_missing"], "nnz_inter": info["nnz_inter"], "steps": steps,
-        "value": n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
+        "workload": ENS_WORKLOAD.format(B=B), "instances": B, "n": n_job, "ranks": world,
+        "scaling": "weak: instances sharded over ranks, no data-path collective" if world > 1 else None,
+        "rank0_instances": Bl, "rank0_n": n, "nnz_graph": info["nnz_graph"],
+        "nnz_missing": info["nnz_missing"], "nnz_inter": info["nnz_inter"], "n_tiles": info["n_tiles"],
+        "plan_s": plan_s, "steps": steps,
+        "value": n_job * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
         "l2": "flushed between timed steps",
-        "graph_replay": {"value": n * steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / steps,
-                         "l2": "warm (steps replayed back to back)", "with_order_parameters": True},
-        "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
-        "autotune": tune, "rhs_coupling_rel_err_vs_fp64_oracle_max_over_instances": err,
+        "graph_replay": {"value": n_job * steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / steps,
+                         "l2": "warm (steps replayed back to back)", "with_order_parameters": True,
+                         "r_last_step_min_max": [float(rr[-1].min()), float(rr[-1].max())]},
+        "stage_ms": stage_ms, "stage_bytes": sb, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
+        "roofline_frac": sb / (stage_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
+        "autotune_on_sample": tune,
+        "rhs_coupling_rel_err_vs_fp64_oracle": {"max": err, "instances": sorted(kept)},
+        "sample_with_direct": sample_block,
     }
 
 
@@ -684,6 +757,11 @@ def main():
             plan.integrate_host(xh, w.dt, 1, r_out=rh)
         e2e_s = max_over_ranks(torch, dist, world, time.perf_counter() - t0, "cuda")
 
+    # the ensemble, sharded by instance over the ranks (every rank takes part)
+    ens = None
+    if not args.no_ensemble and world > 1:
+        ens = ensemble_leg(args, torch, cia, flush, world, rank, dist)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -692,7 +770,6 @@ def main():
     cs = None
     if not args.no_cs and world == 1:
         cs = cs_leg(args, torch, cia, flush)
-    ens = None
     if not args.no_ensemble and world == 1:
         ens = ensemble_leg(args, torch, cia, flush)
     small = None

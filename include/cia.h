@@ -194,6 +194,7 @@ typedef struct {
     int model;                  /* cia_model */
     int state_dim;              /* d: FP64 values per node at the boundary */
     int64_t instances;          /* independent networks (1 unless cia_plan_create_batch) */
+    int ring_slots;             /* staging 4: tile buffers of the ring in shared memory (else 0) */
 } cia_plan_info;
 
 /* ---- status -------------------------------------------------------------- */
@@ -248,6 +249,38 @@ void cia_detect_options_default(cia_detect_options *opt);
  * options or NULL pointers.  report may be NULL. */
 cia_status cia_detect_communities(const cia_graph *g, const cia_detect_options *opt, int32_t *labels,
                                   cia_detect_report *report);
+
+/* Step P1's trade-off between the number of communities and the CIA's cost
+ * per stage, chosen by measuring this library's own kernels (Sec. "Community
+ * Detection (P1)": fewer, larger communities can pay off, more so for a high
+ * expansion order p).  Three partitions are detected and planned with
+ * `coupling` and `opt` (Kuramoto models), and each is timed for `steps` RK4
+ * steps (after two warm-up steps) from the state x (host, g->n doubles,
+ * original order) with step dt: 0 = the fewest entries of S (mu = 0), 1 = a
+ * coarser probe (a charge of one average block's directed pairs per
+ * community), 2 = the partition minimising the modelled stage time
+ *   T = c_tile tiles + c_byte (bytes of nodes, missing links, inter links),
+ * with c_tile and c_byte fitted to the timings of 0 and 1 (p enters through
+ * the gathered phasor bytes and the measured costs): gamma p =
+ * c_miss / (c_miss + c_inter) and mu = c_tile / (c_miss + c_inter) make the
+ * detector's Hamiltonian that model.  labels (host, g->n) receives the
+ * fastest of the three as measured, so the choice never loses to mu = 0.
+ * The device work allocates (plans, one state buffer) and synchronises. */
+typedef struct {
+    int64_t communities[3];      /* of partitions 0 (mu = 0), 1 (probe), 2 (modelled optimum) */
+    int64_t tiles[3];            /* work tiles of their plans */
+    int64_t nnz_s[3];            /* entries of S (missing + inter, directed) */
+    double ms_per_step[3];       /* measured device time of one RK4 step */
+    double per_tile_us;          /* fitted cost of one tile per stage */
+    double per_byte_ps;          /* fitted cost of one byte per stage */
+    double gamma, community_cost;   /* detection options of partition 2 */
+    double probe_community_cost; /* mu of partition 1 */
+    int chosen;                  /* the partition in labels: 0, 1 or 2 */
+} cia_partition_report;
+
+cia_status cia_choose_partition(const cia_graph *g, const double *omega, const cia_coupling *coupling,
+                                const cia_options *opt, const double *x, double dt, int64_t steps,
+                                int32_t *labels, cia_partition_report *report);
 
 /* Build a plan for graph g with the given community labels.
  *

@@ -55,6 +55,35 @@ def detect_communities(rowptr, col, *, gamma=1.0, community_cost=0.0, min_size=2
     return labels, {name: getattr(rep, name) for name, _ in _abi.DetectReport._fields_}
 
 
+def choose_partition(rowptr, col, omega, x, dt, steps=10, *, K=1.0, d_sin=(1.0,), d_cos=(0.0,),
+                     precision="fp32", model="kuramoto", K2=0.0):
+    """Community labels chosen by timing this library's kernels on three
+    detected partitions (include/cia.h, cia_choose_partition): the S-minimal
+    one, a coarser probe and the minimiser of the fitted stage-time model.
+    x: host float64 initial state (original order).  Returns (labels, report)."""
+    lib = load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(rowptr) - 1
+    g = _abi.Graph(n, rowptr.ctypes.data, col.ctypes.data)
+    cp = Plan._coupling(model, d_sin, d_cos, K, K2, 1.0, 0.0)
+    opt = _abi.Options(_abi.PRECISION[precision], 0, 0, 0, 0, 0, 0)
+    om = np.ascontiguousarray(omega, dtype=np.float64) if omega is not None else None
+    xh = np.ascontiguousarray(x, dtype=np.float64)
+    if len(xh) != n or (om is not None and len(om) != n):
+        raise ValueError("x and omega must have n entries")
+    labels = np.empty(n, dtype=np.int32)
+    rep = _abi.PartitionReport()
+    _abi.check(lib.cia_choose_partition(ctypes.byref(g), om.ctypes.data if om is not None else None,
+                                        ctypes.byref(cp), ctypes.byref(opt), xh.ctypes.data, float(dt), int(steps),
+                                        labels.ctypes.data, ctypes.byref(rep)))
+    out = {}
+    for name, _ in _abi.PartitionReport._fields_:
+        v = getattr(rep, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return labels, out
+
+
 class Plan:
     """A CIA plan: step P1 done once, then E1 + E2 on the device every call.
 

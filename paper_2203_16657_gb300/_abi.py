@@ -66,7 +66,7 @@ class PlanInfo(ctypes.Structure):
                 ("tile_nodes", ctypes.c_int), ("missing_index_bytes", ctypes.c_int),
                 ("staging", ctypes.c_int), ("group_size_direct", ctypes.c_int),
                 ("max_tile_index_bytes", ctypes.c_int64), ("model", ctypes.c_int),
-                ("state_dim", ctypes.c_int), ("instances", ctypes.c_int64)]
+                ("state_dim", ctypes.c_int), ("instances", ctypes.c_int64), ("ring_slots", ctypes.c_int)]
 
 
 class DetectOptions(ctypes.Structure):
@@ -84,6 +84,13 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int), ("tile_nodes", ctypes.c_int),
                 ("tile_index_bytes", ctypes.c_int), ("staging", ctypes.c_int),
                 ("best_ms_per_step", ctypes.c_double), ("worst_ms_per_step", ctypes.c_double)]
+
+
+class PartitionReport(ctypes.Structure):
+    _fields_ = [("communities", ctypes.c_int64 * 3), ("tiles", ctypes.c_int64 * 3), ("nnz_s", ctypes.c_int64 * 3),
+                ("ms_per_step", ctypes.c_double * 3), ("per_tile_us", ctypes.c_double),
+                ("per_byte_ps", ctypes.c_double), ("gamma", ctypes.c_double), ("community_cost", ctypes.c_double),
+                ("probe_community_cost", ctypes.c_double), ("chosen", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -140,6 +147,9 @@ SIGNATURES = {
     "cia_plan_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(Graph), _P, _P]),
     "cia_plan_batch_finish": (ctypes.c_int, [_P]),
     "cia_plan_retile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cia_choose_partition": (ctypes.c_int, [ctypes.POINTER(Graph), _P, ctypes.POINTER(Coupling),
+                                            ctypes.POINTER(Options), _P, ctypes.c_double, ctypes.c_int64, _P,
+                                            ctypes.POINTER(PartitionReport)]),
     "cia_detect_options_default": (None, [_P]),
     "cia_detect_communities": (ctypes.c_int, [_P, _P, _P, _P]),
     "cia_plan_set_weights": (ctypes.c_int, [_P, _P, _P]),

@@ -27,12 +27,18 @@ cia_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::cia::cuda_fail(_e, #expr);          \
     } while (0)
 
-// Padding entries of the missing-link vectors are lambda_c .. lambda_c +
-// kPadSlots - 1 (each a distinct shared-memory bank group, so that padding
-// never conflicts with a live gather); kernels that stage the community in
-// shared memory keep kPadSlots zero entries after it, the others skip any
-// index >= lambda_c.
+// Padding entries of the missing-link vectors are lambda_c + 1 .. lambda_c +
+// kPadSlots (each a distinct shared-memory bank group, so that padding never
+// conflicts with a live gather), or lambda_c itself for communities too large
+// for that range in 16 bits; kernels that stage the community in shared
+// memory keep the entries lambda_c .. lambda_c + kPadSlots after it zero (entry
+// lambda_c is a guard that a copy rounded up to 16 bytes may overwrite before
+// the ring kernel reads the window), the others skip any index >= lambda_c.
 constexpr int kPadSlots = 16;
+
+// Most slices of one tile that the persistent ring kernel's slot header holds
+// (their phasor sums are added in slice order into the tile partial).
+constexpr int kRingMaxSlices = 32;
 
 // Descriptor of one work tile (64 bytes, read by every CIA kernel).
 struct alignas(16) TileDesc {
@@ -84,6 +90,8 @@ struct DeviceBuffers {
     void *acc = nullptr;                // [n] sum_s b_s C_s, compute precision
     void *ph[2] = {nullptr, nullptr};   // [p][n] complex phasors e^{i k y}, compute precision
     double *part[2] = {nullptr, nullptr}; // [T][p] complex tile sums (FP64)
+    double *zsum[2] = {nullptr, nullptr}; // [M][p] complex community observables Z_c (FP64; ring kernel)
+    int *comm_done = nullptr;           // [M] tiles of the community finished in the running launch
     void *wdt_half = nullptr;           // [n] wrap(dt omega / 2), compute precision
     void *wdt_full = nullptr;           // [n] wrap(dt omega), compute precision
     double *wdt_full64 = nullptr;       // [n] wrap(dt omega), FP64
@@ -151,7 +159,9 @@ struct cia_plan {
     int64_t ph_stride = 0;              // phasor entries per harmonic: n + 1 rounded up to even
     int tile_index_bytes = 24576;
     int64_t max_tile_idx_bytes = 0;     // largest index footprint of one tile (bytes)
-    int64_t max_tile_buf = 0;           // largest window + blob of one tile (persistent per-tile kernel)
+    int64_t max_tile_buf = 0;           // largest window + blob of one tile (persistent ring kernel)
+    int ring_slots = 0;                 // ring slots of the persistent ring kernel (staging 4)
+    bool blob_segmented = false;        // blobs in the ring kernel's layout (rows on consecutive lanes)
     int64_t n_slices = 0, blob_bytes = 0, max_cta_tiles = 0, max_cta_runs = 0;
     int n_ctas = 0;                     // persistent grid of the pipelined CIA kernel (one per SM)
     int ring_stages = 0;                // tile buffers of its TMA ring
@@ -230,6 +240,7 @@ cudaError_t launch_scatter_master(cia_plan *pl, double *x, cudaStream_t s);
 size_t stage_smem_bytes(const cia_plan *pl, int method);
 size_t pipeline_smem_bytes(const cia_plan *pl, int stages);
 size_t stream_smem_bytes(const cia_plan *pl);
+int ring_slots_that_fit(const cia_plan *pl);
 int64_t stream_tile_buf_bytes(const cia_plan *pl, int64_t lam, int64_t blob_bytes);
 size_t window_smem_bytes(const cia_plan *pl);
 

@@ -35,9 +35,6 @@ constexpr int kWarps = kThreads / 32;
 #ifndef CIA_WINDOW_MIN_BLOCKS
 #define CIA_WINDOW_MIN_BLOCKS 4    // resident CTAs per SM the window kernel's registers are sized for
 #endif
-#ifndef CIA_STREAM_MIN_BLOCKS
-#define CIA_STREAM_MIN_BLOCKS 4    // resident CTAs per SM the persistent per-tile kernel is sized for
-#endif
 #ifndef CIA_WINDOW_VECTORS
 #define CIA_WINDOW_VECTORS 2       // missing-index vectors of a chunk loaded before any is used (<= 8)
 #endif
@@ -101,8 +98,8 @@ __host__ __device__ constexpr size_t zrun_bytes(int64_t runs, int p, size_t comp
 }
 
 // Shared-memory phasor entries per harmonic for TMA staging: lambda_max, the
-// kPadSlots zero entries after it, and up to one entry before it and one
-// after from rounding the window to 16 bytes.
+// guard and kPadSlots zero entries after it, and up to one entry before it
+// from rounding the window to 16 bytes.
 int64_t tma_ph_region(const cia_plan *pl) { return (pl->max_comm + kPadSlots + 3) & ~(int64_t)1; }
 
 template <typename T>
@@ -130,6 +127,9 @@ struct StageParams {
     C *ph_out;                 // [P][ph_stride] phasors of the next stage state
     const double *part_in;     // [tiles][P] complex tile sums of ph_in
     double *part_out;          // [tiles][P] complex tile sums of ph_out
+    const double *z_in;        // ring kernel: [M][P] community observables of ph_in
+    double *z_out;             // ring kernel: [M][P] community observables of ph_out
+    int *comm_done;            // ring kernel: [M] tiles finished per community (reset by the last)
     // kRhs
     const T *omega;
     const int32_t *perm;
@@ -455,9 +455,9 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
         if (dense) mbar_wait_bounded(&wbar, 0, kWaitLimitNs);
         return;
     }
-    // the padding entries lambda .. lambda + kPadSlots - 1 read zero phasors
-    if (dense && threadIdx.x < P * kPadSlots)
-        win[(size_t)(threadIdx.x / kPadSlots) * a.ph_region + d.shift + d.lam + threadIdx.x % kPadSlots] =
+    // the padding entries lambda .. lambda + kPadSlots read zero phasors
+    if (dense && threadIdx.x < P * (kPadSlots + 1))
+        win[(size_t)(threadIdx.x / (kPadSlots + 1)) * a.ph_region + d.shift + d.lam + threadIdx.x % (kPadSlots + 1)] =
             mk2(T(0), T(0));
     __syncthreads();
 
@@ -603,159 +603,282 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
 }
 
-// ---- persistent CIA stage, per-tile staging (staging 4) ---------------------
+// Z_c = sum of community c's tile partials in FP64, by one warp: lane j adds
+// tiles j, j + 32, ..., then a fixed xor tree (the order of
+// community_observable); every lane ends with the sums.  part is read
+// through L2, so that partials other CTAs wrote in this launch are seen.
+template <int P>
+__device__ __forceinline__ void community_sum_fp64(const int32_t *comm_tile_begin, const double *part, int c, int lane,
+                                                   double (&re)[P], double (&im)[P]) {
+    const int u0 = comm_tile_begin[c], u1 = comm_tile_begin[c + 1];
+#pragma unroll
+    for (int k = 0; k < P; ++k) re[k] = im[k] = 0.0;
+    for (int u = u0 + lane; u < u1; u += 32) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + (int64_t)u * P + k);
+            re[k] += v.x;
+            im[k] += v.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re[k] += __shfl_xor_sync(0xffffffffu, re[k], o);
+            im[k] += __shfl_xor_sync(0xffffffffu, im[k], o);
+        }
+    }
+}
+
+// (E1.1) Z_c of every community from the tile partials of a loaded state
+// (one warp per community), and the ring kernel's per-community counters
+// reset, before its first stage.
+template <int P>
+__global__ void community_sums_kernel(int64_t M, const int32_t *comm_tile_begin, const double *part, double *z,
+                                      int *comm_done) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    if (c >= M) return;
+    double re[P], im[P];
+    community_sum_fp64<P>(comm_tile_begin, part, (int)c, lane, re, im);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) reinterpret_cast<double2 *>(z)[c * P + k] = make_double2(re[k], im[k]);
+        comm_done[c] = 0;
+    }
+}
+
+// ---- persistent CIA stage with a ring of per-tile buffers (staging 4) -------
 //
-// Every CTA walks a fixed sequence of tiles: in round j, CTA c takes the
-// tile of launch rank j G + c (j even) or j G + G - 1 - c (j odd), G the
-// grid -- the costliest-first launch order dealt out in a snake, so that no
-// CTA's total work exceeds another's by more than one tile.  Per tile, one
-// mbarrier phase covers bulk (TMA) copies of the community's phasor window
-// (every harmonic) and of the tile's whole index blob into one shared-memory
-// buffer; Phase A then reads indices and missing-link phasors from shared
-// memory and only the inter-community phasors from global memory.  The
-// copies of the next tile are issued as soon as Phase A of the current one
-// has released the buffer (its descriptor arrives by cp.async during Phase
-// A), and its observable and node inputs are loaded while they fly, so the
-// per-tile setup overlaps Phase B of the current tile.
-template <typename T>
-__device__ __forceinline__ uint32_t stream_window_bytes(const TileDesc &d) {
-    // per harmonic: shift + lambda phasors and the kPadSlots zero entries, 16-byte rounded
+// One CTA per SM.  The last warp is the producer: for each of the CTA's
+// tiles (round k of CTA c takes launch rank k G + c for even k, k G + G - 1 - c
+// for odd k: the costliest-first order dealt out in a snake) it waits for a
+// free ring slot, copies the tile's descriptor into the slot's header, issues
+// bulk (TMA) copies of the community's phasor window (every harmonic) and of
+// the tile's index blob into the slot, writes the window's zero padding, sums
+// the community observable Z_c from the previous stage's tile partials and
+// then arrives on the slot's `full` barrier.  The other warps consume: they
+// take the slices of successive tiles round-robin (slice g of the running
+// count goes to warp g mod W), so no warp waits for another within a tile.
+// A slice holds whole rows: a row's missing list is cut into v chunks on v
+// consecutive lanes, the lanes' sums are combined by a segmented shuffle tree,
+// and the row's first lane applies the coupling, the RK4 stage update and the
+// next phasors (Phase B).  Each warp records its slice's phasor sums in the
+// slot header; the warp that completes a tile adds them in slice order into
+// the tile partial and every warp arrives on the slot's `empty` barrier.
+#ifndef CIA_RING_WARPS
+#define CIA_RING_WARPS 16           // consumer warps per CTA
+#endif
+constexpr int kRingWarps = CIA_RING_WARPS;
+constexpr int kRingThreads = 32 * (kRingWarps + 1);
+constexpr int kRingMaxSlots = 6;
+
+template <typename T, int P>
+struct RingHeader {
     using C = typename Vec2<T>::type;
-    return d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam + kPadSlots) * sizeof(C) + 15) & ~(size_t)15) : 0u;
+    TileDesc d;
+    C zc[P];
+    int tile;
+    int done;                                 // slices finished (the completing warp resets it)
+    double part[kRingMaxSlices][2 * P];       // per slice: sum of the next phasors
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+template <typename T, int P>
+__device__ __forceinline__ uint32_t ring_window_stride(const TileDesc &d) {
+    // bytes per harmonic: shift + lambda phasors, the guard entry and the
+    // kPadSlots zero entries, 16-byte rounded
+    using C = typename Vec2<T>::type;
+    return d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam + 1 + kPadSlots) * sizeof(C) + 15) & ~(size_t)15) : 0u;
 }
 
 template <typename T, int P, int MODE>
-__global__ void __launch_bounds__(kThreads, CIA_STREAM_MIN_BLOCKS) cia_stream_kernel(const StageParams<T> a) {
+__global__ void __launch_bounds__(kRingThreads, 1) cia_ring_kernel(const StageParams<T> a) {
     using C = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ C zc[P];
-    __shared__ double red[kWarps][2 * P];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ __align__(16) TileDesc sd[2];       // this round's tile and the next round's
-    __shared__ int s_tile[2];                      // their tile ids (-1: none)
+    __shared__ __align__(8) uint64_t full_bar[kRingMaxSlots], empty_bar[kRingMaxSlots];
+    __shared__ __align__(16) RingHeader<T, P> hdr[kRingMaxSlots];
+    __shared__ volatile int s_abort;
 
-    unsigned char *buf = smem_raw;                                              // window | blob
-    C *sWm = reinterpret_cast<C *>(smem_raw + a.tile_buf);                      // [P][kMaxChunks]
-    C *sWi = sWm + P * kMaxChunks;                                              // [P][tile_nodes]
-    const int64_t stride = a.ph_stride;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = a.stages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
-    auto rank_of = [&](int j) -> int64_t {
-        return (int64_t)j * G + ((j & 1) ? G - 1 - (int)blockIdx.x : (int)blockIdx.x);
+    const int64_t stride = a.ph_stride;
+    auto tile_at = [&](int k) -> int {
+        const int64_t rank = (int64_t)k * G + ((k & 1) ? G - 1 - (int)blockIdx.x : (int)blockIdx.x);
+        return rank < a.n_tiles ? a.tile_order[rank] : -1;
     };
-    auto tile_at = [&](int j) -> int { return rank_of(j) < a.n_tiles ? a.tile_order[rank_of(j)] : -1; };
-    // copies of one tile's window and blob, one mbarrier phase (thread 0)
-    auto issue = [&](const TileDesc &d) {
-        const uint32_t wreg = stream_window_bytes<T>(d);
-        const uint32_t wbytes = d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam) * sizeof(C) + 15) & ~(size_t)15) : 0u;
-        mbar_arrive_expect_tx(&bar, wbytes * P + d.blob_bytes);
-        if (wbytes)
-            for (int k = 0; k < P; ++k)
-                bulk_g2s(buf + (size_t)k * wreg, a.ph_in + k * stride + (d.lo - d.shift), wbytes, &bar);
-        if (d.blob_bytes) bulk_g2s(buf + (size_t)P * wreg, a.blob + d.blob_off, d.blob_bytes, &bar);
-    };
-
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        const int t0 = tile_at(0), t1 = tile_at(1);
-        s_tile[0] = t0;
-        s_tile[1] = t1;
-        if (t0 >= 0) {
-            sd[0] = a.tile_desc[t0];
-            issue(sd[0]);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full_bar[q], 1);
+            mbar_init(&empty_bar[q], kRingWarps);
+            hdr[q].done = 0;
         }
+        s_abort = 0;
     }
     __syncthreads();
-    int t = s_tile[0];
-    if (t < 0) return;
 
-    // node inputs of the current tile (registers) and its observable (warp 0)
-    const int r = threadIdx.x;
-    double theta_m = 0.0, wdt64_m = 0.0;
-    T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
-    int32_t perm_m = 0;
-    auto load_inputs = [&](const TileDesc &d) {
-        if (r < d.count) {
-            const int64_t m = d.first + r;
-            if (MODE == kRhs) {
-                omega_m = a.omega[m];
-                perm_m = a.perm[m];
-            } else {
-                theta_m = a.theta[m];
-                if (!a.first_stage) acc_m = a.acc[m];
-                if (MODE == kStage) wdt_m = a.wdt_next[m];
-                else wdt64_m = a.wdt64[m];
+    if (warp == kRingWarps) {
+        // ------------------------------------------------------------ producer
+        // lane 0 fetches the next tile's descriptor and community observable
+        // before it waits for that tile's slot, so the loads overlap the wait
+        int issued = 0;
+        int t_next = tile_at(0);
+        TileDesc d_next;
+        C z_next[P];
+        auto fetch = [&](int t) {
+            d_next = a.tile_desc[t];
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) {
+                const double2 zz = d_next.comm >= 0
+                                       ? reinterpret_cast<const double2 *>(a.z_in)[(int64_t)d_next.comm * P + kk]
+                                       : make_double2(0.0, 0.0);
+                z_next[kk] = mk2((T)zz.x, (T)zz.y);
             }
+        };
+        if (lane == 0 && t_next >= 0) fetch(t_next);
+        for (int k = 0; t_next >= 0; ++k) {
+            const int t = t_next;
+            const int q = k % S;
+            int ok = 1;
+            if (lane == 0) {
+                if (s_abort) ok = 0;
+                else if (k >= S) ok = mbar_wait_bounded(&empty_bar[q], (uint32_t)((k / S - 1) & 1), kWaitLimitNs);
+                if (!ok && !s_abort) {
+                    atomicExch(a.err_flag, 1);
+                    s_abort = 1;
+                }
+                if (ok) {
+                    hdr[q].d = d_next;
+                    hdr[q].tile = t;
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk) hdr[q].zc[kk] = z_next[kk];
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            __syncwarp();
+            const TileDesc &d = hdr[q].d;
+            unsigned char *buf = smem_raw + (size_t)q * a.tile_buf;
+            const uint32_t wreg = ring_window_stride<T, P>(d);
+            // the window rounded up to 16 bytes (the guard entry lambda may take
+            // the next community's first phasor) and the blob
+            const uint32_t wtma = d.comm >= 0 ? (uint32_t)(((size_t)(d.shift + d.lam) * sizeof(C) + 15) & ~(size_t)15) : 0u;
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(&full_bar[q], wtma * P + d.blob_bytes);
+                if (wtma)
+                    for (int kk = 0; kk < P; ++kk)
+                        bulk_g2s(buf + (size_t)kk * wreg, a.ph_in + kk * stride + (d.lo - d.shift), wtma, &full_bar[q]);
+                if (d.blob_bytes) bulk_g2s(buf + (size_t)P * wreg, a.blob + d.blob_off, d.blob_bytes, &full_bar[q]);
+            }
+            ++issued;
+            // the padding entries lambda + 1 .. lambda + kPadSlots (zero), beyond the copy
+            if (d.comm >= 0)
+                for (int i = lane; i < P * kPadSlots; i += 32)
+                    reinterpret_cast<C *>(buf + (size_t)(i / kPadSlots) * wreg)[d.shift + d.lam + 1 + i % kPadSlots] =
+                        mk2(T(0), T(0));
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[q]);                 // release: header and padding
+            t_next = tile_at(k + 1);
+            if (lane == 0 && t_next >= 0) fetch(t_next);
         }
-    };
-    load_inputs(sd[0]);
-    if (sd[0].comm >= 0) community_observable<T, P>(a, sd[0].comm, zc);
+        // every copy issued has landed before the CTA can retire
+        if (lane == 0)
+            for (int k = issued > S ? issued - S : 0; k < issued; ++k)
+                mbar_wait_bounded(&full_bar[k % S], (uint32_t)((k / S) & 1), kWaitLimitNs);
+        return;
+    }
 
-    for (int j = 0;; ++j) {
-        const int cur = j & 1, nxt = cur ^ 1;
-        const int tn = s_tile[nxt];
-        const TileDesc &d = sd[cur];
-        const bool dense = d.comm >= 0;
-        bool ok = mbar_wait_bounded(&bar, (uint32_t)(j & 1), kWaitLimitNs);
-        if (!ok && threadIdx.x == 0) atomicExch(a.err_flag, 1);
-        if (__syncthreads_or(!ok)) {
-            // the copies may still land: wait for them once more before the
-            // CTA's shared memory is released
-            mbar_wait_bounded(&bar, (uint32_t)(j & 1), kWaitLimitNs);
+    // -------------------------------------------------------------- consumers
+    // this CTA's tiles: the rounds whose launch rank exists (no memory access)
+    int ntiles = 0;
+    while ((int64_t)ntiles * G + ((ntiles & 1) ? G - 1 - (int)blockIdx.x : (int)blockIdx.x) < a.n_tiles) ++ntiles;
+    int64_t base = 0;   // slices of the tiles before this one
+    for (int k = 0; k < ntiles; ++k) {
+        const int q = k % S;
+        bool ok = mbar_wait_bounded(&full_bar[q], (uint32_t)((k / S) & 1), kWaitLimitNs);
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(a.err_flag, 1);
+                s_abort = 1;
+            }
             return;
         }
-        const uint32_t wreg = stream_window_bytes<T>(d);
-        const int wstride = (int)(wreg / sizeof(C));                 // entries between harmonics
-        const C *cw = reinterpret_cast<const C *>(buf) + d.shift;   // cw[k * wstride + l]
-        // the padding entries lambda .. lambda + kPadSlots - 1 read zero phasors
-        if (dense && threadIdx.x < P * kPadSlots)
-            reinterpret_cast<C *>(buf)[(threadIdx.x / kPadSlots) * wstride + d.shift + d.lam +
-                                       threadIdx.x % kPadSlots] = mk2(T(0), T(0));
-        __syncthreads();
+        const RingHeader<T, P> &h = hdr[q];
+        const int t = h.tile;
+        const int nsl = h.d.nsl, count = h.d.count;
+        const bool dense = h.d.comm >= 0;
+        const int64_t first = h.d.first, lo = h.d.lo;
+        const unsigned char *buf = smem_raw + (size_t)q * a.tile_buf;
+        const uint32_t wreg = ring_window_stride<T, P>(h.d);
+        const int wstride = (int)(wreg / sizeof(C));
+        const C *cw = reinterpret_cast<const C *>(buf) + h.d.shift;        // cw[k * wstride + l]
         const unsigned char *b = buf + (size_t)P * wreg;
         const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
-        const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
-        const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
-        const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
-        const bool live = r < d.count;
-        const int64_t m = d.first + r;
-        const int lo = (int)d.lo, first = d.first;
-        const uint32_t vt = live ? reinterpret_cast<const uint32_t *>(b + d.vtab_off)[r] : 0u;
-        C um[P];
+        const uint32_t *lmap = reinterpret_cast<const uint32_t *>(b + 16 * nsl);
+        const uint4 *mvec = reinterpret_cast<const uint4 *>(b + h.d.mvec_off);
+        const int4 *ivec = reinterpret_cast<const int4 *>(b + h.d.ivec_off);
+        const T kn = a.tile_kn ? a.tile_kn[t] : a.k_over_n;
+        (void)count;
+        int mine = 0;
+        for (int sl = (int)(((int64_t)warp - base) % kRingWarps + kRingWarps) % kRingWarps; sl < nsl;
+             sl += kRingWarps) {
+            ++mine;
+            const uint32_t mw = lmap[sl * 32 + lane];
+            const bool live = mw != 0xffffffffu;
+            const int r = (int)(mw & 0xffffu), v = (int)((mw >> 16) & 63u), off = (int)((mw >> 22) & 31u);
+            const bool head = live && off == 0;
+            const int64_t m = first + r;
+            // node inputs of the row (first lane), loaded while the gathers run
+            double theta_m = 0.0, wdt64_m = 0.0;
+            T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
+            int32_t perm_m = 0;
+            C um[P];
 #pragma unroll
-        for (int k = 0; k < P; ++k)
-            um[k] = !live ? mk2(T(0), T(0)) : dense ? cw[k * wstride + (first + r - lo)] : __ldg(a.ph_in + k * stride + m);
-        // the next round's descriptor (async, into the other slot) and tile id
-        if (warp == 0 && lane < 4 && tn >= 0)
-            cp_async16(reinterpret_cast<uint4 *>(&sd[nxt]) + lane, reinterpret_cast<const uint4 *>(a.tile_desc + tn) + lane);
-        const int t2 = threadIdx.x == 0 ? tile_at(j + 2) : -1;
-
-        // Phase A: warp per slice, lane per row
-        for (int sl = warp; sl < d.nsl; sl += kWarps) {
+            for (int kk = 0; kk < P; ++kk) um[kk] = mk2(T(0), T(0));
+            if (head) {
+                if (MODE == kRhs) {
+                    omega_m = a.omega[m];
+                    perm_m = a.perm[m];
+                } else {
+                    theta_m = a.theta[m];
+                    if (!a.first_stage) acc_m = a.acc[m];
+                    if (MODE == kStage) wdt_m = a.wdt_next[m];
+                    else wdt64_m = a.wdt64[m];
+                }
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk)
+                    um[kk] = dense ? cw[kk * wstride + (int)(m - lo)] : __ldg(a.ph_in + kk * stride + m);
+            }
+            // Phase A: inter-community gathers (global) issued first, missing
+            // links from the shared-memory window while they fly
             const uint4 sdv = sdesc[sl];
-            const uint32_t rows = srows[sl * 32 + lane];
-            const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
             C macc[P], iacc[P];
 #pragma unroll
-            for (int k = 0; k < P; ++k) macc[k] = iacc[k] = mk2(T(0), T(0));
+            for (int kk = 0; kk < P; ++kk) macc[kk] = iacc[kk] = mk2(T(0), T(0));
             const int4 *iv = ivec + sdv.z + lane;
             const uint4 *mv = mvec + sdv.x + lane;
-            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;   // inter vectors gathered ahead
+            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;
             for (uint32_t j0 = 0; j0 < sdv.w || j0 == 0; j0 += kPre) {
                 C pre[kPre][4][P];
 #pragma unroll
-                for (uint32_t q = 0; q < kPre; ++q) {
-                    if (j0 + q < sdv.w) {
-                        const int4 iq = iv[32 * (j0 + q)];
+                for (uint32_t qq = 0; qq < kPre; ++qq) {
+                    if (j0 + qq < sdv.w) {
+                        const int4 iq = iv[32 * (j0 + qq)];
                         const int l4[4] = {iq.x, iq.y, iq.z, iq.w};
 #pragma unroll
                         for (int hh = 0; hh < 4; ++hh)
 #pragma unroll
-                            for (int k = 0; k < P; ++k) pre[q][hh][k] = __ldg(a.ph_in + k * stride + l4[hh]);
+                            for (int kk = 0; kk < P; ++kk) pre[qq][hh][kk] = __ldg(a.ph_in + kk * stride + l4[hh]);
                     }
                 }
                 if (j0 == 0) {
-                    // missing links from the shared-memory window while the gathers fly
 #pragma unroll 2
                     for (uint32_t jj = 0; jj < sdv.y; ++jj) {
                         const uint4 mq = mv[32 * jj];
@@ -764,101 +887,139 @@ __global__ void __launch_bounds__(kThreads, CIA_STREAM_MIN_BLOCKS) cia_stream_ke
                         for (int hh = 0; hh < 4; ++hh) {
                             const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
 #pragma unroll
-                            for (int k = 0; k < P; ++k)
-                                macc[k] = add2(macc[k], add2(cw[k * wstride + l0], cw[k * wstride + l1]));
+                            for (int kk = 0; kk < P; ++kk)
+                                macc[kk] = add2(macc[kk], add2(cw[kk * wstride + l0], cw[kk * wstride + l1]));
                         }
                     }
                 }
 #pragma unroll
-                for (uint32_t q = 0; q < kPre; ++q) {
-                    if (j0 + q < sdv.w) {
+                for (uint32_t qq = 0; qq < kPre; ++qq) {
+                    if (j0 + qq < sdv.w) {
 #pragma unroll
-                        for (int k = 0; k < P; ++k)
-                            iacc[k] = add2(iacc[k], add2(add2(pre[q][0][k], pre[q][1][k]), add2(pre[q][2][k], pre[q][3][k])));
+                        for (int kk = 0; kk < P; ++kk)
+                            iacc[kk] = add2(iacc[kk], add2(add2(pre[qq][0][kk], pre[qq][1][kk]),
+                                                           add2(pre[qq][2][kk], pre[qq][3][kk])));
                     }
                 }
             }
-            if (mrow != 0xffffu) {
+            // a row's chunk sums: segmented tree over its v lanes (the first lane
+            // ends with lanes [0, v) of the row, in a fixed order)
 #pragma unroll
-                for (int k = 0; k < P; ++k) sWm[k * kMaxChunks + mrow] = mk2(-macc[k].x, -macc[k].y);
-            }
-            if (irow != 0xffffu) {
+            for (int o = 1; o < 32; o <<= 1) {
+                const bool take = live && off + o < v;
 #pragma unroll
-                for (int k = 0; k < P; ++k) sWi[k * a.tile_nodes + irow] = iacc[k];
-            }
-        }
-        if (warp == 0 && lane < 4) cp_async_wait_all();
-        __syncthreads();   // Phase A done: window and blob free, sums complete, next descriptor landed
-        if (threadIdx.x == 0) {
-            if (tn >= 0) {
-                fence_proxy_async_smem();
-                issue(sd[nxt]);
-            }
-            s_tile[cur] = t2;
-        }
-
-        // Phase B, thread per node
-        T sre[P], sim[P];
-#pragma unroll
-        for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
-        if (live) {
-            T coup = T(0);
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const C u = um[k];
-                C w = sWi[k * a.tile_nodes + r];
-                for (int c = (int)(vt & 0xffffu); c < (int)(vt & 0xffffu) + (int)(vt >> 16); ++c) {
-                    const C v = sWm[k * kMaxChunks + c];
-                    w.x += v.x;
-                    w.y += v.y;
+                for (int kk = 0; kk < P; ++kk) {
+                    const T xr = __shfl_down_sync(0xffffffffu, macc[kk].x, o);
+                    const T xi = __shfl_down_sync(0xffffffffu, macc[kk].y, o);
+                    if (take) macc[kk] = mk2(macc[kk].x + xr, macc[kk].y + xi);
                 }
-                T zr = w.x, zi = w.y;
-                if (dense) {
-                    // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
-                    zr += zc[k].x - u.x;
-                    zi += zc[k].y - u.y;
-                }
-                const T re = zr * u.x + zi * u.y;
-                const T im = zi * u.x - zr * u.y;
-                coup += a.d_sin[k] * im + a.d_cos[k] * re;
             }
-            coup *= a.tile_kn ? a.tile_kn[t] : a.k_over_n;
-            if (P >= 2 && dense && a.k2_over_n2 != T(0))
-                coup += a.k2_over_n2 * triadic_from_moments<T>(zc[0].x, zc[0].y, zc[P >= 2 ? 1 : 0].x,
-                                                               zc[P >= 2 ? 1 : 0].y, um[0].x, um[0].y,
-                                                               um[P >= 2 ? 1 : 0].x, um[P >= 2 ? 1 : 0].y);
-            if (a.tri) coup += a.tri[m];
-            if (MODE == kRhs) {
-                a.rhs_out[perm_m] = (double)omega_m + (double)coup;
-            } else {
-                const T accv = acc_m + a.b_s * coup;
-                T y;
-                if (MODE == kStage) {
-                    a.acc[m] = accv;
-                    y = (T)theta_m + wdt_m + a.c_next_dt * coup;
+            // Phase B, first lane of each row
+            T sre[P], sim[P];
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) sre[kk] = sim[kk] = T(0);
+            if (head) {
+                T coup = T(0);
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) {
+                    const C u = um[kk];
+                    T zr = iacc[kk].x - macc[kk].x, zi = iacc[kk].y - macc[kk].y;
+                    if (dense) {
+                        // (E1.2) dense term: the whole block minus its diagonal (a_mm = 0)
+                        zr += h.zc[kk].x - u.x;
+                        zi += h.zc[kk].y - u.y;
+                    }
+                    const T re = zr * u.x + zi * u.y;
+                    const T im = zi * u.x - zr * u.y;
+                    coup += a.d_sin[kk] * im + a.d_cos[kk] * re;
+                }
+                coup *= kn;
+                if (P >= 2 && dense && a.k2_over_n2 != T(0))
+                    coup += a.k2_over_n2 * triadic_from_moments<T>(h.zc[0].x, h.zc[0].y, h.zc[P >= 2 ? 1 : 0].x,
+                                                                   h.zc[P >= 2 ? 1 : 0].y, um[0].x, um[0].y,
+                                                                   um[P >= 2 ? 1 : 0].x, um[P >= 2 ? 1 : 0].y);
+                if (a.tri) coup += a.tri[m];
+                if (MODE == kRhs) {
+                    a.rhs_out[perm_m] = (double)omega_m + (double)coup;
                 } else {
-                    // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
-                    const double th = wrap_pi(theta_m + wdt64_m + a.dt * (double)accv);
-                    a.theta[m] = th;
-                    y = (T)th;
-                }
-                C u[P];
-                phasors<T, P>(y, u);
+                    const T accv = acc_m + a.b_s * coup;
+                    T y;
+                    if (MODE == kStage) {
+                        a.acc[m] = accv;
+                        y = (T)theta_m + wdt_m + a.c_next_dt * coup;
+                    } else {
+                        // FP64 time accumulation: theta += dt omega + dt sum_s b_s C_s
+                        const double th = wrap_pi(theta_m + wdt64_m + a.dt * (double)accv);
+                        a.theta[m] = th;
+                        y = (T)th;
+                    }
+                    C u[P];
+                    phasors<T, P>(y, u);
 #pragma unroll
-                for (int k = 0; k < P; ++k) {
-                    a.ph_out[k * stride + m] = u[k];
-                    sre[k] = u[k].x;
-                    sim[k] = u[k].y;
+                    for (int kk = 0; kk < P; ++kk) {
+                        a.ph_out[kk * stride + m] = u[kk];
+                        sre[kk] = u[kk].x;
+                        sim[kk] = u[kk].y;
+                    }
+                }
+            }
+            if (MODE != kRhs) {
+#pragma unroll
+                for (int kk = 0; kk < P; ++kk) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sre[kk] += __shfl_xor_sync(0xffffffffu, sre[kk], o);
+                        sim[kk] += __shfl_xor_sync(0xffffffffu, sim[kk], o);
+                    }
+                }
+                if (lane < P) {
+                    hdr[q].part[sl][2 * lane] = (double)sre[lane];
+                    hdr[q].part[sl][2 * lane + 1] = (double)sim[lane];
                 }
             }
         }
-        if (MODE != kRhs) block_tile_sum<T, P>(sre, sim, red, a.part_out + (size_t)t * P * 2);
-        else __syncthreads();   // zc is read above before warp 0 replaces it
-        if (tn < 0) break;
-        // the next tile's node inputs and observable, while its copies fly
-        load_inputs(sd[nxt]);
-        if (sd[nxt].comm >= 0) community_observable<T, P>(a, sd[nxt].comm, zc);
-        t = tn;
+        base += nsl;
+        // the warp that finishes the tile's last slice writes its partial sums
+        int last = 0;
+        if (MODE != kRhs) {
+            if (lane == 0 && mine > 0) {
+                __threadfence_block();
+                last = atomicAdd(&hdr[q].done, mine) + mine == nsl;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                if (lane < 2 * P) {
+                    double sum = 0.0;
+                    for (int sl = 0; sl < nsl; ++sl) sum += hdr[q].part[sl][lane];
+                    a.part_out[(size_t)t * P * 2 + lane] = sum;
+                }
+                // the partial is visible device-wide before the community counter moves
+                __threadfence();
+                if (lane == 0) hdr[q].done = 0;
+            }
+        }
+        const int comm = h.d.comm;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[q]);                    // the slot is free again
+        if (last && comm >= 0) {
+            // the community's last tile: its observable for the next stage from
+            // every tile partial, in the fixed order of the other kernels
+            int fin = 0;
+            if (lane == 0)
+                fin = atomicAdd(a.comm_done + comm, 1) + 1 == a.comm_tile_begin[comm + 1] - a.comm_tile_begin[comm];
+            if (__shfl_sync(0xffffffffu, fin, 0)) {
+                __threadfence();
+                double re[P], im[P];
+                community_sum_fp64<P>(a.comm_tile_begin, a.part_out, comm, lane, re, im);
+                if (lane == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < P; ++kk)
+                        reinterpret_cast<double2 *>(a.z_out)[(int64_t)comm * P + kk] = make_double2(re[kk], im[kk]);
+                    a.comm_done[comm] = 0;
+                }
+            }
+        }
     }
 }
 
@@ -1073,7 +1234,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) cia_pipeline_kernel(const Sta
                     // the slots after the community are where padding entries point: zero them
                     if (!fail)
                         for (int kk = 0; kk < P; ++kk)
-                            for (int j = 0; j < kPadSlots; ++j)
+                            for (int j = 0; j <= kPadSlots; ++j)
                                 pbuf[(h.pbuf * P + kk) * a.ph_region + h.shift + h.lam + j] = mk2(T(0), T(0));
                 }
                 if (!fail && u >= 1) fail = !mbar_wait_bounded(&swempty_bar[b], (u - 1) & 1, kWaitLimitNs);
@@ -1575,6 +1736,7 @@ StageParams<T> base_params(cia_plan *pl, int method) {
     a.theta = pl->d.theta;
     a.wdt64 = pl->d.wdt_full64;
     a.n_tiles = pl->n_tiles;
+    a.comm_done = pl->d.comm_done;
     a.tile_buf = (int)((pl->max_tile_buf + 127) & ~(int64_t)127);
     a.ph_region = (int)tma_ph_region(pl);
     a.idx_cap = (int)((pl->max_tile_idx_bytes + 15) & ~(int64_t)15);
@@ -1610,15 +1772,15 @@ cudaError_t launch_cia_t(const cia_plan *pl, const StageParams<T> &a, cudaStream
     if (pl->staging == 2)
         return launch_kernel(cia_window_kernel<T, P, MODE>, pl, pl->n_tiles, window_smem_bytes(pl), &a, s);
     if (pl->staging == 4) {
-        auto kernel = cia_stream_kernel<T, P, MODE>;
-        const size_t smem = stream_smem_bytes(pl);
+        auto kernel = cia_ring_kernel<T, P, MODE>;
+        const size_t smem = (size_t)pl->ring_slots * (size_t)a.tile_buf;
         cudaError_t e = ensure_dynamic_smem((const void *)kernel, pl->device, smem);
         if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kernel, kThreads, smem);
-        if (e != cudaSuccess) return e;
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(pl->n_tiles, (int64_t)std::max(per_sm, 1) * pl->n_sms));
-        return launch_kernel(kernel, pl, grid, smem, &a, s);
+        StageParams<T> r = a;
+        r.stages = pl->ring_slots;
+        void *args[] = {&r};
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(pl->n_tiles, pl->n_sms));
+        return cudaLaunchKernel((const void *)kernel, dim3((unsigned)grid), dim3(kRingThreads), args, smem, s);
     }
     return launch_kernel(cia_stage_kernel<T, P, MODE>, pl, pl->n_tiles, stage_smem_bytes(pl, Method::CIA), &a, s);
 }
@@ -1671,6 +1833,16 @@ cudaError_t phasors_t(cia_plan *pl, const double *x, bool write_master, int slot
         case 4: phasor_kernel<T, 4><<<g, kThreads, 0, s>>>(pl->n, pl->ph_stride, pl->d.perm, pl->d.tile_first, pl->d.tile_count, x, theta, ph, part); break;
         default: return cudaErrorInvalidValue;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || pl->staging != 4 || pl->M == 0) return e;
+    // the ring kernel reads the community observables, not the tile partials
+    const unsigned blocks = (unsigned)((pl->M * 32 + 255) / 256);
+    switch (pl->p) {
+        case 1: community_sums_kernel<1><<<blocks, 256, 0, s>>>(pl->M, pl->d.comm_tile_begin, part, pl->d.zsum[slot], pl->d.comm_done); break;
+        case 2: community_sums_kernel<2><<<blocks, 256, 0, s>>>(pl->M, pl->d.comm_tile_begin, part, pl->d.zsum[slot], pl->d.comm_done); break;
+        case 3: community_sums_kernel<3><<<blocks, 256, 0, s>>>(pl->M, pl->d.comm_tile_begin, part, pl->d.zsum[slot], pl->d.comm_done); break;
+        default: community_sums_kernel<4><<<blocks, 256, 0, s>>>(pl->M, pl->d.comm_tile_begin, part, pl->d.zsum[slot], pl->d.comm_done); break;
+    }
     return cudaGetLastError();
 }
 
@@ -1680,6 +1852,7 @@ cudaError_t rhs_t(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t
     StageParams<T> a = base_params<T>(pl, method);
     a.ph_in = (const C *)pl->d.ph[slot];
     a.part_in = pl->d.part[slot];
+    a.z_in = pl->d.zsum[slot];
     a.rhs_out = dxdt;
     return dispatch_stage<T, kRhs>(pl, method, a, s);
 }
@@ -1695,6 +1868,8 @@ cudaError_t stage_t(cia_plan *pl, int method, int stage, int slot, double dt, cu
     a.ph_out = (C *)pl->d.ph[slot ^ 1];
     a.part_in = pl->d.part[slot];
     a.part_out = pl->d.part[slot ^ 1];
+    a.z_in = pl->d.zsum[slot];
+    a.z_out = pl->d.zsum[slot ^ 1];
     a.b_s = (T)b[stage - 1];
     a.c_next_dt = (T)(c_next[stage - 1] * dt);
     a.wdt_next = (const T *)(stage == 3 ? pl->d.wdt_full : pl->d.wdt_half);
@@ -1719,11 +1894,20 @@ size_t window_smem_bytes(const cia_plan *pl) {
     return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes);
 }
 
-// Dynamic shared memory of the persistent per-tile kernel: the largest tile's
-// window (every harmonic) and index blob, then chunk sums and inter sums.
+// Ring slots of the persistent ring kernel that fit the device's shared
+// memory (each holds the largest tile's window and blob), at most
+// kRingMaxSlots; the kernel needs two.
+int ring_slots_that_fit(const cia_plan *pl) {
+    const size_t slot = (size_t)((pl->max_tile_buf + 127) & ~(int64_t)127);
+    const size_t stat = pl->precision == CIA_FP64 ? sizeof(RingHeader<double, CIA_MAX_HARMONICS>)
+                                                  : sizeof(RingHeader<float, CIA_MAX_HARMONICS>);
+    const size_t avail = (size_t)pl->smem_optin - 1024 - kRingMaxSlots * (stat + 16);
+    return (int)std::min<size_t>(kRingMaxSlots, slot ? avail / slot : kRingMaxSlots);
+}
+
+// Dynamic shared memory of the persistent ring kernel with its slots.
 size_t stream_smem_bytes(const cia_plan *pl) {
-    const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
-    return (size_t)((pl->max_tile_buf + 127) & ~(int64_t)127) + cb * (size_t)(kMaxChunks + pl->tile_nodes);
+    return (size_t)std::max(pl->ring_slots, 2) * (size_t)((pl->max_tile_buf + 127) & ~(int64_t)127);
 }
 
 // Bytes of the per-tile buffer of the persistent per-tile kernel for a tile
@@ -1732,7 +1916,7 @@ size_t stream_smem_bytes(const cia_plan *pl) {
 int64_t stream_tile_buf_bytes(const cia_plan *pl, int64_t lam, int64_t blob_bytes) {
     const int64_t cb = pl->precision == CIA_FP64 ? 16 : 8;
     const int64_t shift = pl->precision == CIA_FP64 ? 0 : 1;
-    const int64_t wreg = lam > 0 ? ((shift + lam + kPadSlots) * cb + 15) & ~(int64_t)15 : 0;
+    const int64_t wreg = lam > 0 ? ((shift + lam + 1 + kPadSlots) * cb + 15) & ~(int64_t)15 : 0;
     return (int64_t)pl->p * wreg + blob_bytes;
 }
 

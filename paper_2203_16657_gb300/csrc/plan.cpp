@@ -16,6 +16,7 @@
 #include <omp.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -309,7 +310,7 @@ static bool colour_group(const uint16_t *const ent[], const int64_t len[], int G
 // are capped at the longest list rounded up to 8 plus CIA_SCHED_EXTRA_VECTORS
 // vectors; entries of a bank group that then has no free position are placed
 // last, at free positions of their lanes (conflicts).  Padding entries take
-// distinct unused bank groups: sentinel + j, j in [0, G), all of them zero
+// distinct unused bank groups: sentinel + 1 + j, j in [0, G), all of them zero
 // slots after the community window, when `spread` allows (else the sentinel
 // itself).  Returns the number of positions (a multiple of 8);
 // sc.out[p * 32 + lane].
@@ -325,13 +326,14 @@ static int64_t schedule_slice(const uint16_t *const ent[32], const int64_t len[3
             for (int64_t e = 0; e < len[q * G + u]; ++e) ++load[ent[q * G + u][e] & (G - 1)];
         for (int g = 0; g < G; ++g) delta = std::max(delta, load[g]);
     }
-    const int64_t ncol = std::min<int64_t>(std::min<int64_t>((delta + 7) / 8 * 8, npos_min + 8 * CIA_SCHED_EXTRA_VECTORS), 128);
+    const int64_t ncol = std::min<int64_t>((delta + 7) / 8 * 8, npos_min + 8 * CIA_SCHED_EXTRA_VECTORS);
     sc.out.assign((size_t)ncol * 32, sentinel);
     if (ncol == 0) return 0;
     sc.lane_at.resize((size_t)G * ncol);
     sc.grp_at.resize((size_t)G * ncol);
     for (int q = 0; q < 32 / G; ++q) {
-        if (!colour_group(ent + q * G, len + q * G, G, ncol, sc))
+        // the colour sets hold 128 positions: longer lists take the greedy order
+        if (ncol > 128 || !colour_group(ent + q * G, len + q * G, G, ncol, sc))
             greedy_group(ent + q * G, len + q * G, G, ncol, sc.lane_at.data(), sc);
         const int32_t *LA = sc.lane_at.data();
         // padding entries: distinct bank groups unused at their position
@@ -348,7 +350,7 @@ static int64_t schedule_slice(const uint16_t *const ent[32], const int64_t len[3
                 } else if (spread) {
                     while (g < G && (used >> g & 1u)) ++g;
                     const int gg = g < G ? g : (sentinel & (G - 1));
-                    v = (uint16_t)(sentinel + ((gg - sentinel) & (G - 1)));
+                    v = (uint16_t)(sentinel + 1 + ((gg - sentinel - 1) & (G - 1)));
                     if (g < G) used |= 1u << g;
                 } else {
                     v = sentinel;
@@ -444,6 +446,103 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, bool spread,
                     ivec[4 * (iv + 32 * j + lane) + h] = has ? inter_col[inter_off[f + ir] + e] : inter_sent;
                 }
             // position p of the schedule is entry h = p % 8 of vector j = p / 8
+            for (int64_t p = 0; p < 8 * nvm[s]; ++p)
+                mvec[8 * (mv + 32 * (p / 8) + lane) + (p % 8)] = sched[s][(size_t)p * 32 + lane];
+        }
+        mv += 32 * nvm[s];
+        iv += 32 * nvi[s];
+    }
+}
+
+// Segmented blob of one tile for the persistent ring kernel: every row's
+// missing list is cut into v near-equal chunks (v = ceil(len / 64), at most 32)
+// that occupy v consecutive lanes of one slice, so that a warp can add a row's
+// chunk sums itself; rows (longest first) fill slices of 32 lanes in order, a
+// row that does not fit the current slice opening the next.  Lane map word:
+// row within the tile | v << 16 | lane offset within the row << 22
+// (0xffffffff: no row); the inter-community list of a row sits on its first
+// lane.  Layout: [slice descriptors: nsl x uint4 (miss offset, miss vectors,
+// inter offset, inter vectors)][lane maps: nsl x 32 x u32][missing vectors:
+// 8 x u16][inter vectors: 4 x i32].
+static constexpr int64_t kSegChunk = 64;
+
+static int64_t seg_lanes(int64_t entries) {
+    return std::min<int64_t>(32, std::max<int64_t>(1, (entries + kSegChunk - 1) / kSegChunk));
+}
+
+static void build_tile_blob_seg(int64_t f, int64_t cnt, uint16_t msent, bool spread, int32_t inter_sent,
+                                int bank_lanes, const std::vector<int64_t> &miss_cnt,
+                                const std::vector<int64_t> &miss_off, const std::vector<uint16_t> &miss_local,
+                                const std::vector<int64_t> &inter_cnt, const std::vector<int64_t> &inter_off,
+                                const std::vector<int32_t> &inter_col, TileBlob &tb, MissScheduler &sc) {
+    std::vector<int32_t> order(cnt);
+    for (int64_t r = 0; r < cnt; ++r) order[r] = (int32_t)r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return miss_cnt[f + x] > miss_cnt[f + y]; });
+    // slices: per lane (row, chunk index, first entry, length)
+    struct Lane { int32_t row = -1, part = 0, v = 0; int64_t e0 = 0, len = 0; };
+    std::vector<std::array<Lane, 32>> sl;
+    int used = 32;
+    for (int32_t r : order) {
+        const int64_t E = miss_cnt[f + r], v = seg_lanes(E);
+        if (used + v > 32) {
+            sl.emplace_back();
+            used = 0;
+        }
+        int64_t e = 0;
+        for (int64_t c = 0; c < v; ++c) {
+            const int64_t len = E / v + (c < E % v ? 1 : 0);
+            sl.back()[used + c] = Lane{r, (int32_t)c, (int32_t)v, e, len};
+            e += len;
+        }
+        used += (int)v;
+    }
+    const int64_t nsl = (int64_t)sl.size();
+    std::vector<int64_t> nvm(nsl, 0), nvi(nsl, 0);
+    std::vector<std::vector<uint16_t>> sched(nsl);
+    int64_t mv = 0, iv = 0;
+    for (int64_t s = 0; s < nsl; ++s) {
+        const uint16_t *ent[32];
+        int64_t len[32];
+        int64_t imax = 0;
+        for (int lane = 0; lane < 32; ++lane) {
+            const Lane &L = sl[s][lane];
+            ent[lane] = L.row >= 0 ? miss_local.data() + miss_off[f + L.row] + L.e0 : nullptr;
+            len[lane] = L.row >= 0 ? L.len : 0;
+            if (L.row >= 0 && L.part == 0) imax = std::max<int64_t>(imax, inter_cnt[f + L.row]);
+        }
+        nvm[s] = schedule_slice(ent, len, bank_lanes, msent, spread, sc) / 8;
+        sched[s].swap(sc.out);
+        nvi[s] = (imax + 3) / 4;
+        mv += 32 * nvm[s];
+        iv += 32 * nvi[s];
+    }
+    tb.nsl = (int32_t)nsl;
+    tb.vtab_off = 0;
+    tb.mvec_off = (uint32_t)(144 * nsl);
+    tb.ivec_off = tb.mvec_off + (uint32_t)(16 * mv);
+    tb.bytes.assign(tb.ivec_off + 16 * iv, 0);
+    uint32_t *desc = reinterpret_cast<uint32_t *>(tb.bytes.data());
+    uint32_t *rows = reinterpret_cast<uint32_t *>(tb.bytes.data() + 16 * nsl);
+    uint16_t *mvec = reinterpret_cast<uint16_t *>(tb.bytes.data() + tb.mvec_off);
+    int32_t *ivec = reinterpret_cast<int32_t *>(tb.bytes.data() + tb.ivec_off);
+    mv = iv = 0;
+    for (int64_t s = 0; s < nsl; ++s) {
+        desc[4 * s + 0] = (uint32_t)mv;
+        desc[4 * s + 1] = (uint32_t)nvm[s];
+        desc[4 * s + 2] = (uint32_t)iv;
+        desc[4 * s + 3] = (uint32_t)nvi[s];
+        for (int lane = 0; lane < 32; ++lane) {
+            const Lane &L = sl[s][lane];
+            rows[32 * s + lane] = L.row < 0 ? 0xffffffffu
+                                            : (uint32_t)L.row | ((uint32_t)L.v << 16) | ((uint32_t)L.part << 22);
+            const bool head = L.row >= 0 && L.part == 0;
+            for (int64_t j = 0; j < nvi[s]; ++j)
+                for (int h = 0; h < 4; ++h) {
+                    const int64_t e = 4 * j + h;
+                    const bool has = head && e < inter_cnt[f + L.row];
+                    ivec[4 * (iv + 32 * j + lane) + h] = has ? inter_col[inter_off[f + L.row] + e] : inter_sent;
+                }
             for (int64_t p = 0; p < 8 * nvm[s]; ++p)
                 mvec[8 * (mv + 32 * (p / 8) + lane) + (p % 8)] = sched[s][(size_t)p * 32 + lane];
         }
@@ -883,7 +982,7 @@ static cia_status build_tiles(cia_plan *pl) {
             while (r < e && rows < pl->tile_nodes) {
                 // index vectors, plus (staging 4) the row's share of the blob's tables
                 int64_t rb = pad8(miss_cnt[r]) * 2 + pad4(inter_cnt[r]) * 4 + (budget_window ? 9 : 0);
-                int64_t rc = chunks_of(miss_cnt[r]);
+                int64_t rc = budget_window ? seg_lanes(miss_cnt[r]) : chunks_of(miss_cnt[r]);
                 if (rows > 0 && (bytes + rb > limit || chunks + rc > kMaxChunks)) break;
                 bytes += rb;
                 chunks += rc;
@@ -921,7 +1020,15 @@ static cia_status build_tiles(cia_plan *pl) {
     std::vector<unsigned char> blob;
     pl->max_tile_idx_bytes = 0;
     std::vector<int64_t> tile_bytes(T, 0);
-    if (pl->miss_idx_bytes == 2) {
+    pl->blob_segmented = false;
+    // the persistent ring kernel (staging 4) reads rows' chunks from consecutive
+    // lanes; when its ring does not fit, the chunk layout of the other kernels
+    // is built instead
+    for (int attempt = 0; attempt < 2 && pl->miss_idx_bytes == 2; ++attempt) {
+        // (the ring kernel needs tiles of at most 256 rows and spread padding)
+        const bool segmented = attempt == 0 && pl->staging_req == 4 && pl->tile_nodes <= 256 &&
+                               pl->max_comm + kPadSlots <= 65535;
+        pl->max_tile_idx_bytes = 0;
         std::vector<TileBlob> tbs(T);
 #pragma omp parallel
         {
@@ -936,10 +1043,14 @@ static cia_status build_tiles(cia_plan *pl) {
                 const bool wide = pl->model == CIA_MODEL_CUCKER_SMALE ||
                                   (pl->model != CIA_MODEL_POLYNOMIAL && pl->precision == CIA_FP64);
                 const int bank_lanes = wide ? 8 : 16;
-                // padding entries lambda .. lambda + 15 (zero slots after the window)
-                const bool spread = lam + kPadSlots - 1 <= 65535;
-                build_tile_blob(tile_first[t], tile_count[t], msent, spread, (int32_t)n, bank_lanes, miss_cnt, miss_off, miss_local,
-                                inter_cnt, inter_off, inter_col, tbs[t], sched);
+                // padding entries lambda + 1 .. lambda + 16 (zero slots after the window)
+                const bool spread = lam + kPadSlots <= 65535;
+                if (segmented)
+                    build_tile_blob_seg(tile_first[t], tile_count[t], msent, spread, (int32_t)n, bank_lanes, miss_cnt,
+                                        miss_off, miss_local, inter_cnt, inter_off, inter_col, tbs[t], sched);
+                else
+                    build_tile_blob(tile_first[t], tile_count[t], msent, spread, (int32_t)n, bank_lanes, miss_cnt,
+                                    miss_off, miss_local, inter_cnt, inter_off, inter_col, tbs[t], sched);
             }
         }
         std::vector<int64_t> blob_off(T + 1, 0);
@@ -950,12 +1061,14 @@ static cia_status build_tiles(cia_plan *pl) {
 #pragma omp parallel for schedule(dynamic, 64)
         for (int64_t t = 0; t < T; ++t) {
             std::memcpy(blob.data() + blob_off[t], tbs[t].bytes.data(), tbs[t].bytes.size());
+            tile_bytes[t] = (int64_t)tbs[t].bytes.size();
+            std::vector<unsigned char>().swap(tbs[t].bytes);
             TileDesc &d = tdesc[t];
             d.comm = tile_comm[t];
             d.first = tile_first[t];
             d.count = tile_count[t];
             d.nsl = tbs[t].nsl;
-            d.blob_bytes = (uint32_t)tbs[t].bytes.size();
+            d.blob_bytes = (uint32_t)tile_bytes[t];
             d.mvec_off = tbs[t].mvec_off;
             d.ivec_off = tbs[t].ivec_off;
             d.lam = d.comm >= 0 ? (uint32_t)(pl->off[d.comm + 1] - pl->off[d.comm]) : 0u;
@@ -968,7 +1081,6 @@ static cia_status build_tiles(cia_plan *pl) {
         }
         pl->max_tile_buf = 0;
         for (int64_t t = 0; t < T; ++t) {
-            tile_bytes[t] = (int64_t)tbs[t].bytes.size();
             pl->max_tile_idx_bytes = std::max<int64_t>(pl->max_tile_idx_bytes, tile_bytes[t]);
             pl->max_tile_buf = std::max<int64_t>(
                 pl->max_tile_buf,
@@ -977,6 +1089,10 @@ static cia_status build_tiles(cia_plan *pl) {
             pl->n_slices += tbs[t].nsl;
         }
         pl->blob_bytes = blob_off[T];
+        pl->blob_segmented = segmented;
+        bool slices_fit = true;
+        for (int64_t t = 0; t < T && segmented; ++t) slices_fit = slices_fit && tdesc[t].nsl <= kRingMaxSlices;
+        if (!segmented || (slices_fit && ring_slots_that_fit(pl) >= 2)) break;
     }
 
     // ---- upload
@@ -1004,6 +1120,12 @@ static cia_status build_tiles(cia_plan *pl) {
     } else {
         for (int b = 0; b < 2; ++b)
             if ((s2 = upload<double>(pl, &d.part[b], nullptr, (size_t)T * pl->p * 2, true)) != CIA_OK) return s2;
+        // community observables written by the ring kernel (staging 4) for the next stage
+        for (int b = 0; b < 2; ++b)
+            if ((s2 = upload<double>(pl, &d.zsum[b], nullptr, (size_t)std::max<int64_t>(M, 1) * pl->p * 2, true)) !=
+                CIA_OK)
+                return s2;
+        if ((s2 = upload<int>(pl, &d.comm_done, nullptr, (size_t)std::max<int64_t>(M, 1), true)) != CIA_OK) return s2;
     }
     // ensembles: K / N_i per tile and each instance's tile ranges
     if (pl->B > 1) {
@@ -1061,9 +1183,8 @@ static cia_status build_tiles(cia_plan *pl) {
         if (window_smem_bytes(pl) > (size_t)optin - 1024) pl->staging = 1;
     }
     if (pl->staging == 4) {
-        int optin = 0;
-        CIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
-        if (stream_smem_bytes(pl) > (size_t)optin - 1024) pl->staging = 1;
+        pl->ring_slots = pl->blob_segmented ? ring_slots_that_fit(pl) : 0;
+        if (pl->ring_slots < 2) pl->staging = 1;
     }
     if (pl->staging == 3) {
         // contiguous tile ranges, one per SM, balanced by the bytes each tile
@@ -1473,6 +1594,7 @@ extern "C" cia_status cia_plan_destroy(cia_plan_t *plan) {
 extern "C" cia_status cia_plan_get_info(const cia_plan_t *pl, cia_plan_info *info) {
     clear_error();
     if (!pl || !info) return fail(CIA_ERR_INVALID_ARG, "plan or info is NULL");
+    info->ring_slots = pl->staging == 4 ? pl->ring_slots : 0;
     info->n = pl->n;
     info->M = pl->M;
     info->n_free = pl->n_free;
@@ -1526,14 +1648,31 @@ extern "C" cia_status cia_plan_get_split(const cia_plan_t *pl, int64_t *miss_row
         const uint32_t *rows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
         const uint32_t *vtab = reinterpret_cast<const uint32_t *>(b + d.vtab_off);
         std::vector<int32_t> chunk_row;          // chunk -> tile row
-        for (int32_t r = 0; r < d.count; ++r)
-            for (uint32_t c = 0; c < (vtab[r] >> 16); ++c) chunk_row.push_back(r);
+        if (!pl->blob_segmented)
+            for (int32_t r = 0; r < d.count; ++r)
+                for (uint32_t c = 0; c < (vtab[r] >> 16); ++c) chunk_row.push_back(r);
         const uint16_t *sm = reinterpret_cast<const uint16_t *>(b + d.mvec_off);
         const int32_t *si = reinterpret_cast<const int32_t *>(b + d.ivec_off);
         for (int64_t sl = 0; sl < d.nsl; ++sl) {
             const uint32_t moff = desc[4 * sl], nvm = desc[4 * sl + 1], ioff = desc[4 * sl + 2], nvi = desc[4 * sl + 3];
             for (int lane = 0; lane < 32; ++lane) {
                 const uint32_t rr = rows[32 * sl + lane];
+                if (pl->blob_segmented) {
+                    // lane map: row | lanes of the row << 16 | lane within the row << 22
+                    if (rr == 0xffffffffu) continue;
+                    const int32_t row = (int32_t)(rr & 0xffffu);
+                    for (uint32_t j = 0; j < nvm; ++j)
+                        for (int h = 0; h < 8; ++h) {
+                            const uint16_t v = sm[8 * (moff + 32 * j + lane) + h];
+                            if (v < d.lam) mrow[d.first + row].push_back((int32_t)(d.lo + v));
+                        }
+                    for (uint32_t j = 0; j < nvi; ++j)
+                        for (int h = 0; h < 4; ++h) {
+                            const int32_t v = si[4 * (ioff + 32 * j + lane) + h];
+                            if (v != n) irow[d.first + row].push_back(v);
+                        }
+                    continue;
+                }
                 const uint32_t mr = rr & 0xffffu, ir = rr >> 16;
                 if (mr != 0xffffu)
                     for (uint32_t j = 0; j < nvm; ++j)

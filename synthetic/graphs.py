@@ -270,6 +270,38 @@ def hash_sbm_graph(sizes, p_in: float, *, seed: int, inter_degree: float = 0.0,
     return Graph(n=n, rowptr=rowptr, col=col, labels=comm.astype(np.int32), sizes=sizes)
 
 
+def hierarchical_sbm_graph(groups: int, subs: int, size: int, p_sub: float, p_group: float, *,
+                           seed: int, inter_degree: float = 0.0) -> Graph:
+    """Two-level planted partition: `groups` groups of `subs` communities of
+    `size` nodes; pairs inside a community are linked with probability p_sub,
+    pairs of different communities of one group with p_group, and
+    n*inter_degree/2 distinct uniform pairs of different groups.  Labels are
+    the small communities; node ids are in block order."""
+    rng = rng_for(seed)
+    g_n = subs * size
+    n = groups * g_n
+    sub_of = np.arange(g_n) // size
+    prob = np.where(sub_of[:, None] == sub_of[None, :], p_sub, p_group)
+    iu, ju = np.triu_indices(g_n, 1)
+    keys = []
+    for g in range(groups):
+        keep = rng.random(len(iu)) < prob[iu, ju]
+        i, j = iu[keep] + g * g_n, ju[keep] + g * g_n
+        keys += [i * n + j, j * n + i]
+    comm = np.repeat(np.arange(groups, dtype=np.int64), g_n)
+    if inter_degree > 0:
+        i, j = _inter_pairs_degree(comm, inter_degree, rng)
+        keys += [i * n + j, j * n + i]
+    allk = np.sort(np.concatenate(keys))
+    rows = allk // n
+    col = (allk - rows * n).astype(np.int32)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    labels = (np.arange(n) // size).astype(np.int32)
+    return Graph(n=n, rowptr=rowptr, col=col, labels=labels,
+                 sizes=np.full(groups * subs, size, dtype=np.int64))
+
+
 def complete_graph_communities(sizes, *, seed: int, shuffle: bool = True) -> Graph:
     """Disjoint complete graphs (p_in = 1, no inter-community links)."""
     return sbm_graph(sizes, 1.0, seed=seed, inter_degree=0.0, shuffle=shuffle)

@@ -331,3 +331,24 @@ def test_bounded_wait_reports_timeout_and_context_survives(cia, oracle_mod, torc
     with pytest.raises(cia.CiaError) as e:
         plan.selftest_bounded_wait(10)         # out of range
     assert e.value.status_name == "CIA_ERR_INVALID_ARG"
+
+
+def test_partition_choice_beats_the_s_minimal_partition(cia, torch_mod):
+    """Step P1's communities-vs-cost trade-off, measured: 4096 communities of
+    16 nodes (p_in 0.95) in groups of 8 linked at density 0.45, so that the
+    S-minimal partition keeps the small communities (one short tile each)
+    while merging a group adds only a few entries to S and removes 7 tiles.
+    The chosen partition must be coarser and faster, as measured, than the
+    partition with mu = 0."""
+    g = S.hierarchical_sbm_graph(512, 8, 16, 0.95, 0.45, seed=3, inter_degree=4.0)
+    rng = np.random.default_rng(0)
+    x0 = rng.uniform(-np.pi, np.pi, g.n)
+    om = rng.normal(size=g.n)
+    labels, rep = cia.choose_partition(g.rowptr, g.col, om, x0, 0.01, steps=10, K=2.0)
+    ms = rep["ms_per_step"]
+    assert rep["communities"][0] >= 2048            # mu = 0 keeps (nearly all) small communities
+    assert rep["chosen"] != 0
+    c = rep["chosen"]
+    assert rep["communities"][c] < rep["communities"][0] and ms[c] < ms[0]
+    assert rep["per_tile_us"] > 0 and rep["community_cost"] > 0
+    assert len(np.unique(labels[labels >= 0])) == rep["communities"][c]
