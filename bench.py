@@ -187,10 +187,38 @@ def direct_stage_bytes(info: dict, precision: str) -> float:
     return info["n"] * per_node + info["nnz_graph"] * 4
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one stage-1..3 launch of cia_window_kernel on
-# the full workload, from an ncu --set full capture on one GB300.  Valid for that kernel at
-# scale 1 only; it has to be measured again whenever the kernel changes.
-WINDOW_KERNEL_TRAFFIC = 61.19e6 + 0.62e6
+STAGE_KERNEL_SOURCES = ("kuramoto.cu", "plan.cpp", "sync.cuh", "cia_internal.h")
+
+
+def stage_kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the sources that decide a
+    Kuramoto stage launch's memory traffic (kernels and tile layout)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in STAGE_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_16657_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel` on
+    the full workload, from the line
+
+        traffic_per_launch: kernel=<name> bytes=<B> source=<hash>
+
+    of an ncu summary under profiles/, if it was captured from the current
+    sources (stage_kernel_source_hash); else None."""
+    import glob
+    import re
+    want = stage_kernel_source_hash()
+    pat = re.compile(r"traffic_per_launch:\s*kernel=(\S+)\s+bytes=([0-9.eE+]+)\s+source=([0-9a-f]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = pat.search(line)
+            if m and m.group(1) == kernel and m.group(3) == want:
+                return float(m.group(2))
+    return None
 
 
 def stage_kernel_name(info: dict) -> str:
@@ -814,7 +842,9 @@ def main():
             "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 8},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
-                     "traffic": WINDOW_KERNEL_TRAFFIC if (info["staging"] == 2 and args.scale == 1.0) else None,
+                     "traffic": measured_traffic({2: "cia_window_kernel", 4: "cia_ring_kernel"}.get(info["staging"], "?"))
+                                if args.scale == 1.0 else None,
+                     "traffic_source": stage_kernel_source_hash(),
                      "kernel": stage_kernel_name(info), "bytes_per_launch": sb,
                      "avg_launch_ms": stage_avg_ms, "peak_source": pk["source"]},
         "gpu_launches": int(prof["stage_launches"] + prof["other_launches"]),

@@ -256,7 +256,8 @@ cia_status cia_detect_communities(const cia_graph *g, const cia_detect_options *
  * expansion order p).  Three partitions are detected and planned with
  * `coupling` and `opt` (Kuramoto models), and each is timed for `steps` RK4
  * steps (after two warm-up steps) from the state x (host, g->n doubles,
- * original order) with step dt: 0 = the fewest entries of S (mu = 0), 1 = a
+ * original order) with step dt: 0 = the fewest entries of S (gamma p = 1/2,
+ * mu = 0), 1 = a
  * coarser probe (a charge of one average block's directed pairs per
  * community), 2 = the partition minimising the modelled stage time
  *   T = c_tile tiles + c_byte (bytes of nodes, missing links, inter links),
@@ -360,7 +361,8 @@ typedef struct {
 /* Autotuner: time `steps` RK4 steps of the CIA (after two warm-up steps) for
  * each candidate tiling -- the window kernel (staging 2) with 256-row tiles
  * and tile_index_bytes 32768, 65536 or 98304 or with 128-row tiles and 32768,
- * the pipelined (3) and the plain (1) kernel with 256-row tiles and 32768;
+ * the pipelined (3) and the plain (1) kernel with 256-row tiles and 32768, the
+ * ring kernel (4) with 256-row tiles and 49152 or 65536;
  * for Cucker--Smale, 64- or 128-row tiles with 16384 or 32768 -- starting
  * from the state x (device, n x d doubles, original order), and keep the
  * fastest.

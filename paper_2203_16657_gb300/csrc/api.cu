@@ -474,6 +474,7 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
         cands.push_back({128, 32768, 2});
         cands.push_back({256, 32768, 3});
         cands.push_back({256, 32768, 1});
+        for (int tib : {49152, 65536}) cands.push_back({256, tib, 4});
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -35,6 +35,12 @@ constexpr int kWarps = kThreads / 32;
 #ifndef CIA_WINDOW_MIN_BLOCKS
 #define CIA_WINDOW_MIN_BLOCKS 4    // resident CTAs per SM the window kernel's registers are sized for
 #endif
+#ifndef CIA_WINDOW_DYNAMIC
+#define CIA_WINDOW_DYNAMIC 1       // warps take the window kernel's slices from a shared counter
+#endif
+#ifndef CIA_WINDOW_RING
+#define CIA_WINDOW_RING 0          // > 0: index vectors per lane prefetched by cp.async (per-warp ring)
+#endif
 #ifndef CIA_WINDOW_VECTORS
 #define CIA_WINDOW_VECTORS 2       // missing-index vectors of a chunk loaded before any is used (<= 8)
 #endif
@@ -398,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     __shared__ C zc[P];
     __shared__ double red[kWarps][2 * P];
     __shared__ uint64_t wbar;
+    __shared__ int s_next;            // next slice to take (dynamic assignment)
 
     const int t = a.tile_order ? a.tile_order[blockIdx.x] : (int)blockIdx.x;
     const TileDesc d = a.tile_desc[t];
@@ -411,6 +418,12 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     C *sWm = win + (size_t)P * a.ph_region;                         // [P][kMaxChunks]
     C *sWi = sWm + P * kMaxChunks;                                  // [P][tile_nodes]
     const C *cw = win + d.shift;                                    // cw[k * ph_region + l], l in [0, lambda]
+#if CIA_WINDOW_RING
+    // per warp: a ring of CIA_WINDOW_RING missing-link index vectors per lane,
+    // filled by asynchronous copies ahead of their use
+    uint4 *vring = reinterpret_cast<uint4 *>(sWi + P * a.tile_nodes) + (size_t)warp * CIA_WINDOW_RING * 32;
+#endif
+    if (threadIdx.x == 0) s_next = kWarps;
     if (dense && threadIdx.x == 0) {
         mbar_init(&wbar, 1);
         const uint32_t bytes = (uint32_t)(((size_t)(d.shift + d.lam) * sizeof(C) + 15) & ~(size_t)15);
@@ -461,7 +474,13 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
             mk2(T(0), T(0));
     __syncthreads();
 
+#if CIA_WINDOW_DYNAMIC
+    // slices are taken in order (longest first) by whichever warp is free
+    for (int s = warp;; ) {
+        if (s >= d.nsl) break;
+#else
     for (int s = warp; s < d.nsl; s += kWarps) {
+#endif
         const uint4 sd = __ldg(sdesc + s);
         const uint32_t rows = __ldg(srows + s * 32 + lane);
         const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
@@ -502,6 +521,36 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
                 }
             }
             if (j0 == 0) {
+#if CIA_WINDOW_RING
+                // vector j is copied CIA_WINDOW_RING - 1 iterations before its use;
+                // each lane reads only the vectors it copied itself
+                constexpr int R = CIA_WINDOW_RING;
+                for (uint32_t j = kMv; j < kMv + R - 1; ++j) {
+                    if (j < sd.y) cp_async16(vring + (j % R) * 32 + lane, mv + 32 * j);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                }
+                for (uint32_t j = 0; j < sd.y; ++j) {
+                    uint4 q;
+                    if (j < kMv) {
+                        q = qm[j < kMv ? j : 0];
+                    } else {
+                        const uint32_t jn = j + R - 1;
+                        if (jn < sd.y) cp_async16(vring + (jn % R) * 32 + lane, mv + 32 * jn);
+                        asm volatile("cp.async.commit_group;" ::: "memory");
+                        asm volatile("cp.async.wait_group %0;" ::"n"(R - 1) : "memory");
+                        q = vring[(j % R) * 32 + lane];
+                    }
+                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int hh = 0; hh < 4; ++hh) {
+                        const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
+#pragma unroll
+                        for (int k = 0; k < P; ++k)
+                            macc[k] = add2(macc[k], add2(cw[k * a.ph_region + l0], cw[k * a.ph_region + l1]));
+                    }
+                }
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+#else
                 for (uint32_t m0 = 0; m0 < sd.y; m0 += kMv) {
                     if (m0 > 0) {
 #pragma unroll
@@ -522,6 +571,7 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
                         }
                     }
                 }
+#endif
             }
 #pragma unroll
             for (uint32_t j = 0; j < kPre; ++j) {
@@ -540,6 +590,11 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
 #pragma unroll
             for (int k = 0; k < P; ++k) sWi[k * a.tile_nodes + irow] = iacc[k];
         }
+#if CIA_WINDOW_DYNAMIC
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&s_next, 1);
+        s = __shfl_sync(0xffffffffu, nx, 0);
+#endif
     }
     __syncthreads();
     // Phase B, thread per node
@@ -1891,17 +1946,34 @@ size_t stage_smem_bytes(const cia_plan *pl, int method) {
 // of every harmonic, chunk sums and inter sums.
 size_t window_smem_bytes(const cia_plan *pl) {
     const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
-    return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes);
+    return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes) +
+           (size_t)kWarps * CIA_WINDOW_RING * 32 * sizeof(uint4);
 }
 
 // Ring slots of the persistent ring kernel that fit the device's shared
 // memory (each holds the largest tile's window and blob), at most
 // kRingMaxSlots; the kernel needs two.
+template <typename T, int P>
+size_t ring_static_smem() {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, cia_ring_kernel<T, P, kStage>) != cudaSuccess) {
+        cudaGetLastError();
+        return sizeof(RingHeader<T, CIA_MAX_HARMONICS>) * kRingMaxSlots + 1024;
+    }
+    return fa.sharedSizeBytes;
+}
+
 int ring_slots_that_fit(const cia_plan *pl) {
     const size_t slot = (size_t)((pl->max_tile_buf + 127) & ~(int64_t)127);
-    const size_t stat = pl->precision == CIA_FP64 ? sizeof(RingHeader<double, CIA_MAX_HARMONICS>)
-                                                  : sizeof(RingHeader<float, CIA_MAX_HARMONICS>);
-    const size_t avail = (size_t)pl->smem_optin - 1024 - kRingMaxSlots * (stat + 16);
+    size_t stat = 0;
+    switch (pl->p) {
+        case 1: stat = pl->precision == CIA_FP64 ? ring_static_smem<double, 1>() : ring_static_smem<float, 1>(); break;
+        case 2: stat = pl->precision == CIA_FP64 ? ring_static_smem<double, 2>() : ring_static_smem<float, 2>(); break;
+        case 3: stat = pl->precision == CIA_FP64 ? ring_static_smem<double, 3>() : ring_static_smem<float, 3>(); break;
+        default: stat = pl->precision == CIA_FP64 ? ring_static_smem<double, 4>() : ring_static_smem<float, 4>(); break;
+    }
+    if ((size_t)pl->smem_optin < stat + 1024 + 2 * slot) return 0;
+    const size_t avail = (size_t)pl->smem_optin - stat - 1024;
     return (int)std::min<size_t>(kRingMaxSlots, slot ? avail / slot : kRingMaxSlots);
 }
 

@@ -113,7 +113,9 @@ extern "C" cia_status cia_choose_partition(const cia_graph *g, const double *ome
     Candidate cand[3];
     cia_detect_options d0;
     cia_detect_options_default(&d0);
-    // 0: the partition with the fewest entries of S (mu = 0, gamma p at the paper's gamma)
+    // 0: the partition with the fewest entries of S (gamma p = 1/2, mu = 0)
+    const double density = (double)g->rowptr[g->n] / ((double)g->n * (double)(g->n - 1));
+    if (density > 0.0) d0.gamma = 0.5 / density;
     cia_status st = evaluate(g, &d0, omega, coupling, opt, x_dev, dt, steps, cand[0]);
     if (st != CIA_OK) return st;
     // 1: a coarser probe: a charge of one average block (directed pairs) per community
@@ -150,7 +152,6 @@ extern "C" cia_status cia_choose_partition(const cia_graph *g, const double *ome
         c_byte = std::max(1e-30, (t0 - c_tile * a0) / std::max(b0, 1.0));
     }
     const double c_miss = c_byte * bm, c_inter = c_byte * bi;
-    const double density = (double)g->rowptr[g->n] / ((double)g->n * (double)(g->n - 1));
     cia_detect_options d2 = d0;
     if (density > 0.0) d2.gamma = c_miss / (c_miss + c_inter) / density;
     d2.community_cost = c_tile / (c_miss + c_inter);

@@ -30,8 +30,12 @@
 
 namespace cia {
 
+// Raise a kernel's dynamic shared-memory limit to `smem` on `device` (once
+// per kernel, device and size): the default limit covers dynamic plus static
+// shared memory up to 48 KiB, so a kernel with static buffers can need the
+// attribute below 48 KiB of dynamic memory as well.
 cudaError_t ensure_dynamic_smem(const void *kernel, int device, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem == 0) return cudaSuccess;
     static std::mutex mu;
     static std::map<std::pair<const void *, int>, size_t> done;
     std::lock_guard<std::mutex> lock(mu);
@@ -155,7 +159,7 @@ struct MissScheduler {
 // Extra 8-entry vectors per slice that the conflict-free schedule may add
 // beyond the longest lane's list (padding entries read the zero slots).
 #ifndef CIA_SCHED_EXTRA_VECTORS
-#define CIA_SCHED_EXTRA_VECTORS 1
+#define CIA_SCHED_EXTRA_VECTORS 0
 #endif
 
 // Set of colours (positions) < 128.
@@ -464,7 +468,10 @@ static void build_tile_blob(int64_t f, int64_t cnt, uint16_t msent, bool spread,
 // lane.  Layout: [slice descriptors: nsl x uint4 (miss offset, miss vectors,
 // inter offset, inter vectors)][lane maps: nsl x 32 x u32][missing vectors:
 // 8 x u16][inter vectors: 4 x i32].
-static constexpr int64_t kSegChunk = 64;
+#ifndef CIA_SEG_CHUNK
+#define CIA_SEG_CHUNK 64
+#endif
+static constexpr int64_t kSegChunk = CIA_SEG_CHUNK;
 
 static int64_t seg_lanes(int64_t entries) {
     return std::min<int64_t>(32, std::max<int64_t>(1, (entries + kSegChunk - 1) / kSegChunk));

@@ -35,3 +35,25 @@ def test_p1_leg_line():
     d = _run("--only", "p1", "--scale", "0.0625")
     assert d["leg"] == "p1" and d["planted_partition_recovered"] is True
     assert d["nnz_s_detected"] == d["nnz_s_planted"] and d["seconds"] > 0
+
+
+def test_roofline_traffic_is_read_only_for_the_current_sources(tmp_path, monkeypatch):
+    """The bench takes a stage kernel's DRAM bytes per launch from an ncu
+    summary under profiles/ only if that summary was captured from the
+    current kernel sources (their hash); otherwise it reports none."""
+    import shutil
+    import bench
+    src = tmp_path / "paper_2203_16657_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for name in bench.STAGE_KERNEL_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2203_16657_gb300", "csrc", name), src / name)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.stage_kernel_source_hash()
+    (tmp_path / "profiles" / "k.md").write_text(
+        "traffic_per_launch: kernel=cia_window_kernel bytes=6.1e7 source=%s\n"
+        "traffic_per_launch: kernel=cia_ring_kernel bytes=5.0e7 source=0000000000000000\n" % h)
+    assert bench.measured_traffic("cia_window_kernel") == 6.1e7
+    assert bench.measured_traffic("cia_ring_kernel") is None       # stale capture
+    (src / "kuramoto.cu").write_text("// changed\n")
+    assert bench.measured_traffic("cia_window_kernel") is None     # the kernel changed since
