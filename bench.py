@@ -52,13 +52,19 @@ def parse():
     ap.add_argument("--no-cs", action="store_true",
                     help="skip the Cucker-Smale (learned basis) secondary workload")
     ap.add_argument("--cs-pairs", type=int, default=10_000_000, help="training pairs of the CS basis")
+    ap.add_argument("--cs-epochs", type=int, default=4, help="passes over the CS training pairs")
+    ap.add_argument("--cs-snapshots", type=int, default=10, help="trajectory snapshots the pairs are drawn from")
+    ap.add_argument("--cs-lr", type=float, default=3e-4, help="initial Adam step of the CS basis training")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble secondary workload")
     ap.add_argument("--ens-instances", type=int, default=4096,
                     help="instances of the seeded 4096-network ensemble to run")
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the small FP64 and the higher-order Kuramoto workloads")
     ap.add_argument("--no-poly", action="store_true", help="skip the polynomial-coupling workloads")
-    ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly", "p1"], default=None,
+    ap.add_argument("--no-partition", action="store_true", help="skip the P1 partition-choice leg")
+    ap.add_argument("--partition-bench-graph", action="store_true",
+                    help="also choose the partition of the 262144-node lognormal graph (about 2 minutes)")
+    ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly", "p1", "partition"], default=None,
                     help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
 
@@ -344,8 +350,8 @@ def cs_leg(args, torch, cia, flush) -> dict:
     basis = cia.Basis(cia.Basis.params_fourier(w.K, w.sigma, w.beta, 10.0, seed=2203166574))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    fit = plan.learn_fit(basis, x0, dt=w.dt, steps=100, snapshots=10, pairs=args.cs_pairs,
-                         seed=2203166575, batch=16384, epochs=4, lr=3e-4, lr_final=1e-5)
+    fit = plan.learn_fit(basis, x0, dt=w.dt, steps=100, snapshots=args.cs_snapshots, pairs=args.cs_pairs,
+                         seed=2203166575, batch=16384, epochs=args.cs_epochs, lr=args.cs_lr, lr_final=1e-5)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # accuracy at the initial state against the FP64 oracle (velocity part)
@@ -384,7 +390,7 @@ def cs_leg(args, torch, cia, flush) -> dict:
                                  "direct_rhs_velocity_rel": errs["direct"],
                                  "fourier_rank64_cia_rhs_velocity_rel": errs["fourier_rank64_oracle"],
                                  "sampled_check_err_over_ref": check},
-        "basis_training": {"pairs": fit["pairs"], "optimizer_steps": fit["steps"],
+        "basis_training": {"pairs": fit["pairs"], "epochs": args.cs_epochs, "optimizer_steps": fit["steps"],
                            "first_loss": fit["first_loss"], "last_epoch_loss": fit["last_epoch_loss"],
                            "seconds_incl_trajectory": train_s},
     }
@@ -587,6 +593,33 @@ def poly_leg(args, torch, cia, flush) -> dict:
     return out
 
 
+# ------------------------------------------------------------------ step P1: the partition, chosen by measurement
+
+def partition_leg(args, torch, cia, flush) -> dict:
+    """cia_choose_partition (the communities-vs-cost trade-off of step P1):
+    three detected partitions timed with the library's kernels, the fitted
+    stage-cost model, and the chosen community charge mu, on a graph of small
+    dense communities in groups (where merging pays) and, on request, on the
+    262144-node lognormal graph."""
+    import synthetic as S
+    out = {}
+    cases = [("hierarchical_512x8x16", S.hierarchical_sbm_graph(512, 8, 16, 0.95, 0.45, seed=3, inter_degree=4.0),
+              2.0)]
+    if args.partition_bench_graph:
+        w = S.kuramoto_lognormal(scale=args.scale)
+        cases.append(("kuramoto_lognormal", w.graph, w.K))
+    for name, g, K in cases:
+        rng = np.random.default_rng(0)
+        t0 = time.perf_counter()
+        _, rep = cia.choose_partition(g.rowptr, g.col, rng.normal(size=g.n), rng.uniform(-np.pi, np.pi, g.n),
+                                      0.01, steps=10, K=K)
+        rep["seconds"] = time.perf_counter() - t0
+        rep["candidates"] = ["S-minimal (gamma p = 1/2, mu = 0)", "probe (mu = mean block pairs)",
+                             "fitted model optimum"]
+        out[name] = rep
+    return out
+
+
 # ------------------------------------------------------------------ step P1 (host, offline)
 
 def p1_leg(args) -> dict:
@@ -735,7 +768,8 @@ def main():
     import paper_2203_16657_gb300 as cia
     if args.only:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-        leg = {"cs": cs_leg, "ensemble": ensemble_leg, "small": small_configs_leg, "poly": poly_leg}[args.only]
+        leg = {"cs": cs_leg, "ensemble": ensemble_leg, "small": small_configs_leg, "poly": poly_leg,
+               "partition": partition_leg}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, torch, cia, flush)}), flush=True)
         return 0
     w = S.kuramoto_lognormal(scale=args.scale)
@@ -807,6 +841,10 @@ def main():
     if not args.no_poly and world == 1:
         poly = poly_leg(args, torch, cia, flush)
 
+    part = None
+    if not args.no_partition and world == 1:
+        part = partition_leg(args, torch, cia, flush)
+
     pk = peaks()
     stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
     sb = stage_bytes(info, "fp32")
@@ -860,6 +898,8 @@ def main():
         line.update(small)
     if poly is not None:
         line["polynomial"] = poly
+    if part is not None:
+        line["partition_choice"] = part
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

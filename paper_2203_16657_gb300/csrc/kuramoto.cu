@@ -38,9 +38,6 @@ constexpr int kWarps = kThreads / 32;
 #ifndef CIA_WINDOW_DYNAMIC
 #define CIA_WINDOW_DYNAMIC 1       // warps take the window kernel's slices from a shared counter
 #endif
-#ifndef CIA_WINDOW_RING
-#define CIA_WINDOW_RING 0          // > 0: index vectors per lane prefetched by cp.async (per-warp ring)
-#endif
 #ifndef CIA_WINDOW_VECTORS
 #define CIA_WINDOW_VECTORS 2       // missing-index vectors of a chunk loaded before any is used (<= 8)
 #endif
@@ -418,11 +415,6 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     C *sWm = win + (size_t)P * a.ph_region;                         // [P][kMaxChunks]
     C *sWi = sWm + P * kMaxChunks;                                  // [P][tile_nodes]
     const C *cw = win + d.shift;                                    // cw[k * ph_region + l], l in [0, lambda]
-#if CIA_WINDOW_RING
-    // per warp: a ring of CIA_WINDOW_RING missing-link index vectors per lane,
-    // filled by asynchronous copies ahead of their use
-    uint4 *vring = reinterpret_cast<uint4 *>(sWi + P * a.tile_nodes) + (size_t)warp * CIA_WINDOW_RING * 32;
-#endif
     if (threadIdx.x == 0) s_next = kWarps;
     if (dense && threadIdx.x == 0) {
         mbar_init(&wbar, 1);
@@ -521,36 +513,6 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
                 }
             }
             if (j0 == 0) {
-#if CIA_WINDOW_RING
-                // vector j is copied CIA_WINDOW_RING - 1 iterations before its use;
-                // each lane reads only the vectors it copied itself
-                constexpr int R = CIA_WINDOW_RING;
-                for (uint32_t j = kMv; j < kMv + R - 1; ++j) {
-                    if (j < sd.y) cp_async16(vring + (j % R) * 32 + lane, mv + 32 * j);
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                }
-                for (uint32_t j = 0; j < sd.y; ++j) {
-                    uint4 q;
-                    if (j < kMv) {
-                        q = qm[j < kMv ? j : 0];
-                    } else {
-                        const uint32_t jn = j + R - 1;
-                        if (jn < sd.y) cp_async16(vring + (jn % R) * 32 + lane, mv + 32 * jn);
-                        asm volatile("cp.async.commit_group;" ::: "memory");
-                        asm volatile("cp.async.wait_group %0;" ::"n"(R - 1) : "memory");
-                        q = vring[(j % R) * 32 + lane];
-                    }
-                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int hh = 0; hh < 4; ++hh) {
-                        const int l0 = (int)(w4[hh] & 0xffffu), l1 = (int)(w4[hh] >> 16);
-#pragma unroll
-                        for (int k = 0; k < P; ++k)
-                            macc[k] = add2(macc[k], add2(cw[k * a.ph_region + l0], cw[k * a.ph_region + l1]));
-                    }
-                }
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-#else
                 for (uint32_t m0 = 0; m0 < sd.y; m0 += kMv) {
                     if (m0 > 0) {
 #pragma unroll
@@ -571,7 +533,6 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
                         }
                     }
                 }
-#endif
             }
 #pragma unroll
             for (uint32_t j = 0; j < kPre; ++j) {
@@ -1946,8 +1907,7 @@ size_t stage_smem_bytes(const cia_plan *pl, int method) {
 // of every harmonic, chunk sums and inter sums.
 size_t window_smem_bytes(const cia_plan *pl) {
     const size_t cb = (pl->precision == CIA_FP64 ? 16 : 8) * (size_t)pl->p;
-    return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes) +
-           (size_t)kWarps * CIA_WINDOW_RING * 32 * sizeof(uint4);
+    return cb * ((size_t)tma_ph_region(pl) + kMaxChunks + (size_t)pl->tile_nodes);
 }
 
 // Ring slots of the persistent ring kernel that fit the device's shared
