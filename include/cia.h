@@ -360,7 +360,8 @@ typedef struct {
 
 /* Autotuner: time `steps` RK4 steps of the CIA (after two warm-up steps) for
  * each candidate tiling -- the window kernel (staging 2) with 256-row tiles
- * and tile_index_bytes 32768, 65536 or 98304 or with 128-row tiles and 32768,
+ * and tile_index_bytes 32768, 65536 or 98304, with 128-row tiles and 32768 or
+ * with 64-row tiles and 16384,
  * the pipelined (3) and the plain (1) kernel with 256-row tiles and 32768, the
  * ring kernel (4) with 256-row tiles and 49152 or 65536;
  * for Cucker--Smale, 64- or 128-row tiles with 16384 or 32768 -- starting

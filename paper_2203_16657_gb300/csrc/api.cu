@@ -472,6 +472,7 @@ extern "C" cia_status cia_plan_autotune(cia_plan_t *pl, const double *x, double 
     } else {
         for (int tib : {32768, 65536, 98304}) cands.push_back({256, tib, 2});
         cands.push_back({128, 32768, 2});
+        cands.push_back({64, 16384, 2});
         cands.push_back({256, 32768, 3});
         cands.push_back({256, 32768, 1});
         for (int tib : {49152, 65536}) cands.push_back({256, tib, 4});
