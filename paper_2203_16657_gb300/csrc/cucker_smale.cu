@@ -135,8 +135,12 @@ __device__ __forceinline__ float4 rk4_update(const CsParams &a, int64_t m, float
     return y;
 }
 
+#ifndef CIA_CS_MIN_BLOCKS
+#define CIA_CS_MIN_BLOCKS 4   // resident CTAs per SM the stage launches' registers are sized for
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
+__global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(const CsParams a) {
     constexpr bool kFeatures = MODE == kLoad;  // phi of the state and its moment partial sums
     constexpr bool kSums = MODE != kLoad;      // the right-hand side and the stage update
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
     __shared__ float red[4][kPart];
     __shared__ float cred[kWarps][2];
     __shared__ float2 cen;
+    __shared__ int s_next;                     // next slice of the tile to take
 
     mlp::Weights &w = *reinterpret_cast<mlp::Weights *>(smem);
     unsigned char *region = smem + (kFeatures ? kWeightsBytes : 0);
@@ -185,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
         // (0) community window, own rows, moments, chunk -> row table
         for (int i = t; i < lam; i += kThreads) win[i] = a.y_in[d.lo + i];
         if (t < count) yrow[t] = a.y_in[d.first + t];
+        if (t == 0) s_next = kWarps;   // the previous tile's slices ended at its last barrier
         if (kSums) {
             if (comm && t < kPart) {
                 double s = 0.0;
@@ -217,21 +223,40 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
             }
         }
         if (kSums) {
-            // (A) sparse sums: warp per slice, lane per row (missing chunk and inter row)
+            // (A) sparse sums: warp per slice, lane per row (missing chunk and
+            // inter row); slices are taken in order by whichever warp is free.
+            // A slice's first inter vector, its gathers and its first two
+            // missing vectors are issued before any is used, and each missing
+            // vector is loaded two iterations ahead of its use
             const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
             const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
             const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
             const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
-            for (int s = warp; s < d.nsl; s += kWarps) {
+            for (int s = warp;;) {
+                if (s >= d.nsl) break;
                 const uint4 sd = __ldg(sdesc + s);
                 const uint32_t rows = __ldg(srows + s * 32 + lane);
                 const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
+                const int4 *iv = ivec + sd.z + lane;
+                const uint4 *mv = mvec + sd.x + lane;
+                const int4 none = make_int4(a.n, a.n, a.n, a.n);
+                int4 qi = sd.w > 0 ? __ldg(iv) : none;
+                uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
+                if (sd.y > 0) q0 = __ldg(mv);
+                if (sd.y > 1) q1 = __ldg(mv + 32);
+                float4 g[4];
+                {
+                    const int l4[4] = {qi.x, qi.y, qi.z, qi.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) g[e] = l4[e] < a.n ? __ldg(a.y_in + l4[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 float mx = 0.f, my = 0.f, ix = 0.f, iy = 0.f;
                 {
                     const float4 own = yrow[mrow != 0xffffu ? chunk_row[mrow] : 0];
-                    const uint4 *mv = mvec + sd.x + lane;
                     for (uint32_t j = 0; j < sd.y; ++j) {
-                        const uint4 q = __ldg(mv + 32 * j);
+                        const uint4 q = q0;
+                        q0 = q1;
+                        if (j + 2 < sd.y) q1 = __ldg(mv + 32 * (j + 2));
                         const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
@@ -243,17 +268,25 @@ __global__ void __launch_bounds__(kThreads) cs_stage_kernel(const CsParams a) {
                 }
                 {
                     const float4 own = yrow[irow != 0xffffu ? irow : 0];
-                    const int4 *iv = ivec + sd.z + lane;
                     for (uint32_t j = 0; j < sd.w; ++j) {
-                        const int4 q = __ldg(iv + 32 * j);
-                        const int l4[4] = {q.x, q.y, q.z, q.w};
+                        if (j > 0) {
+                            qi = __ldg(iv + 32 * j);
+                            const int l4[4] = {qi.x, qi.y, qi.z, qi.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                g[e] = l4[e] < a.n ? __ldg(a.y_in + l4[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        const int l4[4] = {qi.x, qi.y, qi.z, qi.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            if (l4[e] < a.n) pair_term(a, own, __ldg(a.y_in + l4[e]), ix, iy);
+                            if (l4[e] < a.n) pair_term(a, own, g[e], ix, iy);
                     }
                 }
                 if (mrow != 0xffffu) sWm[mrow] = make_float2(mx, my);
                 if (irow != 0xffffu) sWi[irow] = make_float2(ix, iy);
+                int nx = 0;
+                if (lane == 0) nx = atomicAdd(&s_next, 1);
+                s = __shfl_sync(0xffffffffu, nx, 0);
             }
             __syncthreads();
             // (B) dense term, derivative, RK4 update: thread per row

@@ -32,6 +32,15 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+#ifndef CIA_WINDOW_VECTORS_P2
+#define CIA_WINDOW_VECTORS_P2 1    // the same for two harmonics (higher-order model)
+#endif
+#ifndef CIA_WINDOW_INTER_VECTORS
+#define CIA_WINDOW_INTER_VECTORS 2 // inter-link index vectors of a slice whose gathers fly together (<= 4)
+#endif
+#ifndef CIA_WINDOW_LATE_INPUTS
+#define CIA_WINDOW_LATE_INPUTS 1   // window kernel: load Phase B's node inputs after Phase A
+#endif
 #ifndef CIA_WINDOW_MIN_BLOCKS
 #define CIA_WINDOW_MIN_BLOCKS 4    // resident CTAs per SM the window kernel's registers are sized for
 #endif
@@ -424,14 +433,18 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
             bulk_g2s(win + (size_t)k * a.ph_region, a.ph_in + k * stride + (d.lo - d.shift), bytes, &wbar);
     }
     if (dense) community_observable<T, P>(a, d.comm, zc);
-    // node inputs of Phase B, loaded while the copy is in flight
+    // node inputs of Phase B: loaded while the copy is in flight, or (with
+    // CIA_WINDOW_LATE_INPUTS) brought into L2 now and loaded after Phase A,
+    // which keeps them out of Phase A's registers
     const int r = threadIdx.x;
     const int64_t m = d.first + r;
     const bool live = r < d.count;
     double theta_m = 0.0, wdt64_m = 0.0;
     T acc_m = T(0), wdt_m = T(0), omega_m = T(0);
     int32_t perm_m = 0;
-    if (live) {
+    const unsigned char *b = a.blob + d.blob_off;
+    uint32_t vt = 0u;
+    auto load_inputs = [&]() {
         if (MODE == kRhs) {
             omega_m = a.omega[m];
             perm_m = a.perm[m];
@@ -441,13 +454,22 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
             if (MODE == kStage) wdt_m = a.wdt_next[m];
             else wdt64_m = a.wdt64[m];
         }
+        vt = __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r);
+    };
+#if CIA_WINDOW_LATE_INPUTS
+    if (live && MODE != kRhs) {
+        prefetch_l2(a.theta + m);
+        if (!a.first_stage) prefetch_l2(a.acc + m);
+        if (MODE == kStage) prefetch_l2(a.wdt_next + m);
+        else prefetch_l2(a.wdt64 + m);
     }
-    const unsigned char *b = a.blob + d.blob_off;
+#else
+    if (live) load_inputs();
+#endif
     const uint4 *sdesc = reinterpret_cast<const uint4 *>(b);
     const uint32_t *srows = reinterpret_cast<const uint32_t *>(b + 16 * d.nsl);
     const uint4 *mvec = reinterpret_cast<const uint4 *>(b + d.mvec_off);
     const int4 *ivec = reinterpret_cast<const int4 *>(b + d.ivec_off);
-    const uint32_t vt = live ? __ldg(reinterpret_cast<const uint32_t *>(b + d.vtab_off) + r) : 0u;
     __syncthreads();   // the barrier's initialisation is visible to every waiter
     bool ok = true;
     if (dense) {
@@ -485,8 +507,8 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
         // of them is used: inter-community vectors, then the first missing
         // vectors; the inter gathers (global memory, longest latency) follow,
         // and the missing links (shared memory) are summed while they fly
-        constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;
-        constexpr uint32_t kMv = (P == 1 && sizeof(T) == 4) ? CIA_WINDOW_VECTORS : 1;   // vectors loaded ahead
+        constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? CIA_WINDOW_INTER_VECTORS : 1;
+        constexpr uint32_t kMv = sizeof(T) != 4 ? 1 : P == 1 ? CIA_WINDOW_VECTORS : P == 2 ? CIA_WINDOW_VECTORS_P2 : 1;   // vectors loaded ahead
         int4 qi[kPre];
         uint4 qm[kMv];
 #pragma unroll
@@ -562,6 +584,9 @@ __global__ void __launch_bounds__(kThreads, CIA_WINDOW_MIN_BLOCKS) cia_window_ke
     T sre[P], sim[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) sre[k] = sim[k] = T(0);
+#if CIA_WINDOW_LATE_INPUTS
+    if (live) load_inputs();
+#endif
     if (live) {
         T coup = T(0);
         C uk[P];
@@ -880,7 +905,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) cia_ring_kernel(const StagePa
             for (int kk = 0; kk < P; ++kk) macc[kk] = iacc[kk] = mk2(T(0), T(0));
             const int4 *iv = ivec + sdv.z + lane;
             const uint4 *mv = mvec + sdv.x + lane;
-            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? 2 : 1;
+            constexpr uint32_t kPre = (P == 1 && sizeof(T) == 4) ? CIA_WINDOW_INTER_VECTORS : 1;
             for (uint32_t j0 = 0; j0 < sdv.w || j0 == 0; j0 += kPre) {
                 C pre[kPre][4][P];
 #pragma unroll
