@@ -112,6 +112,7 @@ struct DeviceBuffers {
     int32_t *cs_check_comm = nullptr;         // their communities
     double *cs_check_out = nullptr;           // [check_count][2] error, reference
     float2 *cs_cen = nullptr;                 // [M] community centroids (pair sampling)
+    float2 *cs_shift = nullptr;               // [M] shift of phi's input during one RK4 step
     // general couplings (FP64 stage states and tile feature sums)
     double *gc_y[2] = {nullptr, nullptr};     // [n+1] stage states
     double *gc_part[2] = {nullptr, nullptr};  // [T][K] sums of the (beta-weighted) features per tile

@@ -15,22 +15,28 @@
 // The diagonal l = m of the dense block contributes phi(m).phi(m) (v_m - v_m)
 // = 0, so it needs no correction.
 //
-// Two launches per RK4 stage, both persistent CTAs of 256 threads walking
-// tiles of at most 128 nodes of one community:
+// CTAs of 256 threads walk tiles of at most 128 nodes of one community:
 //  - the feature launch (kLoad) stages the community's positions to get its
-//    centroid and evaluates phi on the tile (layer 2 on the tensor cores),
-//    storing the BF16 features and the tile's partial sums of phi, phi v_x,
-//    phi v_y;
+//    centroid c and evaluates phi(s - c) on the tile (layer 2 on the tensor
+//    cores), storing the BF16 features, the tile's partial sums of phi,
+//    phi v_x, phi v_y, and c as the community's shift;
 //  - the stage launch (0) reduces the community's tile partial sums into
 //    U_c, H_c and stages the community's state in shared memory, (A) sums the
 //    sparse links (missing links from shared memory, inter-community links
-//    from global memory) in the sliced-ELL layout of the plan and (B) adds the
+//    from global memory) in the sliced-ELL layout of the plan, (B) adds the
 //    dense term from each node's stored features and applies the RK4 stage
-//    update.
-// Because the centroid is that of the state being evaluated, the CIA
-// right-hand side is a function of the state alone.  The features are
-// rounded to BF16 once and the same values enter the moments and the dense
-// term, so the approximate pair weight is exactly symmetric.
+//    update and, in stages 1-3, (C) evaluates the features and moment partial
+//    sums of the next stage state it has just written, with the recorded
+//    shift.
+// One RK4 step is thus four stage launches and one feature launch (after
+// stage 4, for the new state).  All four stages of a step evaluate phi with
+// the centroid of the step's initial state as the shift; any shift common to
+// a community leaves every difference s_l - s_m unchanged, and this one moves
+// the inputs by O(dt |v|) from the stage state's own centroid.  The right-hand
+// side at a state that starts a step (cia_rhs, the sampled check, the state
+// after a resume) uses that state's own centroid.  The features are rounded
+// to BF16 once and the same values enter the moments and the dense term, so
+// the approximate pair weight is exactly symmetric.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -49,7 +55,9 @@ constexpr int kTileMax = 128;          // rows of a tile = MMA M
 constexpr int kMaxChunks = 512;        // missing-list chunks per tile (plan limit)
 constexpr int kPart = 3 * CIA_BASIS_RANK;   // U, H_x, H_y per tile
 constexpr int kRank = CIA_BASIS_RANK;
-constexpr int kFs = kRank + 1;               // padded row stride of the shared feature tile
+constexpr int kFw = kRank / 2;               // 32-bit words (BF16 pairs) of a feature-tile row
+constexpr size_t kFeatTileBytes = (size_t)kTileMax * kFw * 4;   // phase C feature tile
+constexpr size_t kRedBytes = 4 * (size_t)3 * kRank * 4;        // phase C moment partials [4][kPart]
 
 enum CsMode { kRhs = 0, kStage = 1, kFinal = 2, kLoad = 3 };
 
@@ -72,6 +80,8 @@ struct CsParams {
     const float4 *y_in;        // [n] stage state (s_x, s_y, v_x, v_y), permuted
     float4 *y_out;             // [n] next stage state
     const double *part_in;     // [tiles][kPart] moment partial sums of y_in's features
+    float2 *shift;             // [M] shift of phi's input: written by the feature launch,
+                               // read by the fused stage launches of the same RK4 step
     double *part_out;          // [tiles][kPart] of y_out's features
     __nv_bfloat16 *feat;       // [n][kRank] features of y_in on entry, of y_out on exit
     const float *params;       // basis parameters (FP32 master, rounded to BF16 on load)
@@ -135,20 +145,23 @@ __device__ __forceinline__ float4 rk4_update(const CsParams &a, int64_t m, float
     return y;
 }
 
+#ifndef CIA_CS_FUSED
+#define CIA_CS_FUSED 1        // stages 1-3 evaluate the next state's features in their epilogue
+#endif
 #ifndef CIA_CS_MIN_BLOCKS
 #define CIA_CS_MIN_BLOCKS 4   // resident CTAs per SM the stage launches' registers are sized for
 #endif
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(const CsParams a) {
-    constexpr bool kFeatures = MODE == kLoad;  // phi of the state and its moment partial sums
-    constexpr bool kSums = MODE != kLoad;      // the right-hand side and the stage update
+    constexpr bool kFused = CIA_CS_FUSED && MODE == kStage;   // features of the next stage state
+    constexpr bool kFeatures = MODE == kLoad || kFused;      // phi and its moment partial sums
+    constexpr bool kSums = MODE != kLoad;                    // the right-hand side and the stage update
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
     __shared__ float4 yrow[kTileMax];          // stage state of the tile's rows, then the next one
     __shared__ float mom[kPart];               // U_c, H_cx, H_cy (with the 1/N)
-    __shared__ float red[4][kPart];
     __shared__ float cred[kWarps][2];
     __shared__ float2 cen;
     __shared__ int s_next;                     // next slice of the tile to take
@@ -160,7 +173,11 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
     float2 *sWi = sWm + kMaxChunks;                                    // inter sums per row
     uint16_t *chunk_row = reinterpret_cast<uint16_t *>(sWi + kTileMax);
     __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(region);      // phase C: layer-2 operand
-    float *F = reinterpret_cast<float *>(region);                      // phase C: features [128][kFs]
+    // phase C: the tile's BF16 features, row r's word j (features 2j, 2j + 1)
+    // at r * kFw + (j ^ (r & 31)), so that a warp's rows or a warp's
+    // features hit distinct banks; then the moment partials
+    uint32_t *F = reinterpret_cast<uint32_t *>(region);
+    float(*red)[kPart] = reinterpret_cast<float(*)[kPart]>(region + kFeatTileBytes);
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, r = t & 127, h = t >> 7;
     uint32_t tmem = 0;
@@ -182,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
         const int tile = a.tile_order ? a.tile_order[k] : k;   // costliest tiles first
         const TileDesc d = a.tile_desc[tile];
         const bool comm = d.comm >= 0;
-        if (kFeatures && !comm) continue;   // nodes without a community have no dense term
+        if (MODE == kLoad && !comm) continue;   // nodes without a community have no dense term
         const int lam = comm ? (int)d.lam : 0;
         const int count = d.count;
         const unsigned char *b = a.blob + d.blob_off;
@@ -191,6 +208,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
         for (int i = t; i < lam; i += kThreads) win[i] = a.y_in[d.lo + i];
         if (t < count) yrow[t] = a.y_in[d.first + t];
         if (t == 0) s_next = kWarps;   // the previous tile's slices ended at its last barrier
+        if (kFused && comm && t == 0) cen = a.shift[d.comm];
         if (kSums) {
             if (comm && t < kPart) {
                 double s = 0.0;
@@ -204,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
             }
         }
         __syncthreads();
-        if (kFeatures && comm) {
+        if (MODE == kLoad && comm) {
             // centroid of the community's positions in this state (the shift
             // of phi's input); a fixed reduction order, identical in every
             // tile of the community
@@ -325,16 +343,20 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
         }
         __syncthreads();
         if (kFeatures && comm) {
-            if (t == 0) {
+            if (MODE == kLoad && t == 0) {
                 float sx = 0.f, sy = 0.f;
                 for (int i = 0; i < kWarps; ++i) {
                     sx += cred[i][0];
                     sy += cred[i][1];
                 }
                 cen = make_float2(sx / (float)lam, sy / (float)lam);
+                // the shift of the fused stages that follow, recorded by the
+                // community's first tile (every tile computes the same value)
+                if (tile == a.comm_tile_begin[d.comm]) a.shift[d.comm] = cen;
             }
             __syncthreads();
-            // (C) features of the next stage state and their tile partial sums
+            // (C) features of this state (feature launch) or of the next
+            // stage state (fused stage launch) and their tile partial sums
             const bool valid = r < count;
             const float4 yn = valid ? yrow[r] : make_float4(0.f, 0.f, 0.f, 0.f);
             mlp::hidden_to_smem(w, yn.x - cen.x, yn.y - cen.y, r, h, valid, A);
@@ -356,8 +378,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
             for (int e = 0; e < 16; ++e) {
                 __nv_bfloat162 v = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
                 pk[e] = *reinterpret_cast<uint32_t *>(&v);
-                F[r * kFs + 32 * h + 2 * e] = bf16_lo(pk[e]);
-                F[r * kFs + 32 * h + 2 * e + 1] = bf16_hi(pk[e]);
+                F[r * kFw + ((16 * h + e) ^ (r & 31))] = pk[e];
             }
             if (valid) {
                 uint4 *dst = reinterpret_cast<uint4 *>(a.feat + (d.first + r) * kRank + 32 * h);
@@ -371,7 +392,8 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
                 float su = 0.f, hx = 0.f, hy = 0.f;
                 const int i1 = min(32 * q4 + 32, count);
                 for (int i = 32 * q4; i < i1; ++i) {
-                    const float v = F[i * kFs + fr];
+                    const uint32_t wv = F[i * kFw + ((fr >> 1) ^ (i & 31))];
+                    const float v = (fr & 1) ? bf16_hi(wv) : bf16_lo(wv);
                     su += v;
                     hx = fmaf(v, yrow[i].z, hx);
                     hy = fmaf(v, yrow[i].w, hy);
@@ -609,6 +631,7 @@ CsParams base_params(const cia_plan *pl, int slot) {
     a.y_out = d.cs_y[slot ^ 1];
     a.part_in = d.cs_part[slot];
     a.part_out = d.cs_part[slot ^ 1];
+    a.shift = d.cs_shift;
     a.feat = static_cast<__nv_bfloat16 *>(d.cs_feat);
     a.params = d.cs_params;
     a.acc = d.cs_acc;
@@ -619,27 +642,33 @@ CsParams base_params(const cia_plan *pl, int slot) {
     return a;
 }
 
-// Dynamic shared memory of the stage launches (features = false) and of the
-// feature launch.
-size_t stage_smem(const cia_plan *pl, bool features) {
+// Dynamic shared memory of a launch: the weights (feature launch and fused
+// stages), then one region holding the community window and the sparse-sum
+// tables (stage launches) and, reused, the layer-2 operand or the feature tile.
+size_t stage_smem(const cia_plan *pl, bool features, bool sums) {
     const size_t win = align_up((size_t)pl->max_comm * sizeof(float4), 16);
-    if (features)
-        return kWeightsBytes + std::max({win, (size_t)kTileMax * CIA_BASIS_HIDDEN * 2, (size_t)kTileMax * kFs * 4});
-    return win + kMaxChunks * sizeof(float2) + kTileMax * sizeof(float2) + kMaxChunks * 2;
+    const size_t tables = sums ? kMaxChunks * sizeof(float2) + kTileMax * sizeof(float2) + kMaxChunks * 2 : 0;
+    const size_t mlp = features ? std::max((size_t)kTileMax * CIA_BASIS_HIDDEN * 2, kFeatTileBytes + kRedBytes) : 0;
+    return (features ? kWeightsBytes : 0) + std::max(win + tables, mlp);
 }
 
 template <int MODE>
+constexpr bool fused_stage() { return CIA_CS_FUSED && MODE == kStage; }
+
+template <int MODE>
 cudaError_t launch_stage_t(const cia_plan *pl, const CsParams &a, cudaStream_t s) {
-    const size_t smem = stage_smem(pl, MODE == kLoad);
+    constexpr bool features = MODE == kLoad || fused_stage<MODE>();
+    const size_t smem = stage_smem(pl, features, MODE != kLoad);
     cudaError_t e = ensure_dynamic_smem((const void *)cs_stage_kernel<MODE>, pl->device, smem);
     if (e != cudaSuccess) return e;
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cs_stage_kernel<MODE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     bps = std::max(1, std::min(bps, 8));   // at most 8 x 64 tensor-memory columns per SM
-    // the feature launch keeps one resident CTA per slot (it loads the weights
-    // and allocates tensor memory once); the stage launches take one CTA per
-    // tile and let the hardware start the next tile wherever a slot frees up
+    // the feature launch keeps one resident CTA per slot (each loads the
+    // weights and allocates tensor memory once); the stage launches take one
+    // CTA per tile and let the hardware start the next tile wherever a slot
+    // frees up
     const int64_t grid = MODE == kLoad ? std::min<int64_t>(pl->n_tiles, (int64_t)bps * pl->n_sms) : pl->n_tiles;
     void *args[] = {const_cast<CsParams *>(&a)};
     return cudaLaunchKernel((const void *)cs_stage_kernel<MODE>, dim3((unsigned)std::max<int64_t>(grid, 1)),
@@ -658,7 +687,9 @@ unsigned grid_1d(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int
 
 }  // namespace
 
-size_t cs_stage_smem_bytes(const cia_plan *pl) { return std::max(stage_smem(pl, false), stage_smem(pl, true)); }
+size_t cs_stage_smem_bytes(const cia_plan *pl) {
+    return std::max({stage_smem(pl, false, true), stage_smem(pl, true, false), stage_smem(pl, true, true)});
+}
 
 cudaError_t cs_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
     cs_load_kernel<<<grid_1d(pl->n), 256, 0, s>>>(pl->n, pl->d.perm, x, write_master ? pl->d.cs_master : nullptr,
@@ -691,7 +722,10 @@ cudaError_t cs_launch_stage(cia_plan *pl, int method, int stage, int slot, doubl
         return stage == 4 ? launch_direct_t<kFinal>(pl, a, s) : launch_direct_t<kStage>(pl, a, s);
     cudaError_t e = stage == 4 ? launch_stage_t<kFinal>(pl, a, s) : launch_stage_t<kStage>(pl, a, s);
     if (e != cudaSuccess) return e;
-    // features and moments of the state just written, for the next stage
+    // the fused stages 1-3 wrote the next stage state's features (with the
+    // shift of this RK4 step); after stage 4 the feature launch evaluates
+    // them with the new state's own centroid, the shift of the next step
+    if (stage < 4 && fused_stage<kStage>()) return cudaSuccess;
     return cs_launch_features(pl, slot ^ 1, s);
 }
 

@@ -889,6 +889,8 @@ static cia_status upload_split(cia_plan *pl, const cia_options *opt, const doubl
         if ((s2 = upload<float>(pl, &d.cs_params, nullptr, CIA_BASIS_PARAMS)) != CIA_OK) return s2;
         if ((s2 = alloc_bytes(pl, (void **)&d.cs_cen, (size_t)std::max<int64_t>(M, 1) * sizeof(float2))) != CIA_OK)
             return s2;
+        if ((s2 = alloc_bytes(pl, (void **)&d.cs_shift, (size_t)std::max<int64_t>(M, 1) * sizeof(float2))) != CIA_OK)
+            return s2;
         // nodes of the learned-basis check: evenly spaced over the community nodes
         const int64_t nc = pl->off[M];
         pl->cs_check_count = std::min<int64_t>(512, nc);
