@@ -169,21 +169,22 @@ def job_throughput(units_per_rank: float, steps: int, world: int, max_seconds: f
     return world * units_per_rank * steps / max_seconds
 
 
-def stage_bytes(info: dict, precision: str) -> float:
+def stage_bytes(info: dict, precision: str, harmonics: int = 1) -> float:
     """Algorithmic (compulsory) bytes of one CIA stage launch, averaged over
     the four RK4 stages.
 
-    Per node: its stage phasor read once (8 B; every gather of it, from the
-    shared-memory community window or from L2, reuses that read), the FP64
-    master (8 B), the next-stage frequency constant (4 B), the stage
-    accumulator read in 3 of 4 stages (3 B on average) and written (4 B), the
-    next phasor written (8 B); the final stage also writes the master and
-    reads wrap(dt omega) in FP64 (+12 B, i.e. +3 B on average): 38 B.
+    Per node: its stage phasors read once (8 B per harmonic; every gather of
+    them, from the shared-memory community window or from L2, reuses that
+    read), the FP64 master (8 B), the next-stage frequency constant (4 B),
+    the stage accumulator read in 3 of 4 stages (3 B on average) and written
+    (4 B), the next phasors written (8 B per harmonic); the final stage also
+    writes the master and reads wrap(dt omega) in FP64 (+12 B, i.e. +3 B on
+    average): 38 B with one harmonic (FP32).
     Per missing link: its 16-bit community-local index (2 B).
     Per inter-community link: its 32-bit index (4 B).
     """
     rb = 4 if precision == "fp32" else 8
-    c = 2 * rb
+    c = 2 * rb * harmonics
     per_node = c + 8 + rb + 0.75 * rb + rb + c + 0.25 * (8 + 8 - rb)
     return (info["n"] * per_node + info["nnz_missing"] * info["missing_index_bytes"]
             + info["nnz_inter"] * 4)
@@ -322,17 +323,18 @@ CS_WORKLOAD = ("cucker_smale: N=131072, 128 communities of 1024, p_in=0.9, inter
 
 
 def cs_stage_bytes(info: dict) -> float:
-    """Algorithmic bytes of one CIA stage of the Cucker--Smale model (the stage
-    launch plus the feature launch), averaged over the four RK4 stages.
+    """Algorithmic bytes of one CIA stage of the Cucker--Smale model (stages
+    1-3 evaluate the next state's features themselves; stage 4 is followed by
+    the feature launch), averaged over the four RK4 stages.
 
     Per node: stage state read (16 B, gathers reuse it), next state written
-    (16 B) and read again by the feature launch (16 B), FP64 master read
-    (32 B; written in the final stage: +8 B on average), accumulator read in
-    3 of 4 stages and written (12 + 16 B), BF16 features read and written
-    (2 x 128 B).  Per missing link a 16-bit index, per inter link a 32-bit
-    index.
+    (16 B) and, after stage 4, read again by the feature launch (+4 B on
+    average), FP64 master read (32 B; written in the final stage: +8 B on
+    average), accumulator read in 3 of 4 stages and written (12 + 16 B), BF16
+    features read and written (2 x 128 B).  Per missing link a 16-bit index,
+    per inter link a 32-bit index.
     """
-    per_node = 16 + 16 + 16 + 32 + 8 + 12 + 16 + 256
+    per_node = 16 + 16 + 4 + 32 + 8 + 12 + 16 + 256
     return info["n"] * per_node + info["nnz_missing"] * 2 + info["nnz_inter"] * 4
 
 
@@ -388,7 +390,8 @@ def cs_leg(args, torch, cia, flush) -> dict:
         "workload": CS_WORKLOAD, "n": g.n, "nnz_graph": info["nnz_graph"],
         "nnz_missing": info["nnz_missing"], "nnz_inter": info["nnz_inter"], "steps": steps,
         "cia": {"value": g.n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
-                "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9},
+                "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
+                "stage_hbm_frac": sb / (stage_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"]},
         "direct": {"value": g.n * steps / (dtotal / 1e3), "unit": UNIT, "ms_per_step": dtotal / steps},
         "speedup_cia_over_direct": dtotal / max(total, 1e-12),
         "error_vs_fp64_oracle": {"cia_rhs_velocity_rel": errs["cia"],
@@ -588,7 +591,9 @@ def poly_leg(args, torch, cia, flush) -> dict:
             "steps": steps, "features_per_node": info_features(name),
             "cia": {"value": g.n * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
                     "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
-                    "staging": {1: "plain loads", 2: "shared-memory community window"}[info["staging"]]},
+                    "stage_hbm_frac": sb / (stage_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
+                    "staging": {1: "plain loads",
+                                2: "shared-memory community windows, one launch per community-size run"}[info["staging"]]},
             "direct": {"value": g.n * steps / (dtotal / 1e3), "unit": UNIT, "ms_per_step": dtotal / steps},
             "speedup_cia_over_direct": dtotal / max(total, 1e-12),
             "error_vs_fp64_oracle": {"cia_rhs_rel": rhs_err["cia"], "direct_rhs_rel": rhs_err["direct"],
@@ -709,13 +714,19 @@ def small_configs_leg(args, torch, cia, flush) -> dict:
         got = plan.rhs(x0, method=m).cpu().numpy()[nodes]
         err[m] = coupling_rel_err(got, ref, w.omega[nodes])
     steps, dsteps = 10, 2
-    t_cia = _time_method(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush)
+    ms, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
+    t_cia = float(sum(ms))
     t_dir = _time_method(torch, plan, x0, w.dt, dsteps, 1, "direct", flush)
+    stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    sb = stage_bytes(plan.info(), "fp32", harmonics=2)
     out["kuramoto_ho"] = {
         "workload": "N=65536, 64x1024 SBM p_in 0.9, inter degree 4, pairwise K1=1 + triadic K2=2 on "
                     "community hyperedges, RK4 dt 0.005, FP32 + FP64 accumulation (L2 flushed between steps)",
         "steps": steps,
-        "cia": {"value": g.n * steps / (t_cia / 1e3), "unit": UNIT, "ms_per_step": t_cia / steps},
+        "cia": {"value": g.n * steps / (t_cia / 1e3), "unit": UNIT, "ms_per_step": t_cia / steps,
+                "stage_ms": stage_ms, "stage_gbs_algorithmic": sb / (stage_ms * 1e-3) / 1e9,
+                "stage_hbm_frac": sb / (stage_ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
+                "note": "65536 nodes fill one wave of CTAs: the stage is bound by one tile's latency"},
         "direct": {"value": g.n * dsteps / (t_dir / 1e3), "unit": UNIT, "ms_per_step": t_dir / dsteps,
                    "note": "triadic term summed pair by pair, O(lambda^2) per node"},
         "speedup_cia_over_direct": (t_dir / dsteps) / max(t_cia / steps, 1e-12),

@@ -435,7 +435,7 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
     }
     pl->gc_weighted = alpha || beta;
     // the window holds one more row when weighted; the moments change
-    pl->staging = (pl->staging_req == 1 || !gc_window_fits(pl)) ? 1 : 2;
+    pl->staging = pl->staging_req == 1 ? 1 : 2;
     pl->needs_load = true;
     invalidate_graphs(pl);
     return CIA_OK;

@@ -76,6 +76,7 @@ struct DeviceBuffers {
     // partial sums are added per row in chunk order.
     cia::TileDesc *tile_desc = nullptr; // [T]
     int32_t *tile_order = nullptr;      // [T] launch order of the per-tile kernels (costliest first)
+    int32_t *gc_tiles = nullptr;        // [T] general couplings: tiles by community size, largest first
     unsigned char *blob = nullptr;      // [sum of blob bytes]
     int32_t *cta_tile_begin = nullptr;  // [n_ctas+1] tile range of each persistent CTA
     int32_t *cta_runs = nullptr;        // [n_ctas] community runs (maximal same-community tile runs) per CTA
@@ -204,6 +205,10 @@ struct cia_plan {
     // general couplings (polynomial and Fourier; model CIA_MODEL_POLYNOMIAL internally)
     int poly_p = 0;                     // polynomial degree (1..4), or harmonics (Fourier)
     int smem_optin = 0;                 // opt-in shared memory per block of the device
+    int smem_per_sm = 0;                // shared memory per SM of the device
+    std::vector<int64_t> gc_tile_lam;   // community size of each tile in gc_tiles' order
+    cudaStream_t gc_side[4] = {};       // general couplings: streams of the concurrent window launches
+    cudaEvent_t gc_fork = nullptr, gc_join[4] = {};
     double poly_c[CIA_MAX_POLY + 1] = {0};  // difference form: h
     double poly_dv[CIA_MAX_POLY + 1] = {0}; // V'
     bool poly_general = false;          // g(x_l, x_m) instead of h(x_l - x_m)
@@ -274,6 +279,5 @@ size_t cs_stage_smem_bytes(const cia_plan *pl);
 cudaError_t gc_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s);
 cudaError_t gc_launch_rhs(cia_plan *pl, int method, int slot, double *dxdt, cudaStream_t s);
 cudaError_t gc_launch_stage(cia_plan *pl, int method, int stage, int slot, double dt, cudaStream_t s);
-bool gc_window_fits(const cia_plan *pl);
 
 }  // namespace cia

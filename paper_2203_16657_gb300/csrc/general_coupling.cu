@@ -29,7 +29,15 @@
 // computed once per node and stage (one sincos and the angle-addition
 // recurrence) and stored; polynomial features are computed where needed.
 //
-// One CTA (256 threads) per tile and launch: (0) the community's moments from
+// The window of a community of lambda nodes takes 8 lambda bytes per feature
+// row, so one large community would set every CTA's shared memory.  The
+// plan therefore sorts the tiles by community size; each stage launches one
+// kernel per run of tiles that fit the same number of resident CTAs per SM
+// (4, 3, 2, 1, with a window sized to the run's largest community; tiles of a
+// community that fits no window read its features from global memory), and
+// these launches run concurrently on forked streams.
+//
+// One CTA (256 threads) per tile: (0) the community's moments from
 // the previous launch's tile sums and its features in shared memory, (A) the
 // sparse feature sums over the tile's sliced-ELL blob, (B) one thread per
 // node: T_k, the coupling, RK4 stage update, the next state's features and the
@@ -68,6 +76,7 @@ struct GcParams {
                                  // community's features from global memory
     int diff;                    // direct method: h(u - y) instead of the separable form
     const TileDesc *tile_desc;
+    const int32_t *tile_list;    // the launch's tiles (window launches), or null: tile = CTA
     const unsigned char *blob;
     const int32_t *comm_tile_begin;
     const int64_t *full_rowptr;
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
     double *sWi = sWm + NR * kMaxChunks;                        // [NR][kTileMax] inter sums per row
     int *smc = reinterpret_cast<int *>(sWi + NR * kTileMax);    // [kMaxChunks] missing links per chunk
     int *sic = smc + kMaxChunks;                                // [kTileMax] inter links per row
-    const int t = blockIdx.x;
+    const int t = a.tile_list ? a.tile_list[blockIdx.x] : (int)blockIdx.x;
     const TileDesc d = a.tile_desc[t];
     const bool comm = d.comm >= 0;
     const int lam = comm ? (int)d.lam : 0;
@@ -496,22 +505,56 @@ __global__ void __launch_bounds__(kThreads) gc_load_kernel(const GcParams a, con
     next_features<B, K>(a, t, m, live, y, wnode, scratch);
 }
 
-size_t window_cap(const cia_plan *pl) { return (size_t)((pl->max_comm + 1) & ~(int64_t)1); }
-
 // Rows of the window and of the sparse sums: features 1..K-1, or 0..K-1 when weighted.
 int rows(const cia_plan *pl) { return pl->gc_k - 1 + (pl->gc_weighted ? 1 : 0); }
 
 size_t tables_bytes(int nr) { return (size_t)nr * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
 
-// The features of the largest community fit the shared-memory window (the
-// kernel's static shared memory is under 4 KB).
-bool window_fits(const cia_plan *pl) {
-    return window_cap(pl) * 8 * rows(pl) + tables_bytes(rows(pl)) + 4096 <= (size_t)pl->smem_optin;
+constexpr size_t kStaticReserve = 4096;   // the stage kernel's static shared memory (under 1 KB) and margin
+
+// The largest window (nodes, even) with which `per_sm` CTAs of the stage
+// kernel fit one SM; 0 if not even the tables do.
+int64_t window_cap_for(const cia_plan *pl, int per_sm) {
+    const size_t sm = pl->smem_per_sm > 0 ? (size_t)pl->smem_per_sm : (size_t)pl->smem_optin;
+    size_t per_cta = sm / (size_t)per_sm;
+    per_cta = per_cta > 1024 ? per_cta - 1024 : 0;   // the runtime reserves 1 KB per CTA
+    per_cta = std::min(per_cta, (size_t)pl->smem_optin);
+    const size_t fixed = tables_bytes(rows(pl)) + kStaticReserve;
+    if (per_cta <= fixed) return 0;
+    return (int64_t)((per_cta - fixed) / (8 * (size_t)rows(pl))) & ~(int64_t)1;
 }
 
-size_t stage_smem(const cia_plan *pl) {
-    return (pl->staging == 2 ? window_cap(pl) * 8 * rows(pl) : 0) + tables_bytes(rows(pl));
+// A window launch over a run of tiles: their community windows need at most
+// `cap` nodes (0: the run reads features from global memory).
+struct Run {
+    int64_t begin, end, cap;
+};
+
+// Runs of the size-sorted tile list: each tile goes to the launch with the
+// most resident CTAs per SM (4, 3, 2, 1) whose window holds its community;
+// tiles of communities no window holds read from global memory.
+std::vector<Run> window_runs(const cia_plan *pl) {
+    std::vector<Run> runs;
+    const auto &lam = pl->gc_tile_lam;
+    const int64_t T = (int64_t)lam.size();
+    int64_t caps[5];
+    for (int k = 1; k <= 4; ++k) caps[k] = window_cap_for(pl, k);
+    auto level = [&](int64_t l) {
+        for (int k = 4; k >= 1; --k)
+            if (l <= caps[k]) return k;
+        return 0;
+    };
+    for (int64_t i = 0; i < T;) {
+        const int k = level(lam[i]);
+        int64_t j = i + 1;
+        while (j < T && level(lam[j]) == k) ++j;
+        runs.push_back({i, j, k == 0 ? 0 : (lam[i] + 1) & ~(int64_t)1});
+        i = j;
+    }
+    return runs;
 }
+
+size_t stage_smem(const cia_plan *pl, int64_t cap) { return (size_t)cap * 8 * rows(pl) + tables_bytes(rows(pl)); }
 
 GcParams base_params(const cia_plan *pl, int slot) {
     GcParams a{};
@@ -527,8 +570,9 @@ GcParams base_params(const cia_plan *pl, int slot) {
     a.diff = pl->gc_basis == kPoly && !pl->poly_general;
     a.k_over_n = pl->K / (double)pl->n;
     a.group = pl->group_size_direct;
-    a.win_cap = pl->staging == 2 ? (int)window_cap(pl) : 0;
+    a.win_cap = 0;
     a.tile_desc = d.tile_desc;
+    a.tile_list = nullptr;
     a.blob = d.blob;
     a.comm_tile_begin = d.comm_tile_begin;
     a.full_rowptr = d.full_rowptr;
@@ -555,6 +599,38 @@ cudaError_t launch(void (*kernel)(GcParams), const cia_plan *pl, size_t smem, co
     return cudaLaunchKernel((const void *)kernel, dim3((unsigned)pl->n_tiles), dim3(kThreads), args, smem, s);
 }
 
+// The CIA stage kernel: one launch over all tiles with plain loads (staging
+// 1), or one launch per run of the size-sorted tiles, each with a window for
+// its largest community (staging 2).  The runs' tiles are disjoint, so their
+// launches run concurrently: the first on the caller's stream, the others on
+// side streams that fork from it and join it again, so that CTAs of every
+// run share the SMs instead of each run's last wave idling them.
+cudaError_t launch_cia(void (*kernel)(GcParams), const cia_plan *pl, const GcParams &a0, cudaStream_t s) {
+    if (pl->staging != 2) return launch(kernel, pl, stage_smem(pl, 0), a0, s);
+    const std::vector<Run> runs = window_runs(pl);
+    if (runs.size() > 5) return cudaErrorInvalidValue;   // at most one run per level (0, 1, 2, 3, 4)
+    cudaError_t e = cudaSuccess;
+    if (runs.size() > 1 && (e = cudaEventRecord(pl->gc_fork, s)) != cudaSuccess) return e;
+    for (size_t i = 0; i < runs.size(); ++i) {
+        const Run &run = runs[i];
+        cudaStream_t rs = i == 0 ? s : pl->gc_side[i - 1];
+        if (i > 0 && (e = cudaStreamWaitEvent(rs, pl->gc_fork, 0)) != cudaSuccess) return e;
+        GcParams a = a0;
+        a.win_cap = (int)run.cap;
+        a.tile_list = pl->d.gc_tiles + run.begin;
+        const size_t smem = stage_smem(pl, run.cap);
+        if ((e = ensure_dynamic_smem((const void *)kernel, pl->device, smem)) != cudaSuccess) return e;
+        void *args[] = {&a};
+        e = cudaLaunchKernel((const void *)kernel, dim3((unsigned)(run.end - run.begin)), dim3(kThreads), args, smem, rs);
+        if (e != cudaSuccess) return e;
+        if (i > 0) {
+            if ((e = cudaEventRecord(pl->gc_join[i - 1], rs)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, pl->gc_join[i - 1], 0)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 template <int MODE, int B, int K>
 cudaError_t launch_shape(const cia_plan *pl, int method, const GcParams &a, cudaStream_t s) {
     if (method == Method::DIRECT) {
@@ -563,8 +639,8 @@ cudaError_t launch_shape(const cia_plan *pl, int method, const GcParams &a, cuda
         return launch(gc_direct_kernel<MODE, B, K, false>, pl, 0, a, s);
     }
     if constexpr (B == kPoly)
-        if (pl->gc_weighted) return launch(gc_stage_kernel<MODE, B, K, true>, pl, stage_smem(pl), a, s);
-    return launch(gc_stage_kernel<MODE, B, K, false>, pl, stage_smem(pl), a, s);
+        if (pl->gc_weighted) return launch_cia(gc_stage_kernel<MODE, B, K, true>, pl, a, s);
+    return launch_cia(gc_stage_kernel<MODE, B, K, false>, pl, a, s);
 }
 
 template <int MODE>
@@ -592,7 +668,6 @@ void launch_load(const cia_plan *pl, const GcParams &a, const double *x, double 
 
 }  // namespace
 
-bool gc_window_fits(const cia_plan *pl) { return window_fits(pl); }
 
 cudaError_t gc_launch_load(cia_plan *pl, const double *x, bool write_master, int slot, cudaStream_t s) {
     // the load writes the state, its features and their sums into slot `slot`

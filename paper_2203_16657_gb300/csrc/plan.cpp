@@ -109,6 +109,14 @@ static void free_all(cia_plan *pl) {
     invalidate_graphs(pl);
     if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
     pl->capture_stream = nullptr;
+    for (int i = 0; i < 4; ++i) {
+        if (pl->gc_side[i]) cudaStreamDestroy(pl->gc_side[i]);
+        if (pl->gc_join[i]) cudaEventDestroy(pl->gc_join[i]);
+        pl->gc_side[i] = nullptr;
+        pl->gc_join[i] = nullptr;
+    }
+    if (pl->gc_fork) cudaEventDestroy(pl->gc_fork);
+    pl->gc_fork = nullptr;
     for (void *p : pl->allocations) cudaFree(p);
     pl->allocations.clear();
     for (void *p : pl->tile_allocs) cudaFree(p);
@@ -875,6 +883,7 @@ static cia_status upload_split(cia_plan *pl, const cia_options *opt, const doubl
     cia_status s2;
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->n_sms, cudaDevAttrMultiProcessorCount, pl->device));
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+    CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, pl->device));
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
@@ -1168,8 +1177,26 @@ static cia_status build_tiles(cia_plan *pl) {
     }
     if (pl->model == CIA_MODEL_POLYNOMIAL) {
         // its own one-CTA-per-tile kernel: community window in shared memory
-        // (auto, window, pipeline) or plain loads (plain, or when it does not fit)
-        pl->staging = (pl->staging == 1 || !gc_window_fits(pl)) ? 1 : 2;
+        // (auto, window, pipeline) or plain loads (plain); the window launches
+        // take the tiles by community size, largest first, so that each run
+        // of tiles gets a window sized to its largest community
+        pl->staging = pl->staging == 1 ? 1 : 2;
+        std::vector<int32_t> order(T);
+        for (int64_t t = 0; t < T; ++t) order[t] = (int32_t)t;
+        auto lam_of = [&](int32_t t) { return tdesc[t].comm >= 0 ? (int64_t)tdesc[t].lam : (int64_t)0; };
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return lam_of(x) > lam_of(y); });
+        pl->gc_tile_lam.resize(T);
+        for (int64_t i = 0; i < T; ++i) pl->gc_tile_lam[i] = lam_of(order[i]);
+        UPT(d.gc_tiles, order.data(), order.size());
+        // the runs' launches fork from the caller's stream and join it again
+        // (created here, outside any graph capture)
+        if (!pl->gc_fork) {
+            CIA_CUDA_TRY(cudaEventCreateWithFlags(&pl->gc_fork, cudaEventDisableTiming));
+            for (int i = 0; i < 4; ++i) {
+                CIA_CUDA_TRY(cudaStreamCreateWithFlags(&pl->gc_side[i], cudaStreamNonBlocking));
+                CIA_CUDA_TRY(cudaEventCreateWithFlags(&pl->gc_join[i], cudaEventDisableTiming));
+            }
+        }
     }
     if (pl->model == CIA_MODEL_CUCKER_SMALE || pl->model == CIA_MODEL_POLYNOMIAL) {
         UPT(d.tile_desc, tdesc.data(), tdesc.size());

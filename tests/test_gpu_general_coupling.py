@@ -453,6 +453,35 @@ def test_fourier_rhs_harmonics(cia, oracle_mod, torch_mod, p, staging):
         assert fourier_err(oracle_mod, g, x, got, ref, L, C, dv) < FP64_TOL, method
 
 
+def test_fourier_window_runs_by_community_size(cia, oracle_mod, torch_mod):
+    """Two harmonics (four window rows of 8 bytes per node): the tiles of the
+    6400-node community fit no window and read features from global memory,
+    the 2000-, 1000- and 500-node communities fit windows for 2, 3 and 4
+    resident CTAs, and the small community and the free nodes share the last
+    run.  Every run against the oracle, in one right-hand side and through
+    an RK4 step replayed as a CUDA graph."""
+    g = S.hash_sbm_graph([6400, 2000, 1000, 500, 100], 0.9, seed=61, inter_degree=4.0, n_free=37)
+    rng = np.random.default_rng(62)
+    C = [rng.normal(size=(3, 3)) for _ in range(4)]
+    dv = (0.1, -1.0, 0.0, 0.4)
+    L = 2.0
+    x = rng.uniform(-2.5, 2.5, g.n)
+    plan = make_fourier(cia, g, 1.1, L, C, dv)
+    assert plan.info()["staging"] == 2
+    ref = oracle_mod.fourierg_direct(g.rowptr, g.col, x, 1.1, L, C, dv)
+    got = gpu_rhs(torch_mod, plan, x, "cia")
+    assert fourier_err(oracle_mod, g, x, got, ref, L, C, dv) < FP64_TOL
+    dt = 0.01
+    rhs = lambda y: oracle_mod.fourierg_direct(g.rowptr, g.col, y, 1.1, L, C, dv)
+    want, _ = oracle_mod.integrate(rhs, x, dt, 2, wrap=False)
+    xd = torch_mod.from_numpy(x.copy()).cuda()
+    plan.state_load(xd)
+    plan.advance(dt, 1)
+    plan.advance(dt, 1)
+    plan.state_store(xd)
+    assert np.abs(xd.cpu().numpy() - want).max() < 1e-11 * np.abs(want).max()
+
+
 def test_fourier_sine_of_difference_matches_kuramoto_plan(cia, torch_mod):
     """sin(w(u - y)) through the general series equals the FP64 Kuramoto plan
     on the phases w x."""
