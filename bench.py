@@ -582,8 +582,9 @@ def poly_leg(args, torch, cia, flush) -> dict:
         # relative error includes the FP64 rounding of that sum (~1e-14 absolute)
         err = {m: coupling_rel_err(got[m], ref, pot) for m in got}
         rhs_err = {m: float(np.abs(got[m] - ref).max() / np.abs(ref).max()) for m in got}
-        ms, prof = timed_steps(torch, plan, x0, dt, steps, args.warmup, "cia", flush, True)
-        dms, _ = timed_steps(torch, plan, x0, dt, steps, args.warmup, "direct", flush, False)
+        ms, _ = timed_steps(torch, plan, x0, dt, steps, args.warmup, "cia", flush, False, graph=True)
+        _, prof = timed_steps(torch, plan, x0, dt, steps, args.warmup, "cia", flush, True)
+        dms, _ = timed_steps(torch, plan, x0, dt, steps, args.warmup, "direct", flush, False, graph=True)
         total, dtotal = float(sum(ms)), float(sum(dms))
         stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
         sb = poly_stage_bytes(info)
@@ -714,8 +715,9 @@ def small_configs_leg(args, torch, cia, flush) -> dict:
         got = plan.rhs(x0, method=m).cpu().numpy()[nodes]
         err[m] = coupling_rel_err(got, ref, w.omega[nodes])
     steps, dsteps = 10, 2
-    ms, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
+    ms, _ = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, False, graph=True)
     t_cia = float(sum(ms))
+    _, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
     t_dir = _time_method(torch, plan, x0, w.dt, dsteps, 1, "direct", flush)
     stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
     sb = stage_bytes(plan.info(), "fp32", harmonics=2)
@@ -738,22 +740,29 @@ def small_configs_leg(args, torch, cia, flush) -> dict:
 
 # ------------------------------------------------------------------ GPU arm
 
-def timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, profile: bool):
+def timed_steps(torch, plan, x0, dt, steps, warmup, method, flush, profile: bool, graph: bool = False):
+    """CUDA-event time of each of `steps` RK4 steps (one advance call each,
+    L2 flushed between them outside the events).  profile: events around
+    every stage launch too (per-launch times; plain launches).  graph: the
+    warm-up captures the step's CUDA graph and the timed steps replay it, as
+    cia_advance does for a run of steps; the launches are counted."""
     plan.state_load(x0)
     for _ in range(warmup):
         plan.advance(dt, 1, method=method)
+    if graph and not profile:
+        plan.advance(dt, 2, method=method)   # captures the step graph the timed steps replay
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    if profile:
-        plan.profile_begin(4 * steps)
+    if profile or graph:
+        plan.profile_begin(4 * steps if profile else 0)
     for i in range(steps):
         flush.add_(1.0)                 # evict L2 between timed steps (outside the events)
         ev[i][0].record()
         plan.advance(dt, 1, method=method)
         ev[i][1].record()
     torch.cuda.synchronize()
-    prof = plan.profile_end() if profile else None
+    prof = plan.profile_end() if (profile or graph) else None
     ms = [a.elapsed_time(b) for a, b in ev]
     return ms, prof
 
@@ -810,28 +819,35 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # CIA, timed
+    # CIA, timed: each step replays the captured step graph (as cia_advance
+    # does over a run of steps), L2 flushed between steps
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms, prof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "cia", flush, True)
+        ms, gprof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "cia", flush, False, graph=True)
     barrier()
     total_ms = max_over_ranks(torch, dist, world, float(sum(ms)), "cuda")
     value = job_throughput(g.n, args.steps, world, total_ms / 1e3)
+    # per-launch times of the stage kernel (events around each plain launch)
+    _, prof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "cia", flush, True)
 
     # direct method, same GPU, same steps
     dtotal, dprof = None, None
     if not args.no_direct:
-        dms, dprof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "direct", flush, True)
+        dms, _ = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "direct", flush, False, graph=True)
         dtotal = float(sum(dms))
+        _, dprof = timed_steps(torch, plan, x0, w.dt, args.steps, args.warmup, "direct", flush, True)
 
     # end to end through the public host-buffer call: copies in every step
     e2e_s = None
     if not args.no_e2e:
         xh = torch.from_numpy(w.theta0.copy()).pin_memory().numpy()
-        rh = torch.zeros(1, dtype=torch.float64).pin_memory().numpy()
+        rh = torch.zeros(2, dtype=torch.float64).pin_memory().numpy()
         for _ in range(args.warmup):
-            plan.integrate_host(xh, w.dt, 1, r_out=rh)
+            plan.integrate_host(xh, w.dt, 1, r_out=rh[:1])
+        # a two-step call captures the step graph that the timed one-step calls replay
+        plan.integrate_host(xh, w.dt, 2, r_out=rh)
+        rh = rh[:1]
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -908,7 +924,7 @@ def main():
                      "traffic_source": stage_kernel_source_hash(),
                      "kernel": stage_kernel_name(info), "bytes_per_launch": sb,
                      "avg_launch_ms": stage_avg_ms, "peak_source": pk["source"]},
-        "gpu_launches": int(prof["stage_launches"] + prof["other_launches"]),
+        "gpu_launches": int(gprof["stage_launches"] + gprof["other_launches"]),
         "clocks": clk.summary(),
     }
     if cpu is not None:

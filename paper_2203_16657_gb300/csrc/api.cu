@@ -299,12 +299,17 @@ extern "C" cia_status cia_advance(cia_plan_t *pl, int method, double dt, int64_t
     }
     if (r_out) CIA_CUDA_TRY(cudaMemsetAsync(pl->d.r_counter, 0, sizeof(int64_t), s));
     const bool profiling = pl->prof_on && pl->prof_used < pl->prof_cap;
-    const bool graphs = pl->use_graphs == 0 && nsteps >= 2 && !profiling;
     int slot = pl->state_slot;
+    // a step graph captured by an earlier call for the same method, slot, dt
+    // and order-parameter buffer is replayed from the first step on
+    const bool graph_ready = pl->graph_exec && pl->graph_method == m && pl->graph_slot == slot &&
+                             pl->graph_dt == dt && pl->graph_r == (r_out != nullptr) && pl->graph_r_out == r_out;
+    const bool graphs = pl->use_graphs == 0 && !profiling && (nsteps >= 2 || graph_ready);
     for (int64_t j = 0; j < nsteps; ++j) {
-        if (graphs && j >= 1) {
-            // steps 1.. replay one captured step (step 0 ran plain launches,
-            // which also configured every kernel); 4 stages return the slot
+        if (graphs && (j >= 1 || graph_ready)) {
+            // steps 1.. replay one captured step (step 0 of the capturing
+            // call ran plain launches, which also configured every kernel);
+            // 4 stages return the slot
             if ((st = ensure_step_graph(pl, m, slot, dt, r_out)) != CIA_OK) return st;
             CIA_CUDA_TRY(cudaGraphLaunch(pl->graph_exec, s));
             pl->prof_other += 4 + (r_out ? 1 : 0);
