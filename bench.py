@@ -68,6 +68,8 @@ def parse():
                     help="tile budget of the main workload (cia_options.tile_index_bytes, 0 = default)")
     ap.add_argument("--partition-bench-graph", action="store_true",
                     help="also choose the partition of the 262144-node lognormal graph (about 2 minutes)")
+    ap.add_argument("--ho-tile", default=None,
+                    help="higher-order leg: tile_nodes:tile_index_bytes instead of autotuning (profiling)")
     ap.add_argument("--only", choices=["cs", "ensemble", "small", "poly", "p1", "partition"], default=None,
                     help="run one secondary workload alone and print its JSON object (profiling)")
     return ap.parse_args()
@@ -381,8 +383,9 @@ def cs_leg(args, torch, cia, flush) -> dict:
     check = plan.check_report()["last_error"]
     plan.set_check(every=0, bound=0.0)
     steps = max(3, args.steps // 2)
-    ms, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
-    dms, dprof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "direct", flush, True)
+    ms, _ = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, False)
+    _, prof = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "cia", flush, True)
+    dms, _ = timed_steps(torch, plan, x0, w.dt, steps, args.warmup, "direct", flush, False)
     total, dtotal = float(sum(ms)), float(sum(dms))
     stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
     sb = cs_stage_bytes(info)
@@ -704,7 +707,13 @@ def small_configs_leg(args, torch, cia, flush) -> dict:
                     precision="fp32", build_direct=True)
     x0 = torch.from_numpy(w.theta0.copy()).cuda()
     # 65536 nodes in 256-row tiles leave most CTA slots of the GPU empty: tune the tiling
-    tune = plan.autotune(x0, w.dt, steps=5)
+    if args.ho_tile:
+        tn, tib = (int(v) for v in args.ho_tile.split(":"))
+        plan.retile(tn, tib, "window")
+        plan.state_load(x0)
+        tune = {"fixed": args.ho_tile}
+    else:
+        tune = plan.autotune(x0, w.dt, steps=5)
     sp = oracle.split(g.rowptr, g.col, g.labels)
     nodes = np.linspace(0, g.n - 1, 512).astype(np.int64)
     pair = oracle.kuramoto_direct(g.rowptr, g.col, w.theta0, w.omega, w.K)

@@ -741,6 +741,8 @@ extern "C" cia_status cia_plan_set_basis(cia_plan_t *plan, const cia_basis_t *ba
     if (st != CIA_OK) return st;
     if ((st = check_basis(basis)) != CIA_OK) return st;
     CIA_CUDA_TRY(cudaMemcpy(plan->d.cs_params, basis->params, kParams * sizeof(float), cudaMemcpyDeviceToDevice));
+    CIA_CUDA_TRY(cs_pack_weights(plan, nullptr));
+    CIA_CUDA_TRY(cudaDeviceSynchronize());
     plan->cs_has_basis = true;
     plan->cs_feat_valid = false;
     reset_check(plan);

@@ -109,6 +109,7 @@ struct DeviceBuffers {
     void *cs_feat = nullptr;                  // [n][64] BF16 features of the current stage state
     double *cs_part[2] = {nullptr, nullptr};  // [T][192] tile sums of phi, phi v_x, phi v_y
     float *cs_params = nullptr;               // basis parameters (FP32 master copy)
+    void *cs_wimage = nullptr;                // the basis weights in their shared-memory layout (BF16 W2)
     int32_t *cs_check_nodes = nullptr;        // [check_count] sampled community nodes
     int32_t *cs_check_comm = nullptr;         // their communities
     double *cs_check_out = nullptr;           // [check_count][2] error, reference
@@ -273,6 +274,9 @@ cudaError_t cs_launch_store(cia_plan *pl, double *x, cudaStream_t s);
 cudaError_t cs_launch_check(cia_plan *pl, int slot, cudaStream_t s);
 cudaError_t cs_launch_sample(cia_plan *pl, int slot, int64_t count, uint64_t seed, float *pairs, cudaStream_t s);
 size_t cs_stage_smem_bytes(const cia_plan *pl);
+// Pack the plan's basis parameters into the shared-memory image that every
+// feature-evaluating CTA copies (after cia_plan_set_basis).
+cudaError_t cs_pack_weights(cia_plan *pl, cudaStream_t s);
 
 // General-coupling launchers (general_coupling.cu): the polynomial models and the
 // real 2-D Fourier model, all kept under model CIA_MODEL_POLYNOMIAL internally.

@@ -63,6 +63,7 @@ enum CsMode { kRhs = 0, kStage = 1, kFinal = 2, kLoad = 3 };
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 constexpr size_t kWeightsBytes = align_up(sizeof(mlp::Weights), 1024);
+static_assert(sizeof(mlp::Weights) % 16 == 0, "the weights travel by one bulk copy");
 
 struct CsParams {
     int64_t n;
@@ -84,7 +85,8 @@ struct CsParams {
                                // read by the fused stage launches of the same RK4 step
     double *part_out;          // [tiles][kPart] of y_out's features
     __nv_bfloat16 *feat;       // [n][kRank] features of y_in on entry, of y_out on exit
-    const float *params;       // basis parameters (FP32 master, rounded to BF16 on load)
+    const float *params;       // basis parameters (FP32 master)
+    const mlp::Weights *wimage;  // the same in their shared-memory layout (W2 in BF16), copied by TMA
     float4 *acc;               // [n] sum_s b_s k_s
     double *master;            // [n][4] FP64 master state
     const int32_t *perm;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
     constexpr bool kSums = MODE != kLoad;                    // the right-hand side and the stage update
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar;
+    __shared__ uint64_t wbar;                  // the weights' bulk copy
     __shared__ uint32_t tslot;
     __shared__ float4 yrow[kTileMax];          // stage state of the tile's rows, then the next one
     __shared__ float mom[kPart];               // U_c, H_cx, H_cy (with the 1/N)
@@ -182,9 +185,14 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, r = t & 127, h = t >> 7;
     uint32_t tmem = 0;
     if (kFeatures) {
-        mlp::load_weights(a.params, w);
         if (warp == 0) umma::tmem_alloc(&tslot, 64);
-        if (t == 0) mbar_init(&bar, 1);
+        if (t == 0) {
+            mbar_init(&bar, 1);
+            // the weights arrive by one bulk copy while the tile's sums run
+            mbar_init(&wbar, 1);
+            mbar_arrive_expect_tx(&wbar, (uint32_t)sizeof(mlp::Weights));
+            bulk_g2s(&w, a.wimage, (uint32_t)sizeof(mlp::Weights), &wbar);
+        }
         umma::fence_before_sync();
     }
     __syncthreads();
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
         tmem = tslot;
     }
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = true, have_w = false;
 
     for (int k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
         const int tile = a.tile_order ? a.tile_order[k] : k;   // costliest tiles first
@@ -354,6 +362,13 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
                 // community's first tile (every tile computes the same value)
                 if (tile == a.comm_tile_begin[d.comm]) a.shift[d.comm] = cen;
             }
+            if (!have_w) {
+                have_w = true;
+                if (__syncthreads_or(!mbar_wait_bounded(&wbar, 0, kWaitLimitNs))) {
+                    ok = false;
+                    break;
+                }
+            }
             __syncthreads();
             // (C) features of this state (feature launch) or of the next
             // stage state (fused stage launch) and their tile partial sums
@@ -414,6 +429,8 @@ __global__ void __launch_bounds__(kThreads, CIA_CS_MIN_BLOCKS) cs_stage_kernel(c
             if (t == 0) atomicExch(a.err_flag, 1);
             mbar_wait_bounded(&bar, phase, kWaitLimitNs);
         }
+        // the weights' copy must have landed before the CTA's shared memory is released
+        if (!have_w || !ok) mbar_wait_bounded(&wbar, 0, kWaitLimitNs);
         umma::fence_before_sync();
         __syncthreads();
         if (warp == 0) umma::tmem_dealloc(tmem, 64);
@@ -634,6 +651,7 @@ CsParams base_params(const cia_plan *pl, int slot) {
     a.shift = d.cs_shift;
     a.feat = static_cast<__nv_bfloat16 *>(d.cs_feat);
     a.params = d.cs_params;
+    a.wimage = static_cast<const mlp::Weights *>(d.cs_wimage);
     a.acc = d.cs_acc;
     a.master = d.cs_master;
     a.perm = d.perm;
@@ -661,15 +679,10 @@ cudaError_t launch_stage_t(const cia_plan *pl, const CsParams &a, cudaStream_t s
     const size_t smem = stage_smem(pl, features, MODE != kLoad);
     cudaError_t e = ensure_dynamic_smem((const void *)cs_stage_kernel<MODE>, pl->device, smem);
     if (e != cudaSuccess) return e;
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cs_stage_kernel<MODE>, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    bps = std::max(1, std::min(bps, 8));   // at most 8 x 64 tensor-memory columns per SM
-    // the feature launch keeps one resident CTA per slot (each loads the
-    // weights and allocates tensor memory once); the stage launches take one
-    // CTA per tile and let the hardware start the next tile wherever a slot
-    // frees up
-    const int64_t grid = MODE == kLoad ? std::min<int64_t>(pl->n_tiles, (int64_t)bps * pl->n_sms) : pl->n_tiles;
+    // one CTA per tile (each loads the weights and, when it evaluates
+    // features, allocates tensor memory for its tile); the hardware starts
+    // the next tile wherever a slot frees up
+    const int64_t grid = pl->n_tiles;
     void *args[] = {const_cast<CsParams *>(&a)};
     return cudaLaunchKernel((const void *)cs_stage_kernel<MODE>, dim3((unsigned)std::max<int64_t>(grid, 1)),
                             dim3(kThreads), args, smem, s);
@@ -686,6 +699,24 @@ cudaError_t launch_direct_t(const cia_plan *pl, const CsParams &a, cudaStream_t 
 unsigned grid_1d(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
 }  // namespace
+
+// The weights' shared-memory image in global memory, packed once per basis.
+__global__ void __launch_bounds__(kThreads) cs_pack_weights_kernel(const float *params, mlp::Weights *out) {
+    mlp::load_weights(params, *out);
+}
+
+cudaError_t cs_pack_weights(cia_plan *pl, cudaStream_t s) {
+    if (!pl->d.cs_wimage) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sizeof(mlp::Weights));
+        if (e != cudaSuccess) return e;
+        pl->allocations.push_back(p);
+        pl->device_bytes += (int64_t)sizeof(mlp::Weights);
+        pl->d.cs_wimage = p;
+    }
+    cs_pack_weights_kernel<<<1, kThreads, 0, s>>>(pl->d.cs_params, static_cast<mlp::Weights *>(pl->d.cs_wimage));
+    return cudaGetLastError();
+}
 
 size_t cs_stage_smem_bytes(const cia_plan *pl) {
     return std::max({stage_smem(pl, false, true), stage_smem(pl, true, false), stage_smem(pl, true, true)});

@@ -55,8 +55,10 @@ __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__floa
 __device__ __forceinline__ void load_weights(const float *__restrict__ params, Weights &w) {
     const int t = threadIdx.x;
     for (int i = t; i < kRank * kHidden / 8; i += kThreads) {
-        // 8 consecutive hidden units j of feature row r: one 16-byte store
-        const int r = i / (kHidden / 8), j0 = (i % (kHidden / 8)) * 8;
+        // 8 consecutive hidden units j of feature row r: one 16-byte store;
+        // consecutive threads take consecutive rows of one core-matrix column,
+        // so that eight of them fill 128 contiguous bytes (all 32 banks)
+        const int r = i % kRank, j0 = (i / kRank) * 8;
         const float *src = params + kOffW2 + r * kHidden + j0;
         uint32_t q[4];
 #pragma unroll

@@ -34,13 +34,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Prefetch [src, src + bytes) into L2 (bulk, asynchronous, no completion
-// signal); src and bytes are multiples of 16.
-// bring the 128-byte line holding p into L2 (no register result)
+// Bring the 128-byte line holding p into L2 (no register result).
 __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Prefetch [src, src + bytes) into L2 (bulk, asynchronous, no completion
+// signal); src and bytes are multiples of 16.
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
