@@ -164,11 +164,18 @@ typedef struct {
                                    tiles are shorter), the next tile's copy overlapping the
                                    current tile's node phase.  2, 3 and 4 fall back to 1 when
                                    their buffers do not fit.  Polynomial and Fourier couplings: 1 =
-                                   the community's features from global memory, 0, 2 and 3 = in
-                                   shared memory as 64-bit fixed point (1 when it does not fit). */
+                                   the community's features from global memory, 0, 2, 3 and 4 = in
+                                   shared memory as 64-bit fixed point: tiles are sorted by
+                                   community size and each stage launches one kernel per run of
+                                   tiles that fit 4, 3, 2 or 1 CTAs per SM (window sized to the
+                                   run's largest community), concurrently on streams forked from
+                                   the caller's and joined to it; tiles of a community that no
+                                   window holds read its features from global memory. */
     int use_graphs;             /* 0 = auto: cia_advance replays one captured CUDA graph per RK4
-                                   step when it advances >= 2 steps (not while profiling);
-                                   1 = plain launches only */
+                                   step when it advances >= 2 steps, or from the first step when
+                                   an earlier call captured the graph of the same method, state
+                                   slot, dt and r_out (not while profiling); 1 = plain launches
+                                   only */
 } cia_options;
 
 typedef struct cia_plan cia_plan_t;
