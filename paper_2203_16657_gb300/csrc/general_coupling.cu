@@ -215,13 +215,14 @@ __device__ __forceinline__ long long to_fixed(double u, int sh) {
 template <int MODE, int B, int K, bool WT>
 __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
     constexpr int NR = K - 1 + (WT ? 1 : 0);   // window rows / sparse sums per link
+    constexpr int NRP = NR == 1 ? 1 : (NR + 1) & ~1;   // a node's window entries (even from 2 on)
     constexpr int A0 = WT ? 0 : 1;             // feature of row 0
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double W[kMaxK];
     __shared__ double red[kWarps][kMaxK];
     static_assert(NR * kMaxChunks >= K * kThreads, "the tile sums reuse the chunk table");
-    double *win = reinterpret_cast<double *>(smem_raw);        // [NR][win_cap] features of the community
-    double *sWm = win + (size_t)NR * a.win_cap;                 // [NR][kMaxChunks] missing-chunk sums
+    double *win = reinterpret_cast<double *>(smem_raw);        // [win_cap][NRP] features of the community
+    double *sWm = win + (size_t)NRP * a.win_cap;                // [NR][kMaxChunks] missing-chunk sums
     double *sWi = sWm + NR * kMaxChunks;                        // [NR][kTileMax] inter sums per row
     int *smc = reinterpret_cast<int *>(sWi + NR * kTileMax);    // [kMaxChunks] missing links per chunk
     int *sic = smc + kMaxChunks;                                // [kTileMax] inter links per row
@@ -233,6 +234,15 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
     const unsigned char *b = a.blob + d.blob_off;
     const int cap = a.win_cap;
     long long *wfix = reinterpret_cast<long long *>(win);   // the window after conversion
+    // Node-major window: node l's entries are contiguous, so that a link reads
+    // them with NRP / 2 16-byte loads.  With four entries the two halves of
+    // node l swap places when bit 2 of l is set: load h of eight lanes then
+    // touches 16-byte units 2l + (h ^ bit2(l)), distinct for distinct l mod 8
+    // (the planner orders each quarter-warp's links by l mod 8).
+    auto wslot = [](int l, int r) {
+        if constexpr (NRP == 4) return 4 * l + ((((r >> 1) ^ (l >> 2)) & 1) << 1) + (r & 1);
+        else return NRP * l + r;
+    };
     double unit[NR];                                         // 2^E per row
     // the NR terms of node l: beta_l^[WT] phi_k(x_l), from its state (powers)
     // or its stored features
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
             terms(d.lo + i, q);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                win[r * cap + i] = q[r];
+                win[wslot(i, r)] = q[r];
                 mx[r] = max(mx[r], (unsigned long long)__double_as_longlong(q[r]) & 0x7fffffffffffffffull);
             }
         }
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
         }
         for (int i = threadIdx.x; i < lam; i += kThreads)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) wfix[r * cap + i] = to_fixed(win[r * cap + i], sh[r]);
+            for (int r = 0; r < NRP; ++r) wfix[wslot(i, r)] = r < NR ? to_fixed(win[wslot(i, r)], sh[r < NR ? r : 0]) : 0;
         __syncthreads();
     }
     // (A) sparse feature sums: warp per slice, lane per missing chunk and inter row
@@ -312,12 +322,11 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
         const uint32_t rows = __ldg(srows + s * 32 + lane);
         const uint32_t mrow = rows & 0xffffu, irow = rows >> 16;
         double ms[NR], is[NR];
-        long long mfix[NR];
+        long long mfix[NRP];   // entry NR of an odd NR sums the zero padding
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            ms[r] = is[r] = 0.0;
-            mfix[r] = 0;
-        }
+        for (int r = 0; r < NR; ++r) ms[r] = is[r] = 0.0;
+#pragma unroll
+        for (int r = 0; r < NRP; ++r) mfix[r] = 0;
         int mc = 0, ic = 0;
         const uint4 *mv = mvec + sd.x + lane;
         // one loop per source of the community's features (the fixed-point
@@ -334,8 +343,17 @@ __global__ void __launch_bounds__(kThreads) gc_stage_kernel(const GcParams a) {
                         if (l < lam) {
                             ++mc;
                             if constexpr (decltype(windowed)::value) {
+                                if constexpr (NRP == 1) {
+                                    mfix[0] += wfix[l];
+                                } else {
+                                    const longlong2 *wp = reinterpret_cast<const longlong2 *>(wfix) + (size_t)l * (NRP / 2);
 #pragma unroll
-                                for (int r = 0; r < NR; ++r) mfix[r] += wfix[r * cap + l];
+                                    for (int hh = 0; hh < NRP / 2; ++hh) {
+                                        const longlong2 v = wp[NRP == 4 ? (hh ^ ((l >> 2) & 1)) : hh];
+                                        mfix[2 * hh] += v.x;
+                                        mfix[2 * hh + 1] += v.y;
+                                    }
+                                }
                             } else {
                                 double tq[NR];
                                 terms(d.lo + l, tq);
@@ -508,6 +526,9 @@ __global__ void __launch_bounds__(kThreads) gc_load_kernel(const GcParams a, con
 // Rows of the window and of the sparse sums: features 1..K-1, or 0..K-1 when weighted.
 int rows(const cia_plan *pl) { return pl->gc_k - 1 + (pl->gc_weighted ? 1 : 0); }
 
+// Window entries per node (the node-major window pads an odd row count from 3 on).
+int window_entries(const cia_plan *pl) { return rows(pl) == 1 ? 1 : (rows(pl) + 1) & ~1; }
+
 size_t tables_bytes(int nr) { return (size_t)nr * (kMaxChunks + kTileMax) * 8 + (kMaxChunks + kTileMax) * 4; }
 
 constexpr size_t kStaticReserve = 4096;   // the stage kernel's static shared memory (under 1 KB) and margin
@@ -521,7 +542,7 @@ int64_t window_cap_for(const cia_plan *pl, int per_sm) {
     per_cta = std::min(per_cta, (size_t)pl->smem_optin);
     const size_t fixed = tables_bytes(rows(pl)) + kStaticReserve;
     if (per_cta <= fixed) return 0;
-    return (int64_t)((per_cta - fixed) / (8 * (size_t)rows(pl))) & ~(int64_t)1;
+    return (int64_t)((per_cta - fixed) / (8 * (size_t)window_entries(pl))) & ~(int64_t)1;
 }
 
 // A window launch over a run of tiles: their community windows need at most
@@ -554,7 +575,9 @@ std::vector<Run> window_runs(const cia_plan *pl) {
     return runs;
 }
 
-size_t stage_smem(const cia_plan *pl, int64_t cap) { return (size_t)cap * 8 * rows(pl) + tables_bytes(rows(pl)); }
+size_t stage_smem(const cia_plan *pl, int64_t cap) {
+    return (size_t)cap * 8 * window_entries(pl) + tables_bytes(rows(pl));
+}
 
 GcParams base_params(const cia_plan *pl, int slot) {
     GcParams a{};

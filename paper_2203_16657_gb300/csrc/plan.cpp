@@ -1057,9 +1057,12 @@ static cia_status build_tiles(cia_plan *pl) {
                 const int64_t lam = c >= 0 ? pl->off[c + 1] - pl->off[c] : 0;
                 const uint16_t msent = (uint16_t)lam;
                 // bank groups of the gathered element: 16-byte elements (Cucker--Smale
-                // states, FP64 phasors) are served per quarter-warp, 8-byte ones per half-warp
+                // states, FP64 phasors, the general couplings' node-major windows of
+                // two or more fixed-point features) are served per quarter-warp,
+                // 8-byte ones per half-warp
                 const bool wide = pl->model == CIA_MODEL_CUCKER_SMALE ||
-                                  (pl->model != CIA_MODEL_POLYNOMIAL && pl->precision == CIA_FP64);
+                                  (pl->model != CIA_MODEL_POLYNOMIAL && pl->precision == CIA_FP64) ||
+                                  (pl->model == CIA_MODEL_POLYNOMIAL && pl->gc_k >= 3);
                 const int bank_lanes = wide ? 8 : 16;
                 // padding entries lambda + 1 .. lambda + 16 (zero slots after the window)
                 const bool spread = lam + kPadSlots <= 65535;
