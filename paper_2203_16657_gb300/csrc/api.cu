@@ -449,10 +449,20 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
 extern "C" cia_status cia_sync(cia_plan_t *pl, void *stream) {
     clear_error();
     if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
-    CIA_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    CIA_CUDA_TRY(cudaGetLastError());
+    // the flag is read behind the stream's work, into pinned memory, so that
+    // one synchronisation covers both
+    cudaStream_t s = (cudaStream_t)stream;
     int flag = 0;
-    CIA_CUDA_TRY(cudaMemcpy(&flag, pl->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (pl->d.err_flag_host) {
+        CIA_CUDA_TRY(cudaMemcpyAsync(pl->d.err_flag_host, pl->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CIA_CUDA_TRY(cudaStreamSynchronize(s));
+        CIA_CUDA_TRY(cudaGetLastError());
+        flag = *pl->d.err_flag_host;
+    } else {
+        CIA_CUDA_TRY(cudaStreamSynchronize(s));
+        CIA_CUDA_TRY(cudaGetLastError());
+        CIA_CUDA_TRY(cudaMemcpy(&flag, pl->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     if (flag) {
         CIA_CUDA_TRY(cudaMemset(pl->d.err_flag, 0, sizeof(int)));
         return fail(CIA_ERR_TIMEOUT, "a device-side wait gave up; results since the last cia_sync are invalid");

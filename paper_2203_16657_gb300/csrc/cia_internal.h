@@ -100,6 +100,7 @@ struct DeviceBuffers {
     void *tri = nullptr;                // [n] triadic term by the direct method (higher-order model)
     double *x_tmp = nullptr;            // [n] staging for host-buffer calls
     int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up
+    int *err_flag_host = nullptr;       // pinned host copy of err_flag read by cia_sync
     double *r_tmp = nullptr;            // [r_cap] staging for order parameters
     int64_t r_cap = 0;
     // Cucker--Smale (4 state values per node)

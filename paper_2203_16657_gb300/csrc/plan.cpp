@@ -126,6 +126,8 @@ static void free_all(cia_plan *pl) {
     if (pl->d.r_tmp) cudaFree(pl->d.r_tmp);
     pl->d.r_tmp = nullptr;
     pl->d.r_cap = 0;
+    if (pl->d.err_flag_host) cudaFreeHost(pl->d.err_flag_host);
+    pl->d.err_flag_host = nullptr;
 }
 
 }  // namespace cia
@@ -887,6 +889,7 @@ static cia_status upload_split(cia_plan *pl, const cia_options *opt, const doubl
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
+    if (!d.err_flag_host) CIA_CUDA_TRY(cudaHostAlloc((void **)&d.err_flag_host, sizeof(int), cudaHostAllocDefault));
     if ((s2 = upload<int64_t>(pl, &d.r_counter, nullptr, 1)) != CIA_OK) return s2;
     if (pl->B > 1) UP(d.inst_off, pl->inst_off.data(), pl->inst_off.size());
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {
