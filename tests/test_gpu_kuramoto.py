@@ -352,3 +352,32 @@ def test_partition_choice_beats_the_s_minimal_partition(cia, torch_mod):
     assert rep["communities"][c] < rep["communities"][0] and ms[c] < ms[0]
     assert rep["per_tile_us"] > 0 and rep["community_cost"] > 0
     assert len(np.unique(labels[labels >= 0])) == rep["communities"][c]
+
+
+def test_single_steps_replay_the_captured_graph_bit_exactly(cia, torch_mod):
+    """advance(dt, 2) captures the step graph; later one-step calls with the
+    same dt replay it from their first step.  Five steps taken that way (2 +
+    1 + 1 + 1), and with r(t) through the host-buffer call (one two-step call,
+    then one-step calls), equal five steps of plain launches bit for bit."""
+    g = S.sbm_graph([300, 200, 120], 0.9, inter_degree=4.0, seed=41, n_free=9)
+    rng = np.random.default_rng(42)
+    omega = S.as_fp32_values(rng.normal(size=g.n))
+    theta0 = S.as_fp32_values(rng.uniform(0.0, 2.0 * np.pi, g.n))
+    dt = 0.01
+    states = {}
+    for graphs in (True, False):
+        plan = make_plan(cia, g, omega, 2.0, precision="fp32", use_graphs=graphs, tile_nodes=64)
+        x = torch_mod.from_numpy(theta0.copy()).cuda()
+        plan.state_load(x)
+        plan.advance(dt, 2)
+        for _ in range(3):
+            plan.advance(dt, 1)
+        plan.state_store(x)
+        xh = theta0.copy()
+        r = np.zeros(5)
+        plan.integrate_host(xh, dt, 2, r_out=r[:2])
+        for k in range(3):
+            plan.integrate_host(xh, dt, 1, r_out=r[2 + k:3 + k])
+        states[graphs] = (x.cpu().numpy(), xh, r)
+    for a, b in zip(states[True], states[False]):
+        np.testing.assert_array_equal(a, b)
