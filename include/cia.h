@@ -434,8 +434,11 @@ cia_status cia_integrate(cia_plan_t *plan, int method, double *x, double dt, int
                          double *r_out, void *stream);
 
 /* cia_integrate with HOST buffers: copies x (n x d doubles) to the device, runs,
- * copies x and, if r_out_host is not NULL, nsteps order parameters back, and
- * synchronises the stream.  Pinned host memory makes the copies asynchronous. */
+ * copies x back and, if r_out_host is not NULL, writes nsteps x instances order
+ * parameters there (step-major, as cia_integrate's r_out), then synchronises
+ * the stream.  Pinned host memory makes the copies asynchronous.  The order
+ * parameters are staged in mapped pinned host memory that the plan keeps
+ * (grown on demand). */
 cia_status cia_integrate_host(cia_plan_t *plan, int method, double *x_host, double dt,
                               int64_t nsteps, double *r_out_host, void *stream);
 

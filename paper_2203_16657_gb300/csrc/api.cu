@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -392,12 +393,16 @@ extern "C" cia_status cia_integrate_host(cia_plan_t *pl, int method, double *x_h
     if (!pl || !x_host) return fail(CIA_ERR_INVALID_ARG, "plan or x_host is NULL");
     if (nsteps < 0) return fail(CIA_ERR_INVALID_ARG, "nsteps < 0");
     cudaStream_t s = (cudaStream_t)stream;
-    if (r_out_host && nsteps > pl->d.r_cap) {
-        if (pl->d.r_tmp) cudaFree(pl->d.r_tmp);
-        pl->d.r_tmp = nullptr;
+    // one order parameter per step and instance, staged in mapped pinned host
+    // memory that the order-parameter kernel writes through its device alias
+    const int64_t r_count = nsteps * (int64_t)std::max<int64_t>(pl->B, 1);
+    if (r_out_host && r_count > pl->d.r_cap) {
+        if (pl->d.r_tmp_host) cudaFreeHost(pl->d.r_tmp_host);
+        pl->d.r_tmp = pl->d.r_tmp_host = nullptr;
         pl->d.r_cap = 0;
-        CIA_CUDA_TRY(cudaMalloc(&pl->d.r_tmp, nsteps * sizeof(double)));
-        pl->d.r_cap = nsteps;
+        CIA_CUDA_TRY(cudaHostAlloc((void **)&pl->d.r_tmp_host, (size_t)r_count * sizeof(double), cudaHostAllocMapped));
+        CIA_CUDA_TRY(cudaHostGetDevicePointer((void **)&pl->d.r_tmp, pl->d.r_tmp_host, 0));
+        pl->d.r_cap = r_count;
     }
     const size_t xb = (size_t)pl->n * pl->state_dim * sizeof(double);
     CIA_CUDA_TRY(cudaMemcpyAsync(pl->d.x_tmp, x_host, xb, cudaMemcpyHostToDevice, s));
@@ -405,10 +410,9 @@ extern "C" cia_status cia_integrate_host(cia_plan_t *pl, int method, double *x_h
     if (st != CIA_OK && st != CIA_ERR_FALLBACK) return st;
     const std::string msg = cia_last_error();
     CIA_CUDA_TRY(cudaMemcpyAsync(x_host, pl->d.x_tmp, xb, cudaMemcpyDeviceToHost, s));
-    if (r_out_host && nsteps)
-        CIA_CUDA_TRY(cudaMemcpyAsync(r_out_host, pl->d.r_tmp, nsteps * sizeof(double), cudaMemcpyDeviceToHost, s));
     cia_status st2 = cia_sync(pl, stream);
     if (st2 != CIA_OK) return st2;
+    if (r_out_host && r_count) std::memcpy(r_out_host, pl->d.r_tmp_host, (size_t)r_count * sizeof(double));
     if (st == CIA_ERR_FALLBACK) set_error(msg);
     return st;
 }
@@ -449,22 +453,14 @@ extern "C" cia_status cia_plan_set_weights(cia_plan_t *pl, const double *alpha, 
 extern "C" cia_status cia_sync(cia_plan_t *pl, void *stream) {
     clear_error();
     if (!pl) return fail(CIA_ERR_INVALID_ARG, "plan is NULL");
-    // the flag is read behind the stream's work, into pinned memory, so that
-    // one synchronisation covers both
-    cudaStream_t s = (cudaStream_t)stream;
-    int flag = 0;
-    if (pl->d.err_flag_host) {
-        CIA_CUDA_TRY(cudaMemcpyAsync(pl->d.err_flag_host, pl->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CIA_CUDA_TRY(cudaStreamSynchronize(s));
-        CIA_CUDA_TRY(cudaGetLastError());
-        flag = *pl->d.err_flag_host;
-    } else {
-        CIA_CUDA_TRY(cudaStreamSynchronize(s));
-        CIA_CUDA_TRY(cudaGetLastError());
-        CIA_CUDA_TRY(cudaMemcpy(&flag, pl->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost));
-    }
+    // the flag lives in mapped pinned host memory: once the stream's work has
+    // finished, whatever a kernel wrote there is visible to the host
+    CIA_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CIA_CUDA_TRY(cudaGetLastError());
+    volatile int *flag_host = pl->d.err_flag_host;
+    const int flag = flag_host ? *flag_host : 0;
     if (flag) {
-        CIA_CUDA_TRY(cudaMemset(pl->d.err_flag, 0, sizeof(int)));
+        *flag_host = 0;
         return fail(CIA_ERR_TIMEOUT, "a device-side wait gave up; results since the last cia_sync are invalid");
     }
     return CIA_OK;

@@ -99,9 +99,12 @@ struct DeviceBuffers {
     double *rhs_tmp = nullptr;          // [n] staging for host-buffer calls
     void *tri = nullptr;                // [n] triadic term by the direct method (higher-order model)
     double *x_tmp = nullptr;            // [n] staging for host-buffer calls
-    int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up
-    int *err_flag_host = nullptr;       // pinned host copy of err_flag read by cia_sync
-    double *r_tmp = nullptr;            // [r_cap] staging for order parameters
+    int *err_flag = nullptr;            // set by a kernel whose bounded wait gave up (device alias
+                                        // of err_flag_host)
+    int *err_flag_host = nullptr;       // the flag in mapped pinned host memory, read by cia_sync
+    double *r_tmp = nullptr;            // [r_cap] staging for order parameters (device alias
+                                        // of r_tmp_host)
+    double *r_tmp_host = nullptr;       // the same in mapped pinned host memory
     int64_t r_cap = 0;
     // Cucker--Smale (4 state values per node)
     float4 *cs_y[2] = {nullptr, nullptr};     // [n] FP32 stage states (s_x, s_y, v_x, v_y)

@@ -123,11 +123,12 @@ static void free_all(cia_plan *pl) {
     pl->tile_allocs.clear();
     for (cudaEvent_t e : pl->prof_ev) cudaEventDestroy(e);
     pl->prof_ev.clear();
-    if (pl->d.r_tmp) cudaFree(pl->d.r_tmp);
-    pl->d.r_tmp = nullptr;
+    if (pl->d.r_tmp_host) cudaFreeHost(pl->d.r_tmp_host);
+    pl->d.r_tmp = pl->d.r_tmp_host = nullptr;
     pl->d.r_cap = 0;
     if (pl->d.err_flag_host) cudaFreeHost(pl->d.err_flag_host);
     pl->d.err_flag_host = nullptr;
+    pl->d.err_flag = nullptr;
 }
 
 }  // namespace cia
@@ -888,8 +889,14 @@ static cia_status upload_split(cia_plan *pl, const cia_options *opt, const doubl
     CIA_CUDA_TRY(cudaDeviceGetAttribute(&pl->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, pl->device));
     if ((s2 = upload<double>(pl, &d.rhs_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
     if ((s2 = upload<double>(pl, &d.x_tmp, nullptr, (size_t)n * pl->state_dim)) != CIA_OK) return s2;
-    if ((s2 = upload<int>(pl, &d.err_flag, nullptr, 1)) != CIA_OK) return s2;
-    if (!d.err_flag_host) CIA_CUDA_TRY(cudaHostAlloc((void **)&d.err_flag_host, sizeof(int), cudaHostAllocDefault));
+    // the error flag lives in mapped pinned host memory: kernels that give up a
+    // bounded wait set it through its device alias, cia_sync reads it after
+    // synchronising without a copy
+    if (!d.err_flag_host) {
+        CIA_CUDA_TRY(cudaHostAlloc((void **)&d.err_flag_host, sizeof(int), cudaHostAllocMapped));
+        *d.err_flag_host = 0;
+        CIA_CUDA_TRY(cudaHostGetDevicePointer((void **)&d.err_flag, d.err_flag_host, 0));
+    }
     if ((s2 = upload<int64_t>(pl, &d.r_counter, nullptr, 1)) != CIA_OK) return s2;
     if (pl->B > 1) UP(d.inst_off, pl->inst_off.data(), pl->inst_off.size());
     if (pl->model == CIA_MODEL_CUCKER_SMALE) {

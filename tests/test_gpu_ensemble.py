@@ -116,6 +116,35 @@ def test_batch_integrate_and_order_parameters(P, oracle_mod):
         o += n
 
 
+def test_host_buffer_integration_of_an_ensemble(P):
+    """cia_integrate_host on an ensemble returns steps x instances order
+    parameters; from pinned and from pageable memory it equals cia_integrate
+    on device buffers bit for bit, twice in a row."""
+    import torch
+    e = _small(5)
+    B, steps = len(e.instances), 7
+    x0 = _concat([w.theta0 for w in e.instances])
+    plan = _batch_plan(P, e.instances)
+    xd = torch.from_numpy(x0.copy()).cuda()
+    rd = torch.zeros(steps * B, dtype=torch.float64, device="cuda")
+    want = []
+    for _ in range(2):
+        plan.integrate(xd, e.dt, steps, r_out=rd)
+        plan.sync()
+        want.append((xd.cpu().numpy().copy(), rd.cpu().numpy().copy()))
+    for pinned in (True, False):
+        xh = torch.from_numpy(x0.copy())
+        rh = torch.zeros(steps * B, dtype=torch.float64)
+        if pinned:
+            xh, rh = xh.pin_memory(), rh.pin_memory()
+        xn, rn = xh.numpy(), rh.numpy()
+        for k in range(2):
+            plan.integrate_host(xn, e.dt, steps, r_out=rn)
+            np.testing.assert_array_equal(xn, want[k][0])
+            np.testing.assert_array_equal(rn, want[k][1])
+            assert (rn > 0).all()
+
+
 def test_graph_replay_is_bit_identical_to_plain_launches(P):
     import torch
     e = _small(6)
